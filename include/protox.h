@@ -1,0 +1,151 @@
+/*
+ * protox.h - C ABI of the B300 (sm_103a) fused periodic 2D Poisson relaxation
+ * library, after ProtoX (Mankad, Rao, Colella, Van Straalen, Franchetti,
+ * "ProtoX: A First Look").
+ *
+ * The library solves the model problem of Sec. IV, Delta phi = rho on a periodic
+ * rectangular grid of cell-centred cells with spacing h, with the 5-point
+ * Laplacian L (taps [0,1,0; 1,-4,1; 0,1,0], scaled by 1/h^2) and weighted
+ * point-Jacobi relaxation (Eq. "jacobi" with a weight omega):
+ *
+ *     phi' = phi + (omega h^2 / 4) (L phi - rho)
+ *
+ * The paper's lambda = h^2/(4D) is omega = 1/D = 1/2 in D = 2 dimensions.
+ * One sweep fuses the periodic ghost fill, the Laplacian, the Jacobi update and
+ * the max-norm of the residual rho - L phi of the sweep's INPUT state into one
+ * pass over memory (the Sigma-OL loop merging of Sec. IV).
+ *
+ * Conventions shared by every call
+ * ---------------------------------
+ *  - Fields are row-major, x fastest: cell (i, j) is at element
+ *    off + j*ld + i with off = 0 (ghost = 0) or ld + 1 (ghost = 1).
+ *    Every field pointer of one call uses the layout of its px_grid.
+ *  - Field pointers are DEVICE pointers owned by the caller (e.g. the
+ *    data_ptr() of a CUDA tensor). The library never frees them.
+ *  - The px_ctx owns its scratch memory (ping-pong buffer, reduction slots),
+ *    allocated on first need with cudaMalloc and grown on demand; a call
+ *    that grows it synchronises the device.
+ *  - Streams are passed as void* (a cudaStream_t); NULL is the legacy
+ *    default stream. Work is enqueued asynchronously unless a call says
+ *    it synchronises.
+ *  - Every call returns a px_status and never aborts or throws across the
+ *    ABI. Arguments are validated before any launch; on error nothing is
+ *    launched and px_last_error() holds a one-line message. Asynchronous
+ *    device errors surface as PX_ECUDA from the next synchronising call.
+ *  - A ctx is bound to the device given at creation. It is not thread-safe:
+ *    one host thread at a time per ctx.
+ */
+#ifndef PROTOX_H
+#define PROTOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PX_OK = 0,
+  PX_EINVAL = 1,        /* bad argument (size, pointer, alias, layout, value) */
+  PX_ECUDA = 2,         /* a CUDA runtime call failed */
+  PX_ENOMEM = 3,        /* device scratch allocation failed */
+  PX_ENOCONV = 4,       /* solve hit its sweep limit before the tolerance */
+  PX_ETIMEOUT = 5,      /* solve or device wait ran past its time limit */
+  PX_EMEAN = 6,         /* rho has a nonzero mean: the periodic problem has no solution */
+  PX_ENAN = 7,          /* a residual became NaN or Inf */
+  PX_EUNSUPPORTED = 8   /* valid request this build does not implement */
+} px_status;
+
+typedef enum { PX_F64 = 0, PX_F32 = 1 } px_dtype;
+
+/* Layout of one periodic field (Sec. III "Proto": Box / BoxData on a periodic
+ * rectangular grid; Sec. IV: an n x n box stored as m x m, m = n + 2 with
+ * ghosts). */
+typedef struct {
+  int32_t nx, ny;  /* interior cells along x (fastest) and y; >= 0 (0 = empty, no-op) */
+  int64_t ld;      /* elements between row starts; >= nx + 2*ghost */
+  int32_t ghost;   /* 0: plain periodic array (ny rows).
+                      1: one ghost layer around the interior, (ny + 2) rows;
+                         input ghosts are ignored (the kernels wrap periodically
+                         while loading) and output ghosts are written with the
+                         periodic images of the interior. */
+  int32_t dtype;   /* px_dtype of every field of the call */
+  double h;        /* mesh spacing, finite and > 0 */
+} px_grid;
+
+typedef struct px_ctx px_ctx;
+
+/* Create a context on CUDA device `device`. *out is NULL on failure. */
+px_status px_create(px_ctx** out, int device);
+
+/* Synchronise the context's device, free its scratch and the context.
+ * NULL is accepted. */
+px_status px_destroy(px_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none). Valid until the next
+ * call on ctx. ctx may be NULL (then a message of the last px_create). */
+const char* px_last_error(const px_ctx* ctx);
+
+/* Static name of a status code. */
+const char* px_status_string(px_status s);
+
+/* Laplacian (Sec. IV, OL rule Laplace): lphi = L phi = s / h^2, s the
+ * unscaled 5-point tap sum with periodic wrap. Computed in the grid's dtype.
+ * phi and lphi must not overlap. Asynchronous. */
+px_status px_apply_stencil(px_ctx* ctx, const px_grid* g, const void* phi,
+                           void* lphi, void* stream);
+
+/* nsweeps fused sweeps (Sec. IV: Laplace, Jacobi and max-norm merged into
+ * one loop; Eq. "jacobi" with weight omega) from phi_in into phi_out.
+ *
+ *  phi_in, phi_out  fields of layout g; phi_in == phi_out is allowed (the
+ *                   context ping-pongs through scratch); any other overlap
+ *                   is PX_EINVAL. phi_in is not modified unless it is phi_out.
+ *  rho              right-hand side, layout g, must not overlap phi_out.
+ *  omega            Jacobi weight, finite (2/3 damps the upper half of the
+ *                   spectrum by at least 1/3 per sweep; 1/2 is the paper's).
+ *  nsweeps          >= 0; 0 copies phi_in to phi_out.
+ *  tblock           sweeps fused per launch (temporal blocking), 0 = choose
+ *                   automatically, else 1..8. A depth the layout cannot use
+ *                   (ghosted, unaligned or x-extent not a multiple of the
+ *                   vector width) silently runs at depth 1; results do not
+ *                   depend on it beyond rounding.
+ *  resid_dev        NULL, or DEVICE array of ceil(nsweeps / report_every)
+ *                   doubles: resid_dev[k] = ||rho - L phi^(k*report_every)||_inf,
+ *                   the max-norm residual of state k*report_every (state 0 is
+ *                   phi_in), computed inside the sweep that reads that state
+ *                   (Sec. IV step 3). The call zero-fills the array first.
+ *                   FP32 fields report the FP32 residual.
+ *  report_every     >= 0; 0 disables reports.
+ * Asynchronous. */
+px_status px_relax_n(px_ctx* ctx, const px_grid* g, const void* phi_in,
+                     void* phi_out, const void* rho, double omega, int nsweeps,
+                     int tblock, double* resid_dev, int report_every,
+                     void* stream);
+
+/* The launch plan px_relax_n would use for these arguments, without running
+ * it: *tblock_used = sweeps fused per launch (after auto choice and layout
+ * fallback), *launches = relax kernel launches (excluding the zero-fill of
+ * resid_dev and a staging copy). Either output may be NULL. Pure host call. */
+px_status px_relax_plan(px_ctx* ctx, const px_grid* g, const void* phi_in,
+                        const void* phi_out, const void* rho, int nsweeps,
+                        int tblock, int* tblock_used, int* launches);
+
+/* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
+ * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,
+ * *rho_norm_host = ||rho||_inf. Evaluated in FP64 for both dtypes (FP32 fields
+ * are widened exactly). NaN anywhere gives NaN. SYNCHRONISES the stream. */
+px_status px_residual_norm(px_ctx* ctx, const px_grid* g, const void* phi,
+                           const void* rho, double* out_host,
+                           double* rho_norm_host, void* stream);
+
+/* Asynchronous form of px_residual_norm: out_dev (DEVICE, 2 doubles) receives
+ * {||rho - L phi||_inf, ||rho||_inf}. out_dev is overwritten, not maxed into. */
+px_status px_residual_norm_async(px_ctx* ctx, const px_grid* g, const void* phi,
+                                 const void* rho, double* out_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROTOX_H */

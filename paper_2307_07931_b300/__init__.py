@@ -1,0 +1,224 @@
+"""Python binding of libprotox.so, the B300 fused periodic Poisson relaxation
+library (ProtoX, Sec. IV). Argument marshalling only: every step of the
+computation runs in the library's CUDA kernels. PyTorch supplies device
+memory and streams.
+
+The names mirror the C ABI in include/protox.h:
+    create / destroy / last_error          px_create / px_destroy / px_last_error
+    apply_stencil(ctx, phi, lphi)          px_apply_stencil
+    relax_n(ctx, phi_in, phi_out, rho,...) px_relax_n
+    residual_norm(ctx, phi, rho)           px_residual_norm
+Fields are CUDA tensors of shape (ny, nx) (ghost=0) or (ny + 2, nx + 2)
+(ghost=1), dtype float64 or float32, unit stride along x; the row stride is
+passed as the pitch ld.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libprotox.so")
+
+PX_OK, PX_EINVAL, PX_ECUDA, PX_ENOMEM, PX_ENOCONV, PX_ETIMEOUT, PX_EMEAN, PX_ENAN, \
+    PX_EUNSUPPORTED = range(9)
+PX_F64, PX_F32 = 0, 1
+
+
+class PxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ld", ctypes.c_int64),
+                ("ghost", ctypes.c_int32), ("dtype", ctypes.c_int32), ("h", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libprotox.so (build it first with paper_2307_07931_b300.build).
+    Raises ImportError if the library is absent: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libprotox.so not found at {path}; run "
+                          "`python -m paper_2307_07931_b300.build` (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    gp = ctypes.POINTER(Grid)
+    i, d = ctypes.c_int, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.px_create.argtypes = [ctypes.POINTER(_vp), i]
+    lib.px_destroy.argtypes = [_vp]
+    lib.px_last_error.argtypes = [_vp]
+    lib.px_last_error.restype = ctypes.c_char_p
+    lib.px_status_string.argtypes = [i]
+    lib.px_status_string.restype = ctypes.c_char_p
+    lib.px_apply_stencil.argtypes = [_vp, gp, _vp, _vp, _vp]
+    lib.px_relax_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
+    lib.px_residual_norm.argtypes = [_vp, gp, _vp, _vp, dp, dp, _vp]
+    lib.px_residual_norm_async.argtypes = [_vp, gp, _vp, _vp, _vp, _vp]
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.px_relax_plan.argtypes = [_vp, gp, _vp, _vp, _vp, i, i, ip, ip]
+    for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
+                 "px_residual_norm", "px_residual_norm_async", "px_relax_plan"):
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def status_name(s: int) -> str:
+    return load_library().px_status_string(int(s)).decode()
+
+
+# ----------------------------------------------------------------- contexts
+class Context:
+    """Owns one px_ctx (device scratch and reduction slots) on one device."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        h = _vp()
+        s = lib.px_create(ctypes.byref(h), int(device))
+        if s != PX_OK:
+            raise PxError(s, lib.px_last_error(None).decode())
+        self.handle = h
+        self.device = int(device)
+
+    def check(self, s: int):
+        if s != PX_OK:
+            raise PxError(s, load_library().px_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            load_library().px_destroy(self.handle)
+            self.handle = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_default: dict[int, Context] = {}
+
+
+def context(device: int | None = None) -> Context:
+    """The process-wide default Context of a device (created on first use)."""
+    import torch
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _default:
+        _default[dev] = Context(dev)
+    return _default[dev]
+
+
+# ----------------------------------------------------------------- marshalling
+def grid_of(t, h: float, ghost: int = 0) -> Grid:
+    """px_grid describing tensor t of shape (ny + 2 ghost, nx + 2 ghost)."""
+    import torch
+    if t.dim() != 2:
+        raise ValueError("fields are 2D tensors (ny, nx)")
+    if t.stride(1) != 1:
+        raise ValueError("fields need unit stride along x")
+    if t.dtype == torch.float64:
+        dt = PX_F64
+    elif t.dtype == torch.float32:
+        dt = PX_F32
+    else:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    ny, nx = t.shape[0] - 2 * ghost, t.shape[1] - 2 * ghost
+    return Grid(nx, ny, t.stride(0) if t.shape[0] > 1 else t.shape[1] + 0, ghost, dt, float(h))
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _same_layout(a, b):
+    if a.shape != b.shape or a.dtype != b.dtype or a.stride() != b.stride():
+        raise ValueError("fields of one call must share shape, dtype and strides")
+
+
+# ----------------------------------------------------------------- the calls
+def apply_stencil(phi, lphi, h: float, ghost: int = 0, ctx: Context | None = None,
+                  stream=None):
+    """lphi = L phi (px_apply_stencil)."""
+    _same_layout(phi, lphi)
+    ctx = ctx or context(phi.device.index)
+    g = grid_of(phi, h, ghost)
+    ctx.check(load_library().px_apply_stencil(ctx.handle, ctypes.byref(g), _ptr(phi),
+                                              _ptr(lphi), _stream(stream)))
+    return lphi
+
+
+def relax_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, tblock: int = 0,
+            resid=None, report_every: int = 0, ghost: int = 0, ctx: Context | None = None,
+            stream=None):
+    """nsweeps fused sweeps phi_in -> phi_out (px_relax_n). `resid`, if given,
+    is a float64 CUDA tensor of ceil(nsweeps / report_every) entries."""
+    _same_layout(phi_in, phi_out)
+    _same_layout(phi_in, rho)
+    ctx = ctx or context(phi_in.device.index)
+    g = grid_of(phi_in, h, ghost)
+    if resid is not None:
+        import torch
+        need = (nsweeps + report_every - 1) // report_every if report_every > 0 else 0
+        if resid.dtype != torch.float64 or not resid.is_cuda or resid.numel() < need \
+                or not resid.is_contiguous():
+            raise ValueError(f"resid must be a contiguous CUDA float64 tensor of >= {need}")
+    ctx.check(load_library().px_relax_n(ctx.handle, ctypes.byref(g), _ptr(phi_in),
+                                        _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
+                                        int(tblock), _ptr(resid), int(report_every),
+                                        _stream(stream)))
+    return phi_out
+
+
+def relax_plan(phi_in, phi_out, rho, h: float, nsweeps: int, tblock: int = 0, ghost: int = 0,
+               ctx: Context | None = None) -> tuple[int, int]:
+    """(sweeps per launch, kernel launches) that relax_n would use (px_relax_plan)."""
+    ctx = ctx or context(phi_in.device.index)
+    g = grid_of(phi_in, h, ghost)
+    tb, nl = ctypes.c_int(), ctypes.c_int()
+    ctx.check(load_library().px_relax_plan(ctx.handle, ctypes.byref(g), _ptr(phi_in),
+                                           _ptr(phi_out), _ptr(rho), int(nsweeps), int(tblock),
+                                           ctypes.byref(tb), ctypes.byref(nl)))
+    return tb.value, nl.value
+
+
+def residual_norm(phi, rho, h: float, ghost: int = 0, ctx: Context | None = None,
+                  stream=None) -> tuple[float, float]:
+    """(||rho - L phi||_inf, ||rho||_inf) in FP64 (px_residual_norm; synchronises)."""
+    _same_layout(phi, rho)
+    ctx = ctx or context(phi.device.index)
+    g = grid_of(phi, h, ghost)
+    r, p = ctypes.c_double(), ctypes.c_double()
+    ctx.check(load_library().px_residual_norm(ctx.handle, ctypes.byref(g), _ptr(phi),
+                                              _ptr(rho), ctypes.byref(r), ctypes.byref(p),
+                                              _stream(stream)))
+    return r.value, p.value
+
+
+def residual_norm_async(phi, rho, out, h: float, ghost: int = 0, ctx: Context | None = None,
+                        stream=None):
+    """out[0:2] = (||rho - L phi||_inf, ||rho||_inf) on the device, no sync."""
+    _same_layout(phi, rho)
+    ctx = ctx or context(phi.device.index)
+    g = grid_of(phi, h, ghost)
+    ctx.check(load_library().px_residual_norm_async(ctx.handle, ctypes.byref(g), _ptr(phi),
+                                                    _ptr(rho), _ptr(out), _stream(stream)))
+    return out

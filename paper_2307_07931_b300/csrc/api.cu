@@ -1,0 +1,339 @@
+// C ABI of the fused periodic Poisson relaxation library (declared in
+// include/protox.h). Validates every argument before any launch, plans the
+// temporal-blocking launches of a relax call and ping-pongs between the
+// caller's output and context scratch so that phi_in == phi_out works.
+#include "../../include/protox.h"
+#include "px_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+struct px_ctx {
+  int device = 0;
+  void* scratch = nullptr;   // ping-pong field buffer
+  size_t scratch_bytes = 0;
+  double* red = nullptr;     // 2 doubles of device reduction output
+  double* red_host = nullptr;  // pinned mirror of red
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+px_status fail(px_ctx* c, px_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf; else g_create_err = buf;
+  return s;
+}
+
+px_status cuda_fail(px_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? PX_ENOMEM : PX_ECUDA, "%s: %s (%s)", what,
+              cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// Makes the context's device current for the scope of a call and restores the
+// caller's device afterwards.
+struct DeviceScope {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t elem_size(int dtype) { return dtype == PX_F64 ? 8 : 4; }
+
+px_status check_grid(px_ctx* c, const px_grid* g, px::FieldDesc* f) {
+  if (!g) return fail(c, PX_EINVAL, "grid is NULL");
+  if (g->dtype != PX_F64 && g->dtype != PX_F32)
+    return fail(c, PX_EINVAL, "dtype %d is not PX_F64 or PX_F32", (int)g->dtype);
+  if (g->ghost != 0 && g->ghost != 1) return fail(c, PX_EINVAL, "ghost must be 0 or 1");
+  if (g->nx < 0 || g->ny < 0) return fail(c, PX_EINVAL, "negative extent %d x %d", g->nx, g->ny);
+  if (g->nx > (1 << 29) || g->ny > (1 << 29))
+    return fail(c, PX_EINVAL, "extent %d x %d above 2^29", g->nx, g->ny);
+  if (g->ld < (int64_t)g->nx + 2 * g->ghost)
+    return fail(c, PX_EINVAL, "ld %lld < nx + 2*ghost", (long long)g->ld);
+  if (!(std::isfinite(g->h) && g->h > 0.0)) return fail(c, PX_EINVAL, "h must be finite and > 0");
+  const double ih2 = 1.0 / (g->h * g->h);
+  if (!std::isfinite(ih2)) return fail(c, PX_EINVAL, "1/h^2 overflows");
+  const double rows = (double)g->ny + 2 * g->ghost;
+  if (rows * (double)g->ld * elem_size(g->dtype) > 9.0e18)
+    return fail(c, PX_EINVAL, "field too large");
+  f->nx = g->nx;
+  f->ny = g->ny;
+  f->ld = g->ld;
+  f->ghost = g->ghost;
+  f->off = g->ghost ? g->ld + 1 : 0;
+  f->dtype = g->dtype;
+  f->h = g->h;
+  return PX_OK;
+}
+
+// Bytes from the field's base pointer to one past its last element.
+size_t field_span(const px::FieldDesc& f) {
+  const int64_t rows = f.ny + 2 * f.ghost;
+  if (rows == 0 || f.nx == 0) return 0;
+  return (size_t)(((rows - 1) * f.ld + f.nx + 2 * f.ghost) * (int64_t)elem_size(f.dtype));
+}
+
+bool overlap(const void* a, const void* b, size_t n) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return n > 0 && x < y + n && y < x + n;
+}
+
+px_status ensure_scratch(px_ctx* c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return PX_OK;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  cudaError_t e = cudaMalloc(&c->scratch, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PX_ENOMEM, "scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  }
+  c->scratch_bytes = bytes;
+  return PX_OK;
+}
+
+int auto_tblock(const px::FieldDesc& f) {
+  // FP64 is bound by the FP64 pipe at depth 1, so deeper blocking only adds
+  // redundant halo work; FP32 is bound by HBM at depth 1.
+  if (f.dtype == PX_F64) return 1;
+  const int64_t cells = (int64_t)f.nx * f.ny;
+  return cells >= (1 << 16) ? 4 : 1;
+}
+
+
+// Launch sizes of a relax call: T, T, ..., remainder, with T the requested or
+// automatic depth (1 when the layout cannot use the tiled kernel). In place,
+// the first launch must not write the buffer it reads: an odd launch count is
+// made even by splitting a multi-sweep launch, else the input is staged into
+// scratch first (*copy_first).
+std::vector<int> plan_launches(const px::FieldDesc& f, bool vec, bool inplace, int nsweeps,
+                               int tblock, bool* copy_first) {
+  int T = tblock == 0 ? auto_tblock(f) : tblock;
+  if (!vec) T = 1;
+  std::vector<int> sizes;
+  for (int left = nsweeps; left > 0; left -= T) sizes.push_back(left < T ? left : T);
+  *copy_first = false;
+  if (inplace && (sizes.size() % 2 == 1)) {
+    size_t k = 0;
+    while (k < sizes.size() && sizes[k] < 2) ++k;
+    if (k < sizes.size()) {
+      const int a = sizes[k];
+      sizes[k] = 1;
+      sizes.insert(sizes.begin() + (long)k + 1, a - 1);
+    } else {
+      *copy_first = true;
+    }
+  }
+  return sizes;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* px_status_string(px_status s) {
+  switch (s) {
+    case PX_OK: return "PX_OK";
+    case PX_EINVAL: return "PX_EINVAL";
+    case PX_ECUDA: return "PX_ECUDA";
+    case PX_ENOMEM: return "PX_ENOMEM";
+    case PX_ENOCONV: return "PX_ENOCONV";
+    case PX_ETIMEOUT: return "PX_ETIMEOUT";
+    case PX_EMEAN: return "PX_EMEAN";
+    case PX_ENAN: return "PX_ENAN";
+    case PX_EUNSUPPORTED: return "PX_EUNSUPPORTED";
+  }
+  return "PX_UNKNOWN";
+}
+
+px_status px_create(px_ctx** out, int device) {
+  if (!out) return fail(nullptr, PX_EINVAL, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, PX_ECUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) return fail(nullptr, PX_EINVAL, "device %d of %d", device, n);
+  DeviceScope ds(device);
+  if (!ds.ok) return fail(nullptr, PX_ECUDA, "cudaSetDevice(%d) failed", device);
+  px_ctx* c = new (std::nothrow) px_ctx();
+  if (!c) return fail(nullptr, PX_ENOMEM, "host allocation failed");
+  c->device = device;
+  e = cudaMalloc(&c->red, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, 2 * sizeof(double));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->red) cudaFree(c->red);
+    delete c;
+    return fail(nullptr, PX_ENOMEM, "context buffers: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return PX_OK;
+}
+
+px_status px_destroy(px_ctx* c) {
+  if (!c) return PX_OK;
+  DeviceScope ds(c->device);
+  cudaDeviceSynchronize();
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->red) cudaFree(c->red);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  delete c;
+  return PX_OK;
+}
+
+const char* px_last_error(const px_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+px_status px_apply_stencil(px_ctx* c, const px_grid* g, const void* phi, void* lphi,
+                           void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (f.nx == 0 || f.ny == 0) return PX_OK;
+  if (!phi || !lphi) return fail(c, PX_EINVAL, "NULL field pointer");
+  if (overlap(phi, lphi, field_span(f))) return fail(c, PX_EINVAL, "phi and lphi overlap");
+  DeviceScope ds(c->device);
+  cudaError_t e = px::launch_apply_stencil(f, phi, lphi, (cudaStream_t)stream);
+  return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "apply_stencil launch");
+}
+
+px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_out,
+                     const void* rho, double omega, int nsweeps, int tblock,
+                     double* resid_dev, int report_every, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (nsweeps < 0) return fail(c, PX_EINVAL, "nsweeps %d < 0", nsweeps);
+  if (report_every < 0) return fail(c, PX_EINVAL, "report_every %d < 0", report_every);
+  if (tblock < 0 || tblock > 8) return fail(c, PX_EINVAL, "tblock %d not in 0..8", tblock);
+  if (!std::isfinite(omega)) return fail(c, PX_EINVAL, "omega must be finite");
+  const bool reports = resid_dev && report_every > 0 && nsweeps > 0;
+  const int nrep = reports ? (nsweeps + report_every - 1) / report_every : 0;
+  DeviceScope ds(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (reports) {
+    cudaError_t e = cudaMemsetAsync(resid_dev, 0, sizeof(double) * (size_t)nrep, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear resid_dev");
+  }
+  if (f.nx == 0 || f.ny == 0) return PX_OK;
+  if (!phi_in || !phi_out || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
+  const size_t span = field_span(f);
+  const bool inplace = phi_in == phi_out;
+  if (!inplace && overlap(phi_in, phi_out, span))
+    return fail(c, PX_EINVAL, "phi_in and phi_out overlap without being equal");
+  if (overlap(rho, phi_out, span)) return fail(c, PX_EINVAL, "rho overlaps phi_out");
+  if (reports && overlap(resid_dev, phi_out, span))
+    return fail(c, PX_EINVAL, "resid_dev overlaps phi_out");
+
+  if (nsweeps == 0) {
+    if (inplace) return PX_OK;
+    cudaError_t e = px::launch_copy_field(f, phi_in, phi_out, st);
+    return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "copy launch");
+  }
+
+  const bool vec = px::vector_ok(f, phi_in, phi_out, rho);
+  bool copy_first = false;
+  std::vector<int> sizes = plan_launches(f, vec, inplace, nsweeps, tblock, &copy_first);
+  const size_t L = sizes.size();
+  if (L >= 2 || copy_first) {
+    // Scratch uses the caller's layout (same pitch and ghost offset), and
+    // cudaMalloc returns 256-byte aligned memory, so alignment is preserved.
+    s = ensure_scratch(c, span);
+    if (s != PX_OK) return s;
+  }
+  void* scratch = c->scratch;
+  const void* src = phi_in;
+  if (copy_first) {
+    cudaError_t e = px::launch_copy_field(f, phi_in, scratch, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy launch");
+    src = scratch;
+  }
+  const bool vec_all = vec && (L < 2 && !copy_first ? true : px::vector_ok(f, scratch, scratch, scratch));
+  int s0 = 0;
+  for (size_t k = 0; k < L; ++k) {
+    void* dst = ((L - 1 - k) % 2 == 0) ? phi_out : scratch;
+    cudaError_t e = px::launch_relax(f, src, dst, rho, omega, sizes[k], vec_all,
+                                     reports ? resid_dev : nullptr, s0, report_every, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "relax launch");
+    s0 += sizes[k];
+    src = dst;
+  }
+  return PX_OK;
+}
+
+px_status px_relax_plan(px_ctx* c, const px_grid* g, const void* phi_in,
+                        const void* phi_out, const void* rho, int nsweeps, int tblock,
+                        int* tblock_used, int* launches) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (nsweeps < 0 || tblock < 0 || tblock > 8) return fail(c, PX_EINVAL, "bad nsweeps/tblock");
+  const bool vec = px::vector_ok(f, phi_in, phi_out, rho);
+  bool copy_first = false;
+  std::vector<int> sizes = plan_launches(f, vec, phi_in == phi_out, nsweeps, tblock, &copy_first);
+  int tb = 0;
+  for (int v : sizes) tb = v > tb ? v : tb;
+  if (tblock_used) *tblock_used = tb;
+  if (launches) *launches = (int)sizes.size();
+  return PX_OK;
+}
+
+px_status px_residual_norm_async(px_ctx* c, const px_grid* g, const void* phi,
+                                 const void* rho, double* out_dev, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (!out_dev) return fail(c, PX_EINVAL, "out_dev is NULL");
+  if ((f.nx && f.ny) && (!phi || !rho)) return fail(c, PX_EINVAL, "NULL field pointer");
+  DeviceScope ds(c->device);
+  cudaError_t e = px::launch_residual_norm(f, phi, rho, out_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "residual_norm launch");
+}
+
+px_status px_residual_norm(px_ctx* c, const px_grid* g, const void* phi, const void* rho,
+                           double* out_host, double* rho_norm_host, void* stream) {
+  if (!c) return PX_EINVAL;
+  if (!out_host) return fail(c, PX_EINVAL, "out_host is NULL");
+  px_status s = px_residual_norm_async(c, g, phi, rho, c->red, stream);
+  if (s != PX_OK) return s;
+  DeviceScope ds(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(c->red_host, c->red, 2 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "residual_norm sync");
+  *out_host = c->red_host[0];
+  if (rho_norm_host) *rho_norm_host = c->red_host[1];
+  return PX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace px {
+
+constexpr int kWarp = 32;
+
+// Periodic index for i in [-n, 2n).
+__device__ __forceinline__ int wrap1(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+// Periodic index for any i.
+__device__ __forceinline__ int wrapn(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+// Non-negative floats / doubles (and +NaN) order like their bit patterns read
+// as unsigned integers, so a max-norm reduces with integer max.
+__device__ __forceinline__ uint32_t absbits(float v) { return __float_as_uint(fabsf(v)); }
+__device__ __forceinline__ uint64_t absbits(double v) {
+  return (uint64_t)__double_as_longlong(fabs(v));
+}
+__device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
+__device__ __forceinline__ uint64_t umax(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ uint32_t warp_max(uint32_t v) {
+  return __reduce_max_sync(0xffffffffu, v);
+}
+__device__ __forceinline__ uint64_t warp_max(uint64_t v) {
+  uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+  uint32_t mhi = __reduce_max_sync(0xffffffffu, hi);
+  uint32_t mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
+// Widen a max-bits value of the storage type to the bits of the equal double.
+__device__ __forceinline__ uint64_t to_f64_bits(uint32_t b) {
+  return (uint64_t)__double_as_longlong((double)__uint_as_float(b));
+}
+__device__ __forceinline__ uint64_t to_f64_bits(uint64_t b) { return b; }
+
+__device__ __forceinline__ void atomic_max_bits(double* slot, uint64_t bits) {
+  atomicMax(reinterpret_cast<unsigned long long*>(slot), (unsigned long long)bits);
+}
+
+template <typename T> struct MaxBits;
+template <> struct MaxBits<float> { using type = uint32_t; };
+template <> struct MaxBits<double> { using type = uint64_t; };
+
+// Coefficients of one sweep in the storage type:
+//   s = (W + E) + (S + N) - 4 C;  r = s / h^2 - rho;  C' = C + c r,  c = omega h^2 / 4.
+template <typename T> struct Coef {
+  T c;    // omega h^2 / 4
+  T ih2;  // 1 / h^2
+};
+
+// One launch's residual-report window: state index s0 + t is reported into
+// resid[(s0 + t) / every] when every > 0 and (s0 + t) % every == 0.
+struct Reports {
+  double* resid;
+  int s0;
+  int every;
+  __host__ __device__ __forceinline__ bool due(int t) const {
+    return resid != nullptr && ((s0 + t) % every) == 0;
+  }
+  __host__ __device__ __forceinline__ double* slot(int t) const { return resid + (s0 + t) / every; }
+};
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (relax.cu, stencil.cu). All return the cudaError_t of
+// the launch; arguments were validated by the API layer.
+struct FieldDesc {
+  int nx, ny;
+  int64_t ld;
+  int64_t off;   // element offset of interior cell (0, 0)
+  int ghost;
+  int dtype;     // 0 = f64, 1 = f32
+  double h;
+};
+
+// Whether the vectorised kernels may run on this layout / these pointers.
+bool vector_ok(const FieldDesc& f, const void* a, const void* b, const void* c);
+
+// One launch of `tb` fused sweeps (tb in 1..8) reading src, writing dst.
+cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst,
+                         const void* rho, double omega, int tb, bool vec,
+                         double* resid, int s0, int every, cudaStream_t st);
+
+cudaError_t launch_apply_stencil(const FieldDesc& f, const void* phi, void* out,
+                                 cudaStream_t st);
+// out2[0] = max|rho - L phi| (FP64), out2[1] = max|rho|; out2 zero-filled here.
+cudaError_t launch_residual_norm(const FieldDesc& f, const void* phi, const void* rho,
+                                 double* out2, cudaStream_t st);
+// Copy the interior (and, for ghost layout, refill ghosts) of src into dst.
+cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
+                              cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace px

@@ -1,0 +1,406 @@
+// Fused relaxation sweeps for sm_103a: periodic ghost fill folded into the
+// loads, 5-point Laplacian, weighted Jacobi update and the max-norm of the
+// input-state residual in one pass (ProtoX Sec. IV, the Sigma-OL merged loop of
+// the OL rules Laplace, Jacobi = (1, w, -lambda) x I and
+// ||.||_inf = Max o pw|x| o (0, 1/a^2, -1) x I).
+//
+// Per cell, in the storage type T (FP64 or FP32):
+//   s  = (W + E) + (S + N) - 4 C        (unscaled taps, one rounding for the -4C)
+//   r  = s / h^2 - rho                  (residual of the input state, fused FMA)
+//   C' = C + (omega h^2 / 4) r          (weighted Jacobi, Eq. "jacobi")
+// which is the paper's C + w s - lambda rho with w = omega/4, lambda = omega h^2/4.
+// On B300 one FP64 FMA issues at 1/64 of the FP32 rate, so the FP64 sweep is
+// held to 6 FP64 operations per cell (3 adds, 3 FMAs); |r| and the running max
+// run on the integer pipe as bit patterns.
+//
+// Two kernels:
+//  * relax1_stream: one sweep per launch. A warp owns an x-strip of 32*V cells
+//    (V = 16 bytes / element) and marches down a segment of rows keeping rows
+//    j-1, j, j+1 in registers with loads issued two rows ahead; x neighbours
+//    come from warp shuffles, the strip edges from two scalar loads. DRAM
+//    traffic is the algorithmic 2 reads + 1 write per cell. V = 1 is the
+//    general path (any pitch, alignment, ghost layout, tiny grids).
+//  * relaxT_tile: TB sweeps per launch (temporal blocking). A CTA stages a
+//    (TY + 2 TB) x (TX + 2 HX) tile of phi and rho in shared memory with
+//    cp.async (periodic wrap applied to the global coordinates), runs TB
+//    Jacobi sweeps between two shared buffers, each sweep valid on a region
+//    one cell smaller per side, and stores only its TX x TY interior, so DRAM
+//    sees one read of phi and rho and one write per TB sweeps.
+#include "px_internal.cuh"
+
+#include <algorithm>
+
+namespace px {
+
+namespace {
+
+template <typename T, int V> struct VecOf;
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<double, 2> { using type = double2; };
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<double, 1> { using type = double; };
+
+template <typename T, int V>
+__device__ __forceinline__ void ldv(T (&v)[V], const T* p) {
+  using VT = typename VecOf<T, V>::type;
+  VT t = *reinterpret_cast<const VT*>(p);
+  static_assert(sizeof(VT) == sizeof(T) * V, "vector size");
+  *reinterpret_cast<VT*>(v) = t;
+}
+template <typename T, int V>
+__device__ __forceinline__ void ldv_stream(T (&v)[V], const T* p) {
+  using VT = typename VecOf<T, V>::type;
+  VT t = __ldcs(reinterpret_cast<const VT*>(p));
+  *reinterpret_cast<VT*>(v) = t;
+}
+template <typename T, int V>
+__device__ __forceinline__ void stv(T* p, const T (&v)[V]) {
+  using VT = typename VecOf<T, V>::type;
+  *reinterpret_cast<VT*>(p) = *reinterpret_cast<const VT*>(v);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Store v at interior cell (x, j) and, for the ghosted layout, at every ghost
+// cell that is a periodic image of it (rows -1 / ny, columns -1 / nx).
+template <typename T>
+__device__ __forceinline__ void store_images(T* O, int x, int j, int nx, int ny,
+                                             int64_t ld, T v) {
+  int xs[3] = {x, 0, 0}, ys[3] = {j, 0, 0};
+  int nxs = 1, nys = 1;
+  if (x == 0) xs[nxs++] = nx;
+  if (x == nx - 1) xs[nxs++] = -1;
+  if (j == 0) ys[nys++] = ny;
+  if (j == ny - 1) ys[nys++] = -1;
+  for (int a = 0; a < nys; ++a)
+    for (int b = 0; b < nxs; ++b)
+      if (a | b) O[(int64_t)ys[a] * ld + xs[b]] = v;
+}
+
+// One ring entry of the streaming kernel: the thread's V cells of a row plus
+// the strip-edge neighbours (left: lane 0, right: the strip's last valid lane).
+template <typename T, int V> struct RowReg {
+  T v[V];
+  T el, er;
+};
+
+template <typename T, int V, bool kRep>
+__global__ void __launch_bounds__(256)
+relax1_stream(const T* __restrict__ phi, T* __restrict__ out, const T* __restrict__ rho,
+              int nx, int ny, int64_t ld, int ghost, int ry, int nstrips, int nseg,
+              Coef<T> k, double* __restrict__ slot) {
+  using MB = typename MaxBits<T>::type;
+  constexpr int SW = kWarp * V;
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int ntasks = nstrips * nseg;
+  MB mx = 0;
+
+  for (int task = gw; task < ntasks; task += nw) {
+    const int strip = task % nstrips, seg = task / nstrips;
+    const int xs = strip * SW;
+    const int x = xs + lane * V;
+    const bool valid = x < nx;
+    const int xc = valid ? x : xs;  // in-bounds address for idle lanes
+    const int xend = min(xs + SW, nx);
+    const bool need_l = lane == 0;
+    const bool need_r = valid && (x + V >= xend);
+    const int xl = wrap1(xs - 1, nx);
+    const int xr = wrap1(x + V, nx);
+    const int j0 = seg * ry, j1 = min(j0 + ry, ny);
+
+    auto load_row = [&](int j, RowReg<T, V>& rr) {
+      const T* rp = phi + (int64_t)wrap1(j, ny) * ld;
+      ldv<T, V>(rr.v, rp + xc);
+      if (need_l) rr.el = rp[xl];
+      if (need_r) rr.er = rp[xr];
+    };
+    RowReg<T, V> up, cur, dn, pf;
+    T rh0[V], rh1[V];
+    load_row(j0 - 1, up);
+    load_row(j0, cur);
+    load_row(j0 + 1, dn);  // j0 + 1 <= j1 always (segments are non-empty)
+    if (j0 + 2 <= j1) load_row(j0 + 2, pf);
+    ldv_stream<T, V>(rh0, rho + (int64_t)j0 * ld + xc);
+    if (j0 + 1 < j1) ldv_stream<T, V>(rh1, rho + (int64_t)(j0 + 1) * ld + xc);
+
+    for (int j = j0; j < j1; ++j) {
+      RowReg<T, V> nxt;
+      T rh2[V];
+      if (j + 3 <= j1) load_row(j + 3, nxt);
+      if (j + 2 < j1) ldv_stream<T, V>(rh2, rho + (int64_t)(j + 2) * ld + xc);
+
+      T left0 = __shfl_up_sync(0xffffffffu, cur.v[V - 1], 1);
+      T rightV = __shfl_down_sync(0xffffffffu, cur.v[0], 1);
+      if (need_l) left0 = cur.el;
+      if (need_r) rightV = cur.er;
+      T o[V];
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const T w = (i == 0) ? left0 : cur.v[i - 1];
+        const T e = (i == V - 1) ? rightV : cur.v[i + 1];
+        const T q = (w + e) + (up.v[i] + dn.v[i]);
+        const T s = fma((T)-4, cur.v[i], q);
+        const T r = fma(s, k.ih2, -rh0[i]);
+        o[i] = fma(k.c, r, cur.v[i]);
+        if (kRep && valid) mx = umax(mx, absbits(r));
+      }
+      if (valid) {
+        T* op = out + (int64_t)j * ld + x;
+        if constexpr (V == 1) {
+          op[0] = o[0];
+          if (ghost) store_images<T>(out, x, j, nx, ny, ld, o[0]);
+        } else {
+          stv<T, V>(op, o);
+        }
+      }
+      up = cur;
+      cur = dn;
+      dn = pf;
+      pf = nxt;
+#pragma unroll
+      for (int i = 0; i < V; ++i) { rh0[i] = rh1[i]; rh1[i] = rh2[i]; }
+    }
+  }
+
+  if constexpr (kRep) {
+    __shared__ MB wmax[8];
+    mx = warp_max(mx);
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      MB m = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = umax(m, wmax[w]);
+      atomic_max_bits(slot, to_f64_bits(m));
+    }
+  }
+}
+
+constexpr int kTileRows = 72;  // shared-memory tile height R = TY + 2 TB
+constexpr int kTileThreads = 256;
+
+template <typename T, int TB>
+struct TileGeom {
+  static constexpr int V = 16 / (int)sizeof(T);
+  static constexpr int PX = kWarp * V;                   // tile width in cells
+  static constexpr int HX = ((TB + V - 1) / V) * V;      // x halo, multiple of V
+  static constexpr int TX = PX - 2 * HX;                 // owned width
+  static constexpr int R = kTileRows;
+  static constexpr int TY = R - 2 * TB;                  // owned height
+  static constexpr size_t smem = sizeof(T) * (size_t)PX * (2 * R + (R - 2));
+};
+
+template <typename T, int TB>
+__global__ void __launch_bounds__(kTileThreads, 2)
+relaxT_tile(const T* __restrict__ phi, T* __restrict__ out, const T* __restrict__ rho,
+            int nx, int ny, int64_t ld, int tiles_x, Coef<T> k, Reports rep) {
+  using G = TileGeom<T, TB>;
+  using MB = typename MaxBits<T>::type;
+  constexpr int V = G::V, PX = G::PX, HX = G::HX, TX = G::TX, R = G::R, TY = G::TY;
+  constexpr int NW = kTileThreads / kWarp;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* B = A + R * PX;
+  T* RH = B + R * PX;  // row r (1..R-2) at RH + (r - 1) * PX
+  __shared__ MB sres[TB][NW];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int gx0 = tx * TX - HX, gy0 = ty * TY - TB;
+
+  if (tid < TB * NW) (&sres[0][0])[tid] = 0;
+
+  {
+    const int gx = wrapn(gx0 + lane * V, nx);
+    for (int r = warp; r < R; r += NW) {
+      const int64_t row = (int64_t)wrapn(gy0 + r, ny) * ld + gx;
+      cp_async16(A + r * PX + lane * V, phi + row);
+      if (r >= 1 && r <= R - 2) cp_async16(RH + (r - 1) * PX + lane * V, rho + row);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+
+  // Rows 1..R-2 split over the warps.
+  const int rb = 1 + ((R - 2) * warp) / NW, re = 1 + ((R - 2) * (warp + 1)) / NW;
+  const int cx = lane * V;                       // first tile column of this lane
+  const bool own_x = cx >= HX && cx < HX + TX && (tx * TX + cx - HX) < nx;
+  const int gxo = tx * TX + cx - HX;
+
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    const T* S = (t & 1) ? B : A;
+    T* D = (t & 1) ? A : B;
+    const bool last = t == TB - 1;
+    const bool rep_t = rep.due(t);
+    int r0 = max(rb, t + 1), r1 = min(re, R - 1 - t);
+    if (last) { r0 = max(r0, TB); r1 = min(r1, TB + TY); }
+    MB mx = 0;
+    if (r0 < r1) {
+      T up[V], cur[V];
+      ldv<T, V>(up, S + (r0 - 1) * PX + cx);
+      ldv<T, V>(cur, S + r0 * PX + cx);
+      for (int r = r0; r < r1; ++r) {
+        T dn[V], rh[V], o[V];
+        ldv<T, V>(dn, S + (r + 1) * PX + cx);
+        ldv<T, V>(rh, RH + (r - 1) * PX + cx);
+        const T left0 = __shfl_up_sync(0xffffffffu, cur[V - 1], 1);
+        const T rightV = __shfl_down_sync(0xffffffffu, cur[0], 1);
+        const int gy = ty * TY + r - TB;
+        const bool own = own_x && r >= TB && r < TB + TY && gy < ny;
+#pragma unroll
+        for (int i = 0; i < V; ++i) {
+          const T w = (i == 0) ? left0 : cur[i - 1];
+          const T e = (i == V - 1) ? rightV : cur[i + 1];
+          const T q = (w + e) + (up[i] + dn[i]);
+          const T s = fma((T)-4, cur[i], q);
+          const T rr = fma(s, k.ih2, -rh[i]);
+          o[i] = fma(k.c, rr, cur[i]);
+          if (rep_t && own) mx = umax(mx, absbits(rr));
+        }
+        if (!last) {
+          stv<T, V>(D + r * PX + cx, o);
+        } else if (own) {
+          stv<T, V>(out + (int64_t)gy * ld + gxo, o);
+        }
+#pragma unroll
+        for (int i = 0; i < V; ++i) { up[i] = cur[i]; cur[i] = dn[i]; }
+      }
+    }
+    if (rep_t) {
+      mx = warp_max(mx);
+      if (lane == 0) sres[t][warp] = mx;
+    }
+    __syncthreads();
+  }
+
+  if (tid < TB && rep.due(tid)) {
+    MB m = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) m = umax(m, sres[tid][w]);
+    atomic_max_bits(rep.slot(tid), to_f64_bits(m));
+  }
+}
+
+int g_sms[64];
+
+template <typename T, int V, bool kRep>
+cudaError_t launch_stream_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
+                            Coef<T> k, double* slot, cudaStream_t st) {
+  constexpr int SW = kWarp * V;
+  const int ry = 32;
+  const int nstrips = (f.nx + SW - 1) / SW;
+  const int nseg = (f.ny + ry - 1) / ry;
+  const int64_t ntasks = (int64_t)nstrips * nseg;
+  static int blocks_per_sm = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &blocks_per_sm, relax1_stream<T, V, kRep>, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int64_t resident = (int64_t)blocks_per_sm * device_sm_count();
+  const int64_t want = (ntasks + 7) / 8;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, resident));
+  relax1_stream<T, V, kRep><<<blocks, 256, 0, st>>>(
+      src + f.off, dst + f.off, rho + f.off, f.nx, f.ny, f.ld, f.ghost, ry, nstrips,
+      nseg, k, slot);
+  return cudaGetLastError();
+}
+
+template <typename T, int TB>
+cudaError_t launch_tile_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
+                          Coef<T> k, Reports rep, cudaStream_t st) {
+  using G = TileGeom<T, TB>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(relaxT_tile<T, TB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int tiles_x = (f.nx + G::TX - 1) / G::TX;
+  const int tiles_y = (f.ny + G::TY - 1) / G::TY;
+  const int64_t blocks = (int64_t)tiles_x * tiles_y;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  relaxT_tile<T, TB><<<(unsigned)blocks, kTileThreads, G::smem, st>>>(
+      src, dst, rho, f.nx, f.ny, f.ld, tiles_x, k, rep);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
+                           double omega, int tb, bool vec, Reports rep, cudaStream_t st) {
+  Coef<T> k;
+  k.c = (T)(omega * f.h * f.h / 4.0);
+  k.ih2 = (T)(1.0 / (f.h * f.h));
+  if (tb == 1) {
+    const bool r = rep.due(0);
+    double* slot = r ? rep.slot(0) : nullptr;
+    constexpr int VV = 16 / (int)sizeof(T);
+    if (vec) {
+      return r ? launch_stream_t<T, VV, true>(f, src, dst, rho, k, slot, st)
+               : launch_stream_t<T, VV, false>(f, src, dst, rho, k, slot, st);
+    }
+    return r ? launch_stream_t<T, 1, true>(f, src, dst, rho, k, slot, st)
+             : launch_stream_t<T, 1, false>(f, src, dst, rho, k, slot, st);
+  }
+  switch (tb) {
+    case 2: return launch_tile_t<T, 2>(f, src, dst, rho, k, rep, st);
+    case 3: return launch_tile_t<T, 3>(f, src, dst, rho, k, rep, st);
+    case 4: return launch_tile_t<T, 4>(f, src, dst, rho, k, rep, st);
+    case 5: return launch_tile_t<T, 5>(f, src, dst, rho, k, rep, st);
+    case 6: return launch_tile_t<T, 6>(f, src, dst, rho, k, rep, st);
+    case 7: return launch_tile_t<T, 7>(f, src, dst, rho, k, rep, st);
+    case 8: return launch_tile_t<T, 8>(f, src, dst, rho, k, rep, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+int device_sm_count() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 148;
+  if (g_sms[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = n > 0 ? n : 148;
+  }
+  return g_sms[dev];
+}
+
+bool vector_ok(const FieldDesc& f, const void* a, const void* b, const void* c) {
+  if (f.ghost) return false;
+  const int V = f.dtype == 0 ? 2 : 4;
+  if (f.nx % V != 0 || f.ld % V != 0) return false;
+  auto al = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  return al(a) && al(b) && al(c);
+}
+
+cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst, const void* rho,
+                         double omega, int tb, bool vec, double* resid, int s0,
+                         int every, cudaStream_t st) {
+  Reports rep;
+  rep.resid = (resid && every > 0) ? resid : nullptr;
+  rep.s0 = s0;
+  rep.every = every > 0 ? every : 1;
+  if (!vec) tb = 1;
+  if (f.dtype == 0)
+    return launch_relax_t<double>(f, (const double*)src, (double*)dst, (const double*)rho,
+                                  omega, tb, vec, rep, st);
+  return launch_relax_t<float>(f, (const float*)src, (float*)dst, (const float*)rho, omega,
+                               tb, vec, rep, st);
+}
+
+}  // namespace px

@@ -1,0 +1,153 @@
+// Laplacian application, FP64 residual max-norm and periodic field copy.
+//
+// These run once per solve check rather than once per sweep, so they use one
+// thread per cell with a grid-stride loop on any layout (ghosted or not, any
+// pitch). The residual norm evaluates in FP64 with the taps summed as
+// ((W + E) + (S + N)) - 4 C and r = (s * (1/h^2)) - rho without contraction,
+// which reproduces the plain evaluation of the max-norm check of Sec. IV
+// (OL rule ||.||_inf with a = h) exactly for FP64 fields.
+#include "px_internal.cuh"
+
+#include <algorithm>
+
+namespace px {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void store_all_images(T* O, int x, int j, int nx, int ny,
+                                                 int64_t ld, int ghost, T v) {
+  O[(int64_t)j * ld + x] = v;
+  if (!ghost) return;
+  int xs[3] = {x, 0, 0}, ys[3] = {j, 0, 0};
+  int nxs = 1, nys = 1;
+  if (x == 0) xs[nxs++] = nx;
+  if (x == nx - 1) xs[nxs++] = -1;
+  if (j == 0) ys[nys++] = ny;
+  if (j == ny - 1) ys[nys++] = -1;
+  for (int a = 0; a < nys; ++a)
+    for (int b = 0; b < nxs; ++b)
+      if (a | b) O[(int64_t)ys[a] * ld + xs[b]] = v;
+}
+
+template <typename T>
+__global__ void apply_stencil_k(const T* __restrict__ phi, T* __restrict__ out, int nx,
+                                int ny, int64_t ld, int ghost, T ih2) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
+    const T* row = phi + (int64_t)j * ld;
+    const T C = row[i];
+    const T W = row[wrap1(i - 1, nx)], E = row[wrap1(i + 1, nx)];
+    const T S = phi[(int64_t)wrap1(j - 1, ny) * ld + i];
+    const T N = phi[(int64_t)wrap1(j + 1, ny) * ld + i];
+    const T s = fma((T)-4, C, (W + E) + (S + N));
+    store_all_images<T>(out, i, j, nx, ny, ld, ghost, s * ih2);
+  }
+}
+
+template <typename T>
+__global__ void residual_norm_k(const T* __restrict__ phi, const T* __restrict__ rho, int nx,
+                                int ny, int64_t ld, double ih2, double* __restrict__ out2) {
+  const int64_t n = (int64_t)nx * ny;
+  uint64_t mr = 0, mp = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
+    const T* row = phi + (int64_t)j * ld;
+    const double C = (double)row[i];
+    const double W = (double)row[wrap1(i - 1, nx)], E = (double)row[wrap1(i + 1, nx)];
+    const double S = (double)phi[(int64_t)wrap1(j - 1, ny) * ld + i];
+    const double N = (double)phi[(int64_t)wrap1(j + 1, ny) * ld + i];
+    const double s = __dsub_rn(__dadd_rn(__dadd_rn(W, E), __dadd_rn(S, N)), __dmul_rn(4.0, C));
+    const double rv = (double)rho[(int64_t)j * ld + i];
+    const double r = __dsub_rn(__dmul_rn(ih2, s), rv);
+    mr = umax(mr, absbits(r));
+    mp = umax(mp, absbits(rv));
+  }
+  __shared__ uint64_t sm[2][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mr = warp_max(mr);
+  mp = warp_max(mp);
+  if (lane == 0) { sm[0][warp] = mr; sm[1][warp] = mp; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a = umax(a, sm[0][w]); b = umax(b, sm[1][w]); }
+    atomic_max_bits(out2, a);
+    atomic_max_bits(out2 + 1, b);
+  }
+}
+
+template <typename T>
+__global__ void copy_field_k(const T* __restrict__ src, T* __restrict__ dst, int nx, int ny,
+                             int64_t ld, int ghost) {
+  // Writes every cell of the layout: interior, plus ghosts (periodic images)
+  // when ghost = 1. Reads only interior cells of src.
+  const int wx = nx + 2 * ghost, wy = ny + 2 * ghost;
+  const int64_t n = (int64_t)wx * wy;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / wx) - ghost, i = (int)(c - (int64_t)(c / wx) * wx) - ghost;
+    dst[(int64_t)j * ld + i] = src[(int64_t)wrap1(j, ny) * ld + wrap1(i, nx)];
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  const int64_t cap = (int64_t)device_sm_count() * 8;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+cudaError_t launch_apply_stencil(const FieldDesc& f, const void* phi, void* out,
+                                 cudaStream_t st) {
+  const int64_t n = (int64_t)f.nx * f.ny;
+  const int blocks = grid_for(n, 256);
+  const double ih2 = 1.0 / (f.h * f.h);
+  if (f.dtype == 0)
+    apply_stencil_k<double><<<blocks, 256, 0, st>>>((const double*)phi + f.off,
+                                                    (double*)out + f.off, f.nx, f.ny, f.ld,
+                                                    f.ghost, ih2);
+  else
+    apply_stencil_k<float><<<blocks, 256, 0, st>>>((const float*)phi + f.off,
+                                                   (float*)out + f.off, f.nx, f.ny, f.ld,
+                                                   f.ghost, (float)ih2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norm(const FieldDesc& f, const void* phi, const void* rho,
+                                 double* out2, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)f.nx * f.ny;
+  if (n == 0) return cudaSuccess;
+  const int blocks = grid_for(n, 256);
+  const double ih2 = 1.0 / (f.h * f.h);
+  if (f.dtype == 0)
+    residual_norm_k<double><<<blocks, 256, 0, st>>>((const double*)phi + f.off,
+                                                    (const double*)rho + f.off, f.nx, f.ny,
+                                                    f.ld, ih2, out2);
+  else
+    residual_norm_k<float><<<blocks, 256, 0, st>>>((const float*)phi + f.off,
+                                                   (const float*)rho + f.off, f.nx, f.ny,
+                                                   f.ld, ih2, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
+                              cudaStream_t st) {
+  const int64_t n = (int64_t)(f.nx + 2 * f.ghost) * (f.ny + 2 * f.ghost);
+  const int blocks = grid_for(n, 256);
+  if (f.dtype == 0)
+    copy_field_k<double><<<blocks, 256, 0, st>>>((const double*)src + f.off,
+                                                 (double*)dst + f.off, f.nx, f.ny, f.ld,
+                                                 f.ghost);
+  else
+    copy_field_k<float><<<blocks, 256, 0, st>>>((const float*)src + f.off, (float*)dst + f.off,
+                                                f.nx, f.ny, f.ld, f.ghost);
+  return cudaGetLastError();
+}
+
+}  // namespace px
