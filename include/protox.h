@@ -84,7 +84,8 @@ px_status px_create(px_ctx** out, int device);
 px_status px_destroy(px_ctx* ctx);
 
 /* Message of the last failed call on ctx ("" if none). Valid until the next
- * call on ctx. ctx may be NULL (then a message of the last px_create). */
+ * call on ctx. ctx may be NULL (then the message of the calling thread's last
+ * failed px_create or px_relax_n_static). */
 const char* px_last_error(const px_ctx* ctx);
 
 /* Static name of a status code. */
@@ -123,6 +124,36 @@ px_status px_relax_n(px_ctx* ctx, const px_grid* g, const void* phi_in,
                      void* phi_out, const void* rho, double omega, int nsweeps,
                      int tblock, double* resid_dev, int report_every,
                      void* stream);
+
+/* px_relax_n for callers that cannot allocate device memory. The paper has
+ * no counterpart: this is a deployment variant of the same fused sweeps.
+ *
+ * Some callers may not call cudaMalloc at all: code inside a host callback
+ * or a latency-bound loop that must never block on the allocator, an
+ * application whose own memory pool owns the device, or a plug-in that may
+ * not create library contexts (px_create allocates). This call needs no
+ * px_ctx and allocates nothing. The caller still passes phi_in, phi_out, rho
+ * and resid_dev, with exactly the meaning, layout and results of px_relax_n
+ * (same kernels, same launch plan). The one working buffer of a multi-launch
+ * relax, the ping-pong field, is a fixed 16 MiB device array inside the
+ * library: every GPU that loads the library holds it until the process
+ * exits.
+ *
+ *  - Limit: the field's span, ((rows - 1) * ld + width) * element size, must
+ *    be at most 16 MiB (e.g. 2048 x 2048 FP32, 1448 x 1448 FP64); larger
+ *    fields are rejected with PX_EINVAL before anything is launched.
+ *  - Runs on the CURRENT CUDA device. The first call on each device looks
+ *    up the array's device address (cudaGetSymbolAddress) and caches it;
+ *    make that first call before any stream capture.
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (nothing in it needs to start at zero; resid_dev is zero-filled by the
+ *    call as in px_relax_n). Calls whose work overlaps on the GPU (other
+ *    streams, other host threads) race on it: serialise them.
+ *  - Errors return a px_status; the message is px_last_error(NULL) on the
+ *    calling thread. */
+px_status px_relax_n_static(const px_grid* g, const void* phi_in, void* phi_out,
+                            const void* rho, double omega, int nsweeps, int tblock,
+                            double* resid_dev, int report_every, void* stream);
 
 /* The launch plan px_relax_n would use for these arguments, without running
  * it: *tblock_used = sweeps fused per launch (after auto choice and layout

@@ -66,8 +66,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_residual_norm_async.argtypes = [_vp, gp, _vp, _vp, _vp, _vp]
     ip = ctypes.POINTER(ctypes.c_int)
     lib.px_relax_plan.argtypes = [_vp, gp, _vp, _vp, _vp, i, i, ip, ip]
+    lib.px_relax_n_static.argtypes = [gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
-                 "px_residual_norm", "px_residual_norm_async", "px_relax_plan"):
+                 "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
+                 "px_relax_n_static"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -185,6 +187,24 @@ def relax_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, tblock: 
                                         _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
                                         int(tblock), _ptr(resid), int(report_every),
                                         _stream(stream)))
+    return phi_out
+
+
+def relax_n_static(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int,
+                   tblock: int = 0, resid=None, report_every: int = 0, ghost: int = 0,
+                   stream=None):
+    """px_relax_n_static: relax_n for callers that cannot allocate device memory
+    (no context; the ping-pong field comes from a fixed 16 MiB array in the
+    library). Runs on the current device; fields up to 16 MiB."""
+    _same_layout(phi_in, phi_out)
+    _same_layout(phi_in, rho)
+    g = grid_of(phi_in, h, ghost)
+    lib = load_library()
+    st = lib.px_relax_n_static(ctypes.byref(g), _ptr(phi_in), _ptr(phi_out), _ptr(rho),
+                               float(omega), int(nsweeps), int(tblock), _ptr(resid),
+                               int(report_every), _stream(stream))
+    if st != PX_OK:
+        raise PxError(st, lib.px_last_error(None).decode())
     return phi_out
 
 

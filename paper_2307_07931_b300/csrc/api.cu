@@ -146,6 +146,19 @@ std::vector<int> plan_launches(const px::FieldDesc& f, bool vec, bool inplace, i
 
 }  // namespace
 
+// Helpers shared with the context-free entry point in relax_static.cu. They
+// report failures through the thread's context-free message (px_last_error(NULL)).
+namespace px {
+px_status unbound_check_grid(const px_grid* g, FieldDesc* f) { return check_grid(nullptr, g, f); }
+px_status unbound_fail(px_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
+size_t field_bytes(const FieldDesc& f) { return field_span(f); }
+bool ranges_overlap(const void* a, const void* b, size_t n) { return overlap(a, b, n); }
+std::vector<int> plan_relax_launches(const FieldDesc& f, bool vec, bool inplace, int nsweeps,
+                                     int tblock, bool* copy_first) {
+  return plan_launches(f, vec, inplace, nsweeps, tblock, copy_first);
+}
+}  // namespace px
+
 extern "C" {
 
 const char* px_status_string(px_status s) {

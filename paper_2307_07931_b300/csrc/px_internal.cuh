@@ -102,3 +102,19 @@ cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
 int device_sm_count();
 
 }  // namespace px
+
+#include <vector>
+#include "../../include/protox.h"
+
+namespace px {
+
+// Validation and planning of api.cu, for entry points without a context;
+// failures set the message returned by px_last_error(NULL).
+px_status unbound_check_grid(const px_grid* g, FieldDesc* f);
+px_status unbound_fail(px_status s, const char* msg);
+size_t field_bytes(const FieldDesc& f);
+bool ranges_overlap(const void* a, const void* b, size_t n);
+std::vector<int> plan_relax_launches(const FieldDesc& f, bool vec, bool inplace, int nsweeps,
+                                     int tblock, bool* copy_first);
+
+}  // namespace px
