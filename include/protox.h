@@ -163,6 +163,51 @@ px_status px_relax_plan(px_ctx* ctx, const px_grid* g, const void* phi_in,
                         const void* phi_out, const void* rho, int nsweeps,
                         int tblock, int* tblock_used, int* launches);
 
+/* ----------------------------------------------------------------------------
+ * Solve to a tolerance (Sec. IV: relax, then check the max-norm against the
+ * convergence criterion, repeated). Two modes:
+ *  PX_SOLVE_PLAIN   sweeps in the grid's dtype (FP64 or FP32 storage), an FP64
+ *                   residual check every check_every sweeps.
+ *  PX_SOLVE_REFINE  FP64 phi and rho; an FP64 outer loop of iterative
+ *                   refinement around FP32-storage sweeps: r = rho - L phi in
+ *                   FP64, scaled by an exact power of two and stored as FP32;
+ *                   inner_sweeps FP32 sweeps solve L e = r from e = 0; then
+ *                   phi += e in FP64. The residual, the correction and the
+ *                   final norm are the only FP64 steps.
+ * Convergence: ||rho - L phi||_inf <= rtol * ||rho||_inf, evaluated in FP64 on
+ * the current state (px_residual_norm), one host synchronisation per check.
+ */
+typedef enum { PX_SOLVE_PLAIN = 0, PX_SOLVE_REFINE = 1 } px_solve_mode;
+
+typedef struct {
+  int32_t mode;          /* px_solve_mode */
+  int32_t tblock;        /* sweeps per launch of the sweeps, 0 = automatic */
+  double omega;          /* Jacobi weight, finite */
+  double rtol;           /* relative max-norm target, >= 0 */
+  int64_t max_sweeps;    /* sweep budget (inner sweeps count), >= 0 */
+  int32_t check_every;   /* PLAIN: sweeps between checks, > 0 */
+  int32_t inner_sweeps;  /* REFINE: FP32 sweeps per outer cycle, > 0 */
+  int64_t timeout_ms;    /* host wall-clock limit checked at each check, 0 = none */
+  int32_t check_mean;    /* nonzero: PX_EMEAN if |mean rho| > 1e-12 ||rho||_inf */
+  int32_t reserved;      /* must be 0 */
+} px_solve_opts;
+
+typedef struct {
+  int64_t sweeps;        /* sweeps performed (inner sweeps in REFINE) */
+  int64_t cycles;        /* REFINE outer cycles (0 in PLAIN) */
+  int64_t checks;        /* FP64 residual evaluations */
+  double rel_resid;      /* ||rho - L phi||_inf / ||rho||_inf of the returned phi */
+  double wall_ms;        /* host wall time of the call */
+} px_solve_info;
+
+/* Solve L phi = rho in place from the phi given (the initial guess). Returns
+ * PX_OK when converged, PX_ENOCONV when max_sweeps ran out, PX_ETIMEOUT past
+ * timeout_ms, PX_ENAN for a NaN/Inf residual, PX_EMEAN (check_mean), PX_EINVAL
+ * for bad options (REFINE needs PX_F64). info may be NULL; it is filled on
+ * every return after validation. Synchronises the stream at each check. */
+px_status px_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho,
+                   const px_solve_opts* opts, px_solve_info* info, void* stream);
+
 /* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
  * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,
  * *rho_norm_host = ||rho||_inf. Evaluated in FP64 for both dtypes (FP32 fields

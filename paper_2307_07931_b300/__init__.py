@@ -31,6 +31,22 @@ class PxError(RuntimeError):
         self.status = status
 
 
+PX_SOLVE_PLAIN, PX_SOLVE_REFINE = 0, 1
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("tblock", ctypes.c_int32), ("omega", ctypes.c_double),
+                ("rtol", ctypes.c_double), ("max_sweeps", ctypes.c_int64),
+                ("check_every", ctypes.c_int32), ("inner_sweeps", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int64), ("check_mean", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int64), ("cycles", ctypes.c_int64), ("checks", ctypes.c_int64),
+                ("rel_resid", ctypes.c_double), ("wall_ms", ctypes.c_double)]
+
+
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ld", ctypes.c_int64),
                 ("ghost", ctypes.c_int32), ("dtype", ctypes.c_int32), ("h", ctypes.c_double)]
@@ -67,9 +83,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     ip = ctypes.POINTER(ctypes.c_int)
     lib.px_relax_plan.argtypes = [_vp, gp, _vp, _vp, _vp, i, i, ip, ip]
     lib.px_relax_n_static.argtypes = [gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
+    lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
+                             ctypes.POINTER(SolveInfo), _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
                  "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
-                 "px_relax_n_static"):
+                 "px_relax_n_static", "px_solve"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -242,3 +260,29 @@ def residual_norm_async(phi, rho, out, h: float, ghost: int = 0, ctx: Context | 
     ctx.check(load_library().px_residual_norm_async(ctx.handle, ctypes.byref(g), _ptr(phi),
                                                     _ptr(rho), _ptr(out), _stream(stream)))
     return out
+
+
+def solve(phi, rho, h: float, mode: str = "plain", omega: float = 2.0 / 3.0, rtol: float = 1e-8,
+          max_sweeps: int = 10**7, check_every: int = 1000, inner_sweeps: int = 500,
+          tblock: int = 0, timeout_ms: int = 0, check_mean: bool = False, ghost: int = 0,
+          ctx: Context | None = None, stream=None) -> dict:
+    """px_solve: relax phi in place until ||rho - L phi|| <= rtol ||rho|| (FP64
+    check). mode "plain" sweeps in the tensors' dtype; "refine" runs FP32-storage
+    sweeps inside an FP64 refinement loop (FP64 tensors). Returns the info as a
+    dict; raises PxError (with .info) on any status other than PX_OK."""
+    _same_layout(phi, rho)
+    ctx = ctx or context(phi.device.index)
+    g = grid_of(phi, h, ghost)
+    o = SolveOpts(PX_SOLVE_PLAIN if mode == "plain" else PX_SOLVE_REFINE, int(tblock),
+                  float(omega), float(rtol), int(max_sweeps), int(check_every),
+                  int(inner_sweeps), int(timeout_ms), 1 if check_mean else 0, 0)
+    info = SolveInfo()
+    st = load_library().px_solve(ctx.handle, ctypes.byref(g), _ptr(phi), _ptr(rho),
+                                 ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    d = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+    d["status"] = status_name(st)
+    if st != PX_OK:
+        err = PxError(st, load_library().px_last_error(ctx.handle).decode())
+        err.info = d
+        raise err
+    return d

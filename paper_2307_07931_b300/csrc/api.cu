@@ -5,9 +5,12 @@
 #include "../../include/protox.h"
 #include "px_internal.cuh"
 
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <limits>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -16,8 +19,10 @@ struct px_ctx {
   int device = 0;
   void* scratch = nullptr;   // ping-pong field buffer
   size_t scratch_bytes = 0;
-  double* red = nullptr;     // 2 doubles of device reduction output
-  double* red_host = nullptr;  // pinned mirror of red
+  double* red = nullptr;     // device aux block: [0,1] norms, [2] scale, [3] sum, [8..] partials
+  double* red_host = nullptr;  // pinned mirror of red[0..3]
+  void* ws = nullptr;        // solve workspace: FP32 r and e fields
+  size_t ws_bytes = 0;
   std::string err;
 };
 
@@ -191,8 +196,8 @@ px_status px_create(px_ctx** out, int device) {
   px_ctx* c = new (std::nothrow) px_ctx();
   if (!c) return fail(nullptr, PX_ENOMEM, "host allocation failed");
   c->device = device;
-  e = cudaMalloc(&c->red, 2 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, 2 * sizeof(double));
+  e = cudaMalloc(&c->red, (8 + (size_t)px::sum_partials_count()) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, 4 * sizeof(double));
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->red) cudaFree(c->red);
@@ -208,6 +213,7 @@ px_status px_destroy(px_ctx* c) {
   DeviceScope ds(c->device);
   cudaDeviceSynchronize();
   if (c->scratch) cudaFree(c->scratch);
+  if (c->ws) cudaFree(c->ws);
   if (c->red) cudaFree(c->red);
   if (c->red_host) cudaFreeHost(c->red_host);
   delete c;
@@ -350,3 +356,132 @@ px_status px_residual_norm(px_ctx* c, const px_grid* g, const void* phi, const v
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+namespace {
+
+px_status sync_norms(px_ctx* c, const px::FieldDesc& f, const void* phi, const void* rho,
+                     cudaStream_t st, double* R, double* P) {
+  cudaError_t e = px::launch_residual_norm(f, phi, rho, c->red, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->red_host, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "solve residual check");
+  *R = c->red_host[0];
+  *P = c->red_host[1];
+  return PX_OK;
+}
+
+}  // namespace
+
+extern "C" px_status px_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho,
+                              const px_solve_opts* o, px_solve_info* info, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  const auto t0 = std::chrono::steady_clock::now();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (!o) return fail(c, PX_EINVAL, "opts is NULL");
+  if (o->mode != PX_SOLVE_PLAIN && o->mode != PX_SOLVE_REFINE)
+    return fail(c, PX_EINVAL, "unknown solve mode %d", o->mode);
+  if (o->mode == PX_SOLVE_REFINE && f.dtype != PX_F64)
+    return fail(c, PX_EINVAL, "refinement needs FP64 phi and rho");
+  if (!std::isfinite(o->omega) || !(o->rtol >= 0.0) || o->max_sweeps < 0 ||
+      o->tblock < 0 || o->tblock > 8 || o->timeout_ms < 0 || o->reserved != 0)
+    return fail(c, PX_EINVAL, "bad solve options");
+  if (o->mode == PX_SOLVE_PLAIN && o->check_every <= 0)
+    return fail(c, PX_EINVAL, "check_every must be > 0");
+  if (o->mode == PX_SOLVE_REFINE && o->inner_sweeps <= 0)
+    return fail(c, PX_EINVAL, "inner_sweeps must be > 0");
+  if (f.nx == 0 || f.ny == 0) {
+    if (info) *info = px_solve_info{0, 0, 0, 0.0, 0.0};
+    return PX_OK;
+  }
+  if (!phi || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
+  const size_t span = field_span(f);
+  if (overlap(phi, rho, span)) return fail(c, PX_EINVAL, "phi and rho overlap");
+  DeviceScope ds(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  px_solve_info inf{0, 0, 0, 0.0, 0.0};
+  auto finish = [&](px_status rc) {
+    inf.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                      .count();
+    if (info) *info = inf;
+    return rc;
+  };
+
+  if (o->check_mean) {
+    cudaError_t e = px::launch_field_sum(f, rho, c->red + 8, c->red + 3, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->red_host + 3, c->red + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return finish(cuda_fail(c, e, "mean of rho"));
+    double R = 0, P = 0;
+    s = sync_norms(c, f, phi, rho, st, &R, &P);
+    if (s != PX_OK) return finish(s);
+    const double mean = c->red_host[3] / ((double)f.nx * (double)f.ny);
+    if (!(std::fabs(mean) <= 1e-12 * P))
+      return finish(fail(c, PX_EMEAN, "mean of rho %.3e exceeds 1e-12 * ||rho||_inf (%.3e)", mean, P));
+  }
+
+  // REFINE workspace: two unghosted FP32 fields with a 16-byte aligned pitch.
+  const int64_t ld32 = ((int64_t)f.nx + 3) / 4 * 4;
+  px_grid g32{f.nx, f.ny, ld32, 0, PX_F32, f.h};
+  float *r32 = nullptr, *e32 = nullptr;
+  if (o->mode == PX_SOLVE_REFINE) {
+    const size_t one = (size_t)ld32 * (size_t)f.ny * sizeof(float);
+    const size_t need = 2 * ((one + 255) / 256 * 256);
+    if (c->ws_bytes < need) {
+      if (c->ws) cudaFree(c->ws);
+      c->ws = nullptr;
+      c->ws_bytes = 0;
+      cudaError_t e = cudaMalloc(&c->ws, need);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return finish(fail(c, PX_ENOMEM, "solve workspace of %zu bytes", need));
+      }
+      c->ws_bytes = need;
+    }
+    r32 = (float*)c->ws;
+    e32 = (float*)((char*)c->ws + need / 2);
+  }
+
+  const double inf_d = std::numeric_limits<double>::infinity();
+  for (;;) {
+    double R = 0, P = 0;
+    s = sync_norms(c, f, phi, rho, st, &R, &P);
+    if (s != PX_OK) return finish(s);
+    inf.checks++;
+    inf.rel_resid = P > 0 ? R / P : (R == 0 ? 0.0 : inf_d);
+    if (!std::isfinite(R) || !std::isfinite(P))
+      return finish(fail(c, PX_ENAN, "residual is %g (rho norm %g)", R, P));
+    if (inf.rel_resid <= o->rtol || R == 0.0) return finish(PX_OK);
+    if (inf.sweeps >= o->max_sweeps)
+      return finish(fail(c, PX_ENOCONV, "%lld sweeps, relative residual %.3e > %.3e",
+                         (long long)inf.sweeps, inf.rel_resid, o->rtol));
+    if (o->timeout_ms > 0) {
+      const double ms = std::chrono::duration<double, std::milli>(
+                            std::chrono::steady_clock::now() - t0).count();
+      if (ms > (double)o->timeout_ms)
+        return finish(fail(c, PX_ETIMEOUT, "timeout after %.0f ms", ms));
+    }
+    const int64_t left = o->max_sweeps - inf.sweeps;
+    if (o->mode == PX_SOLVE_PLAIN) {
+      const int n = (int)std::min<int64_t>(o->check_every, left);
+      s = px_relax_n(c, g, phi, phi, rho, o->omega, n, o->tblock, nullptr, 0, stream);
+      if (s != PX_OK) return finish(s);
+      inf.sweeps += n;
+    } else {
+      const int n = (int)std::min<int64_t>(o->inner_sweeps, left);
+      cudaError_t e = px::launch_refine_residual(f, phi, rho, c->red, r32, e32, ld32, c->red + 2, st);
+      if (e != cudaSuccess) return finish(cuda_fail(c, e, "refine residual"));
+      s = px_relax_n(c, &g32, e32, e32, r32, o->omega, n, o->tblock, nullptr, 0, stream);
+      if (s != PX_OK) return finish(s);
+      e = px::launch_refine_update(f, phi, e32, ld32, c->red + 2, st);
+      if (e != cudaSuccess) return finish(cuda_fail(c, e, "refine update"));
+      inf.sweeps += n;
+      inf.cycles++;
+    }
+  }
+}

@@ -101,6 +101,18 @@ cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
 
 int device_sm_count();
 
+// Iterative refinement (stencil.cu). phi/rho FP64 with layout f; r32/e32 are
+// unghosted FP32 fields of pitch ld32. norm[0] = ||rho - L phi||_inf > 0.
+cudaError_t launch_refine_residual(const FieldDesc& f, const void* phi, const void* rho,
+                                   const double* norm, float* r32, float* e32, int64_t ld32,
+                                   double* inv_scale, cudaStream_t st);
+cudaError_t launch_refine_update(const FieldDesc& f, void* phi, const float* e32, int64_t ld32,
+                                 const double* inv_scale, cudaStream_t st);
+// Deterministic FP64 sum of a field's interior into *out (partials: sum_partials_count()).
+int sum_partials_count();
+cudaError_t launch_field_sum(const FieldDesc& f, const void* a, double* partials, double* out,
+                             cudaStream_t st);
+
 }  // namespace px
 
 #include <vector>

@@ -151,3 +151,117 @@ cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
 }
 
 }  // namespace px
+
+// ---------------------------------------------------------------------------
+// Iterative refinement around FP32-storage sweeps. The outer loop works in FP64:
+//   r = rho - L phi (FP64, same evaluation as the residual norm), scaled by the
+//   exact power of two s = 2^-ilogb(R) with R = ||r||_inf, stored as FP32;
+//   the FP32 sweeps solve L e = s r from e = 0;
+//   phi += e / s (FP64; the division by a power of two is exact).
+namespace px {
+namespace {
+
+__global__ void refine_residual_k(const double* __restrict__ phi, const double* __restrict__ rho,
+                                  int nx, int ny, int64_t ld, double ih2,
+                                  const double* __restrict__ norm, float* __restrict__ r32,
+                                  float* __restrict__ e32, int64_t ld32,
+                                  double* __restrict__ inv_scale) {
+  const double R = norm[0];
+  const int ex = ilogb(R);
+  const double s = ldexp(1.0, -ex);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *inv_scale = ldexp(1.0, ex);
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
+    const double* row = phi + (int64_t)j * ld;
+    const double C = row[i];
+    const double W = row[wrap1(i - 1, nx)], E = row[wrap1(i + 1, nx)];
+    const double S = phi[(int64_t)wrap1(j - 1, ny) * ld + i];
+    const double N = phi[(int64_t)wrap1(j + 1, ny) * ld + i];
+    const double s5 = __dsub_rn(__dadd_rn(__dadd_rn(W, E), __dadd_rn(S, N)), __dmul_rn(4.0, C));
+    const double r = __dsub_rn(rho[(int64_t)j * ld + i], __dmul_rn(ih2, s5));
+    r32[(int64_t)j * ld32 + i] = __double2float_rn(r * s);
+    e32[(int64_t)j * ld32 + i] = 0.0f;
+  }
+}
+
+__global__ void refine_update_k(double* __restrict__ phi, const float* __restrict__ e32, int nx,
+                                int ny, int64_t ld, int64_t ld32, int ghost,
+                                const double* __restrict__ inv_scale) {
+  const double is = *inv_scale;
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
+    const double v = __dadd_rn(phi[(int64_t)j * ld + i], (double)e32[(int64_t)j * ld32 + i] * is);
+    store_all_images<double>(phi, i, j, nx, ny, ld, ghost, v);
+  }
+}
+
+// Deterministic FP64 sum: fixed grid, per-block partials, one block sums them
+// in index order.
+constexpr int kSumBlocks = 512;
+template <typename T>
+__global__ void sum_partials_k(const T* __restrict__ a, int nx, int ny, int64_t ld,
+                               double* __restrict__ partials) {
+  const int64_t n = (int64_t)nx * ny;
+  double acc = 0.0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
+    acc += (double)a[(int64_t)j * ld + i];
+  }
+  __shared__ double sm[256];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sm[0];
+}
+
+__global__ void sum_final_k(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += partials[k];
+    *out = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_refine_residual(const FieldDesc& f, const void* phi, const void* rho,
+                                   const double* norm, float* r32, float* e32, int64_t ld32,
+                                   double* inv_scale, cudaStream_t st) {
+  const int64_t n = (int64_t)f.nx * f.ny;
+  refine_residual_k<<<grid_for(n, 256), 256, 0, st>>>(
+      (const double*)phi + f.off, (const double*)rho + f.off, f.nx, f.ny, f.ld,
+      1.0 / (f.h * f.h), norm, r32, e32, ld32, inv_scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update(const FieldDesc& f, void* phi, const float* e32, int64_t ld32,
+                                 const double* inv_scale, cudaStream_t st) {
+  const int64_t n = (int64_t)f.nx * f.ny;
+  refine_update_k<<<grid_for(n, 256), 256, 0, st>>>((double*)phi + f.off, e32, f.nx, f.ny, f.ld,
+                                                    ld32, f.ghost, inv_scale);
+  return cudaGetLastError();
+}
+
+int sum_partials_count() { return kSumBlocks; }
+
+cudaError_t launch_field_sum(const FieldDesc& f, const void* a, double* partials, double* out,
+                             cudaStream_t st) {
+  if (f.dtype == 0)
+    sum_partials_k<double><<<kSumBlocks, 256, 0, st>>>((const double*)a + f.off, f.nx, f.ny, f.ld,
+                                                       partials);
+  else
+    sum_partials_k<float><<<kSumBlocks, 256, 0, st>>>((const float*)a + f.off, f.nx, f.ny, f.ld,
+                                                      partials);
+  sum_final_k<<<1, 32, 0, st>>>(partials, kSumBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace px
