@@ -337,6 +337,216 @@ cudaError_t launch_tile_t(const FieldDesc& f, const T* src, T* dst, const T* rho
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// relaxW_f32: wavefront temporal blocking for FP32 storage, TB sweeps per launch.
+//
+// A CTA owns a strip of 256 cells (32 lanes x two float4 groups, columns
+// 4*lane and 128 + 4*lane) and a segment of H output rows. It streams down the
+// segment: stage t (warp t - 1) turns level t - 1 (the state after t - 1
+// sweeps) into level t one row per step, two rows behind stage t - 1, keeping
+// rows r - 1 and r of its input level in registers and reading row r + 1 from a
+// 4-row shared-memory ring. A loader warp keeps level 0 (phi) and rho rows
+// arriving kWPrefetch steps ahead with cp.async, so DRAM reads overlap the
+// sweeps; the last stage stores straight from registers. One barrier per step.
+// Each sweep is valid on a region one cell narrower per side, so the strip
+// owns its central 256 - 2*HX columns; in y the segment loads TB extra rows
+// above and below. Redundant work is (256 / (256 - 2 HX)) x (1 + TB / H).
+constexpr int kWStrip = 256;
+
+template <int TB>
+struct WGeom {
+  static constexpr int P = 6;                               // rows loaded ahead
+  static constexpr int HX = ((TB + 3) / 4) * 4;             // x halo, multiple of 4
+  static constexpr int OW = kWStrip - 2 * HX;               // owned width
+  static constexpr int R0 = 16;                             // level-0 ring rows (>= P + 4)
+  static constexpr int RR = (2 * TB + P + 1) <= 16 ? 16 : 32;  // rho ring rows (>= 2 TB + P + 1)
+  static constexpr int RL = 4;                              // rows per level ring
+  static constexpr int kThreads = (TB + 1) * kWarp;         // TB stages + loader
+  static constexpr size_t smem = sizeof(float) * kWStrip * (size_t)(R0 + RR + RL * (TB - 1));
+  static_assert(R0 >= P + 4 && RR >= 2 * TB + P + 1, "ring sizes");
+};
+
+__device__ __forceinline__ void lds4(float* v, const float* p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void sts4(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <int TB>
+__global__ void __launch_bounds__(WGeom<TB>::kThreads)
+relaxW_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
+           int nx, int ny, int64_t ld, int H, int nstrips, Coef<float> k, Reports rep) {
+  using G = WGeom<TB>;
+  extern __shared__ __align__(16) float wsm[];
+  float* L0 = wsm;                        // level 0, R0 rows
+  float* RH = L0 + G::R0 * kWStrip;       // rho, RR rows
+  float* LV = RH + G::RR * kWStrip;       // levels 1..TB-1, RL rows each
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+  const int y0 = seg * H;
+  const int base = y0 - TB;               // global row of load index 0
+  const int nload = H + 2 * TB;
+  const int gx0 = strip * G::OW - G::HX;  // global column of strip column 0 (unwrapped)
+  const int steps = H + 3 * TB;
+  const int c0 = lane * 4, c1 = 128 + lane * 4;
+
+  if (warp == TB) {
+    // Loader: load index i (global row base + i) of phi and rho into ring slots.
+    const int gxa = wrapn(gx0 + c0, nx), gxb = wrapn(gx0 + c1, nx);
+    int grow = wrapn(base, ny);           // global row of the next load index
+    int i = 0;
+    auto issue = [&]() {
+      if (i < nload) {
+        const int64_t row = (int64_t)grow * ld;
+        float* d0 = L0 + (i & (G::R0 - 1)) * kWStrip;
+        float* d1 = RH + (i & (G::RR - 1)) * kWStrip;
+        cp_async16(d0 + c0, phi + row + gxa);
+        cp_async16(d0 + c1, phi + row + gxb);
+        cp_async16(d1 + c0, rho + row + gxa);
+        cp_async16(d1 + c1, rho + row + gxb);
+        grow = (grow + 1 == ny) ? 0 : grow + 1;
+      }
+      ++i;
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+#pragma unroll 1
+    for (int q = 0; q < G::P; ++q) issue();
+#pragma unroll 1
+    for (int st = 0; st < steps; ++st) {
+      issue();
+      // row st is complete; rows st+1 .. st+P may still be in flight
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(G::P) : "memory");
+      __syncthreads();
+    }
+    return;
+  }
+
+  const int t = warp + 1;  // stage: computes level t from level t - 1
+  const float* src = (t == 1) ? L0 : LV + (t - 2) * G::RL * kWStrip;
+  const int smask = (t == 1) ? G::R0 - 1 : G::RL - 1;
+  float* dstL = LV + (t - 1) * G::RL * kWStrip;  // used when t < TB
+  const bool rep_t = rep.due(t - 1);
+  const bool own0 = c0 >= G::HX && c0 < kWStrip - G::HX && gx0 + c0 < nx;
+  const bool own1 = c1 >= G::HX && c1 < kWStrip - G::HX && gx0 + c1 < nx;
+  const int own_hi = min(TB + H, TB + ny - y0);  // owned rows: TB <= ridx < own_hi
+  float* const orow0 = out + gx0;                 // + gy * ld + column
+  const int first = t, count = H + 2 * TB - 2 * t;
+  uint32_t mx = 0;
+
+#pragma unroll 1
+  for (int st = 0; st < 3 * t; ++st) __syncthreads();
+
+  float A[8], B[8], C[8];
+  lds4(A, src + ((first - 1) & smask) * kWStrip + c0);
+  lds4(A + 4, src + ((first - 1) & smask) * kWStrip + c1);
+  lds4(B, src + (first & smask) * kWStrip + c0);
+  lds4(B + 4, src + (first & smask) * kWStrip + c1);
+  int ridx = first;
+
+  // One row of level t: up, cu hold rows ridx-1, ridx of level t-1; dn receives ridx+1.
+  auto row = [&](const float* up, const float* cu, float* dn) {
+    const float* sdn = src + ((ridx + 1) & smask) * kWStrip;
+    const float* srh = RH + (ridx & (G::RR - 1)) * kWStrip;
+    lds4(dn, sdn + c0);
+    lds4(dn + 4, sdn + c1);
+    float rh[8];
+    lds4(rh, srh + c0);
+    lds4(rh + 4, srh + c1);
+    // x neighbours across the lanes; columns -1 and 256 are never owned
+    const float l0 = __shfl_sync(0xffffffffu, cu[3], (lane + 31) & 31);
+    const float l1 = __shfl_sync(0xffffffffu, lane == 31 ? cu[3] : cu[7], (lane + 31) & 31);
+    const float r0 = __shfl_sync(0xffffffffu, lane == 0 ? cu[4] : cu[0], (lane + 1) & 31);
+    const float r1 = __shfl_sync(0xffffffffu, cu[4], (lane + 1) & 31);
+    float o[8], rr[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float w = (i == 0) ? l0 : (i == 4) ? l1 : cu[i - 1];
+      const float e = (i == 3) ? r0 : (i == 7) ? r1 : cu[i + 1];
+      const float q = (w + e) + (up[i] + dn[i]);
+      const float sv = fmaf(-4.0f, cu[i], q);
+      rr[i] = fmaf(sv, k.ih2, -rh[i]);
+      o[i] = fmaf(k.c, rr[i], cu[i]);
+    }
+    if (rep_t) {
+      const bool own_row = ridx >= TB && ridx < own_hi;
+      const uint32_t m0 = (own_row && own0) ? 0x7fffffffu : 0u;
+      const uint32_t m1 = (own_row && own1) ? 0x7fffffffu : 0u;
+      mx = __vimax3_u32(mx, __float_as_uint(rr[0]) & m0, __float_as_uint(rr[1]) & m0);
+      mx = __vimax3_u32(mx, __float_as_uint(rr[2]) & m0, __float_as_uint(rr[3]) & m0);
+      mx = __vimax3_u32(mx, __float_as_uint(rr[4]) & m1, __float_as_uint(rr[5]) & m1);
+      mx = __vimax3_u32(mx, __float_as_uint(rr[6]) & m1, __float_as_uint(rr[7]) & m1);
+    }
+    if (t < TB) {
+      float* d = dstL + (ridx & (G::RL - 1)) * kWStrip;
+      sts4(d + c0, o);
+      sts4(d + c1, o + 4);
+    } else {
+      const int gy = base + ridx;
+      if (gy < ny) {
+        float* orow = orow0 + (int64_t)gy * ld;
+        if (own0) sts4(orow + c0, o);
+        if (own1) sts4(orow + c1, o + 4);
+      }
+    }
+    ++ridx;
+    __syncthreads();
+  };
+
+  int n = count;
+#pragma unroll 1
+  while (n >= 3) {
+    row(A, B, C);
+    row(B, C, A);
+    row(C, A, B);
+    n -= 3;
+  }
+  if (n >= 1) row(A, B, C);
+  if (n >= 2) row(B, C, A);
+
+#pragma unroll 1
+  for (int st = 3 * t + count; st < steps; ++st) __syncthreads();
+
+  if (rep_t) {
+    mx = warp_max(mx);
+    if (lane == 0) atomic_max_bits(rep.slot(t - 1), to_f64_bits(mx));
+  }
+}
+
+template <int TB>
+cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
+                          Coef<float> k, Reports rep, cudaStream_t st) {
+  using G = WGeom<TB>;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(relaxW_f32<TB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxW_f32<TB>, G::kThreads, G::smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  const int nstrips = (f.nx + G::OW - 1) / G::OW;
+  const int64_t resident = (int64_t)occ * device_sm_count();
+  // Segment height: minimise (waves of CTAs) x (steps per CTA).
+  static const int cand[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+  int H = 16;
+  double best = 1e300;
+  for (int h : cand) {
+    const int64_t ctas = (int64_t)nstrips * ((f.ny + h - 1) / h);
+    const double cost = (double)((ctas + resident - 1) / resident) * (h + 3 * TB);
+    if (cost <= best) { best = cost; H = h; }
+    if (h >= f.ny) break;
+  }
+  const int64_t blocks = (int64_t)nstrips * ((f.ny + H - 1) / H);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  relaxW_f32<TB><<<(unsigned)blocks, G::kThreads, G::smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
+                                                                  H, nstrips, k, rep);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
                            double omega, int tb, bool vec, Reports rep, cudaStream_t st) {
@@ -353,6 +563,18 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
     }
     return r ? launch_stream_t<T, 1, true>(f, src, dst, rho, k, slot, st)
              : launch_stream_t<T, 1, false>(f, src, dst, rho, k, slot, st);
+  }
+  if constexpr (sizeof(T) == 4) {
+    switch (tb) {
+      case 2: return launch_wave_t<2>(f, src, dst, rho, k, rep, st);
+      case 3: return launch_wave_t<3>(f, src, dst, rho, k, rep, st);
+      case 4: return launch_wave_t<4>(f, src, dst, rho, k, rep, st);
+      case 5: return launch_wave_t<5>(f, src, dst, rho, k, rep, st);
+      case 6: return launch_wave_t<6>(f, src, dst, rho, k, rep, st);
+      case 7: return launch_wave_t<7>(f, src, dst, rho, k, rep, st);
+      case 8: return launch_wave_t<8>(f, src, dst, rho, k, rep, st);
+      default: return cudaErrorInvalidValue;
+    }
   }
   switch (tb) {
     case 2: return launch_tile_t<T, 2>(f, src, dst, rho, k, rep, st);
