@@ -34,6 +34,15 @@ N_DEFAULT = 16384
 SWEEPS = 200
 OMEGA = 2.0 / 3.0
 ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cell per launch
+# DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
+# (profiles/relaxW_f32_6144.md: dram read + write of one 6144^2 launch / cells).
+MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (312.119296e6 + 121.245184e6) / 6144**2}
+
+
+def kernel_name(dt: str, tb: int) -> str:
+    if tb == 1:
+        return "relax1_stream<float,4>" if dt == "f32" else "relax1_stream<double,2>"
+    return f"relaxW_f32<{tb}>" if dt == "f32" else f"relaxT_tile<double,{tb}>"
 
 
 def peaks():
@@ -250,7 +259,7 @@ def run_gpu(args, world, rank, local):
         lps = launches_per_step(tb)
         launch_s = t / lps
         variants[key] = {
-            "tblock": tb, "ms_per_step": 1000 * t, "GLUP_s": cells * SWEEPS / t / 1e9,
+            "kernel": kernel_name(dt, tb), "tblock": tb, "ms_per_step": 1000 * t, "GLUP_s": cells * SWEEPS / t / 1e9,
             "ms_per_launch": 1000 * launch_s,
             "algo_GB_s": ALGO_BYTES[dt] * cells / launch_s / 1e9,
             "effective_GB_s": ALGO_BYTES[dt] * cells * SWEEPS / t / 1e9,
@@ -328,12 +337,16 @@ def run_gpu(args, world, rank, local):
                 "parallelism": f"replicas x{world}",
             },
             "roofline": {
-                "kernel": f"relaxT_tile<float,{auto_tb}>", "bound": "hbm",
+                "kernel": kernel_name("f32", auto_tb), "bound": "hbm",
                 "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": args.traffic,
+                "frac": achieved / hbm_peak,
+                "traffic": (args.traffic if args.traffic is not None else
+                            (MEASURED_TRAFFIC_PER_CELL[("f32", auto_tb)] * cells
+                             if ("f32", auto_tb) in MEASURED_TRAFFIC_PER_CELL else None)),
                 "note": f"algorithmic bytes 12 B/cell per launch of {auto_tb} sweeps over "
                         f"{cells} cells / mean launch time (step time / {lps} launches); "
-                        f"peak {peak_kind}",
+                        f"peak {peak_kind}; traffic = ncu DRAM bytes per cell of a 6144^2 "
+                        f"launch scaled by the cell count",
             },
             "variants": variants,
             "fp64_note": "FP64 sweep is bound by the FP64 pipe (0.555 T DFMA/s measured), "
