@@ -208,6 +208,48 @@ typedef struct {
 px_status px_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho,
                    const px_solve_opts* opts, px_solve_info* info, void* stream);
 
+/* ----------------------------------------------------------------------------
+ * Batched relaxation: many independent periodic instances of uneven sizes and
+ * mixed dtypes, nsweeps fused sweeps each (the same sweep as px_relax_n), in
+ * ONE persistent kernel launch replayed from a CUDA graph. Instances are
+ * independent problems, so the batch needs no exchange between them.
+ *
+ * Execution per size class (dtype, nx, ny), chosen by an autotuner:
+ *  WHOLE   one CTA keeps the instance in shared memory for all sweeps
+ *          (fits when 2 * nx * ny * element size <= 200 KiB);
+ *  BANDED  a cluster of 8 CTAs shares the instance, one band of rows each,
+ *          sweeping from global memory with a cluster barrier per sweep.
+ * The tuner times both modes (and the rows per warp task of BANDED) on one
+ * representative instance per class and keeps the fastest rate per SM; the
+ * results are cached as JSON keyed by GPU name. The schedule assigns
+ * instances longest-first to the least loaded cluster / CTA.
+ *
+ * px_batch_plan   grids[n]: layouts (unghosted; nx, ld multiples of 4 for FP32,
+ *                 2 for FP64; PX_EUNSUPPORTED otherwise). nsweeps, omega,
+ *                 report_every as in px_relax_n. tune_cache: JSON path or NULL.
+ *                 tune: nonzero = measure classes missing from the cache
+ *                 (synchronises the device; allocates temporary buffers).
+ *                 Allocates the plan's device tables, BANDED scratch fields and
+ *                 captures the graph. *out is NULL on failure.
+ * px_batch_run    phis[i], rhos[i]: DEVICE fields of instance i (16-byte aligned,
+ *                 phi and rho must not overlap); phi is relaxed in place.
+ *                 resid_dev: NULL or DEVICE array of n * nrep doubles, instance
+ *                 i's reports at i * nrep (nrep = ceil(nsweeps / report_every)),
+ *                 zero-filled by the call. Waits for the plan's previous run,
+ *                 then enqueues on `stream` and returns.
+ * px_batch_describe  JSON text of the plan (classes, modes, rates, clusters,
+ *                 predicted time); valid until px_batch_destroy.
+ * px_batch_destroy   synchronises the device and frees the plan.
+ */
+typedef struct px_batch px_batch;
+
+px_status px_batch_plan(px_ctx* ctx, int n, const px_grid* grids, int nsweeps, double omega,
+                        int report_every, const char* tune_cache, int tune, px_batch** out);
+px_status px_batch_run(px_batch* plan, void* const* phis, const void* const* rhos,
+                       double* resid_dev, void* stream);
+const char* px_batch_describe(const px_batch* plan);
+px_status px_batch_destroy(px_batch* plan);
+
 /* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
  * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,
  * *rho_norm_host = ||rho||_inf. Evaluated in FP64 for both dtypes (FP32 fields

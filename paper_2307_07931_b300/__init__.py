@@ -83,11 +83,17 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     ip = ctypes.POINTER(ctypes.c_int)
     lib.px_relax_plan.argtypes = [_vp, gp, _vp, _vp, _vp, i, i, ip, ip]
     lib.px_relax_n_static.argtypes = [gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
+    lib.px_batch_plan.argtypes = [_vp, i, gp, i, d, i, ctypes.c_char_p, i, ctypes.POINTER(_vp)]
+    lib.px_batch_run.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _vp]
+    lib.px_batch_describe.argtypes = [_vp]
+    lib.px_batch_describe.restype = ctypes.c_char_p
+    lib.px_batch_destroy.argtypes = [_vp]
     lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
                              ctypes.POINTER(SolveInfo), _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
                  "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
-                 "px_relax_n_static", "px_solve"):
+                 "px_relax_n_static", "px_solve", "px_batch_plan", "px_batch_run",
+                 "px_batch_destroy"):
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -286,3 +292,49 @@ def solve(phi, rho, h: float, mode: str = "plain", omega: float = 2.0 / 3.0, rto
         err.info = d
         raise err
     return d
+
+
+class Batch:
+    """px_batch_plan / px_batch_run: many independent instances in one persistent
+    launch replayed from a CUDA graph. `grids` are Grid layouts (or tensors,
+    whose layout is taken with h = 1 / nx)."""
+
+    def __init__(self, grids, nsweeps: int, omega: float = 2.0 / 3.0, report_every: int = 0,
+                 tune_cache: str | None = None, tune: bool = False, ctx: Context | None = None):
+        self.ctx = ctx or context()
+        gs = [g if isinstance(g, Grid) else grid_of(g, 1.0 / g.shape[1]) for g in grids]
+        self.n = len(gs)
+        self.nsweeps = int(nsweeps)
+        self.every = int(report_every)
+        self.nrep = (self.nsweeps + self.every - 1) // self.every if self.every > 0 else 0
+        arr = (Grid * self.n)(*gs)
+        h = _vp()
+        self.ctx.check(load_library().px_batch_plan(
+            self.ctx.handle, self.n, arr, self.nsweeps, float(omega), self.every,
+            tune_cache.encode() if tune_cache else None, 1 if tune else 0, ctypes.byref(h)))
+        self.handle = h
+
+    def describe(self) -> dict:
+        import json
+        return json.loads(load_library().px_batch_describe(self.handle).decode())
+
+    def run(self, phis, rhos, resid=None, stream=None):
+        if len(phis) != self.n or len(rhos) != self.n:
+            raise ValueError("one phi and one rho per instance")
+        pa = (_vp * self.n)(*[p.data_ptr() for p in phis])
+        ra = (_vp * self.n)(*[r.data_ptr() for r in rhos])
+        if resid is not None and resid.numel() < self.n * self.nrep:
+            raise ValueError("resid needs n * nrep entries")
+        self.ctx.check(load_library().px_batch_run(self.handle, pa, ra, _ptr(resid),
+                                                   _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().px_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -15,16 +15,6 @@
 #include <string>
 #include <vector>
 
-struct px_ctx {
-  int device = 0;
-  void* scratch = nullptr;   // ping-pong field buffer
-  size_t scratch_bytes = 0;
-  double* red = nullptr;     // device aux block: [0,1] norms, [2] scale, [3] sum, [8..] partials
-  double* red_host = nullptr;  // pinned mirror of red[0..3]
-  void* ws = nullptr;        // solve workspace: FP32 r and e fields
-  size_t ws_bytes = 0;
-  std::string err;
-};
 
 namespace {
 
@@ -154,6 +144,8 @@ std::vector<int> plan_launches(const px::FieldDesc& f, bool vec, bool inplace, i
 // Helpers shared with the context-free entry point in relax_static.cu. They
 // report failures through the thread's context-free message (px_last_error(NULL)).
 namespace px {
+px_status ctx_fail(px_ctx* c, px_status st, const char* msg) { return fail(c, st, "%s", msg); }
+px_status ctx_check_grid(px_ctx* c, const px_grid* g, FieldDesc* f) { return check_grid(c, g, f); }
 px_status unbound_check_grid(const px_grid* g, FieldDesc* f) { return check_grid(nullptr, g, f); }
 px_status unbound_fail(px_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
 size_t field_bytes(const FieldDesc& f) { return field_span(f); }

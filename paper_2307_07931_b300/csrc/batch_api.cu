@@ -1,0 +1,471 @@
+// C ABI of the batched persistent relaxation: plan (size classes, autotuning,
+// schedule, CUDA graph) and run. The kernel is in batch.cu.
+#include "px_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+namespace {
+
+struct ClassCfg {
+  int mode = px::MODE_BANDED;
+  int ry = 8;
+  double rate_per_sm = 0.0;  // measured cell updates / s per SM (0 = not measured)
+  bool tuned = false;
+};
+
+std::string class_key(int dtype, int nx, int ny) {
+  char b[64];
+  snprintf(b, sizeof b, "%s:%dx%d", dtype == PX_F64 ? "f64" : "f32", nx, ny);
+  return b;
+}
+
+bool fits_whole(int nx, int ny, int dtype) {
+  return px::whole_bytes(nx, ny, dtype) <= px::batch_whole_smem();
+}
+
+// Default rates per SM (cell updates / s) when a class was not measured: FP64
+// is bound by the FP64 pipe (about 0.555e12 DFMA/s over 148 SMs, 6 per
+// update); FP32 by shared memory (WHOLE) or L2 bandwidth (BANDED).
+double default_rate(int dtype, int mode) {
+  if (dtype == PX_F64) return 0.6e9;
+  return mode == px::MODE_WHOLE ? 8e9 : 6e9;
+}
+
+std::string gpu_name(int dev) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  return p.name;
+}
+
+// Tune cache: one JSON object, {"gpu": "...", "classes": {"f32:96x96": {"mode": 0,
+// "ry": 8, "rate_per_sm": 1.2e10}, ...}}. Written and read only by this file.
+void load_cache(const char* path, const std::string& gpu, std::map<std::string, ClassCfg>& out) {
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  std::string s;
+  char buf[4096];
+  size_t n;
+  while ((n = fread(buf, 1, sizeof buf, f)) > 0) s.append(buf, n);
+  fclose(f);
+  const std::string gk = "\"gpu\": \"" + gpu + "\"";
+  if (s.find(gk) == std::string::npos) return;  // another GPU: ignore
+  size_t pos = 0;
+  while ((pos = s.find("\"f", pos)) != std::string::npos) {
+    const size_t q = s.find('"', pos + 1);
+    if (q == std::string::npos) break;
+    const std::string key = s.substr(pos + 1, q - pos - 1);
+    int mode = 0, ry = 0;
+    double rate = 0;
+    if (sscanf(s.c_str() + q + 1, ": {\"mode\": %d, \"ry\": %d, \"rate_per_sm\": %lf}", &mode,
+               &ry, &rate) == 3 && key.find(':') != std::string::npos) {
+      ClassCfg c;
+      c.mode = mode;
+      c.ry = ry;
+      c.rate_per_sm = rate;
+      c.tuned = true;
+      out[key] = c;
+    }
+    pos = q + 1;
+  }
+}
+
+void save_cache(const char* path, const std::string& gpu, const std::map<std::string, ClassCfg>& m) {
+  if (!path) return;
+  std::string tmp = std::string(path) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\"gpu\": \"%s\", \"classes\": {", gpu.c_str());
+  bool first = true;
+  for (const auto& kv : m) {
+    if (!kv.second.tuned) continue;
+    fprintf(f, "%s\n  \"%s\": {\"mode\": %d, \"ry\": %d, \"rate_per_sm\": %.6e}", first ? "" : ",",
+            kv.first.c_str(), kv.second.mode, kv.second.ry, kv.second.rate_per_sm);
+    first = false;
+  }
+  fprintf(f, "\n}}\n");
+  fclose(f);
+  rename(tmp.c_str(), path);
+}
+
+}  // namespace
+
+struct px_batch {
+  px_ctx* ctx = nullptr;
+  int n = 0, nsweeps = 0, every = 0, nrep = 0;
+  double omega = 0;
+  std::vector<px_grid> grids;
+  std::vector<px::BInst> inst;       // host copy; pointers filled per run
+  px::BInst* inst_dev = nullptr;
+  px::BInst* inst_pinned = nullptr;
+  int* idx_dev = nullptr;            // cl_off | cl_items | cta_off | cta_items
+  void* scratch = nullptr;
+  int nclusters = 0;
+  size_t smem = 0;
+  px::BParams params{};
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string desc;
+};
+
+namespace {
+
+// Measures one class on one representative instance: WHOLE (one CTA) and
+// BANDED (one cluster) with rows-per-task 4, 8, 16; keeps the fastest rate
+// per SM. Buffers are zero fields allocated for the measurement.
+px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double omega,
+                     ClassCfg* out) {
+  const int64_t ld = nx;
+  const size_t es = dtype == PX_F64 ? 8 : 4;
+  const size_t bytes = (size_t)ld * ny * es;
+  void *phi = nullptr, *rho = nullptr, *scr = nullptr, *idx = nullptr, *ins = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  px_status st = PX_OK;
+  const int C = px::batch_cluster_size();
+  std::vector<std::pair<int, int>> cands;  // (mode, ry)
+  if (fits_whole(nx, ny, dtype)) cands.push_back({px::MODE_WHOLE, 0});
+  for (int ry : {4, 8, 16}) cands.push_back({px::MODE_BANDED, ry});
+  double best = -1;
+  cudaError_t e = cudaMalloc(&phi, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&rho, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&scr, bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&idx, 64 * sizeof(int) + 4 * C * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ins, sizeof(px::BInst));
+  if (e == cudaSuccess) e = cudaMemset(phi, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(rho, 0, bytes);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (size_t k = 0; e == cudaSuccess && k < cands.size(); ++k) {
+    px::BInst I{};
+    I.phi = phi; I.rho = rho; I.scratch = scr; I.nx = nx; I.ny = ny; I.ld = ld;
+    I.dtype = dtype; I.mode = cands[k].first; I.ry = cands[k].second;
+    const double h = 1.0 / nx;
+    I.c = omega * h * h / 4.0; I.ih2 = 1.0 / (h * h); I.resid = nullptr;
+    // one cluster: BANDED -> cluster list {0}; WHOLE -> CTA 0 list {0}
+    std::vector<int> ix;
+    const bool band = I.mode == px::MODE_BANDED;
+    ix.push_back(0); ix.push_back(band ? 1 : 0);          // cl_off
+    ix.push_back(0);                                      // cl_items
+    for (int r = 0; r <= C; ++r) ix.push_back(band ? 0 : (r == 0 ? 0 : 1));  // cta_off
+    ix.push_back(0);                                      // cta_items
+    e = cudaMemcpy(idx, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ins, &I, sizeof I, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) break;
+    px::BParams p{};
+    p.inst = (px::BInst*)ins;
+    p.cl_off = (int*)idx;
+    p.cl_items = (int*)idx + 2;
+    p.cta_off = (int*)idx + 3;
+    p.cta_items = (int*)idx + 4 + C;
+    p.nsweeps = sweeps;
+    p.every = 0;
+    const size_t smem = band ? 0 : px::whole_bytes(nx, ny, dtype);
+    e = px::batch_launch(p, 1, smem, 0);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
+    if (e == cudaSuccess) e = px::batch_launch(p, 1, smem, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    const double sms = band ? C : 1;
+    const double rate = (double)nx * ny * sweeps / (ms * 1e-3) / sms;
+    if (rate > best) {
+      best = rate;
+      out->mode = I.mode;
+      out->ry = band ? I.ry : 8;
+      out->rate_per_sm = rate;
+      out->tuned = true;
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    st = px::ctx_fail(c, PX_ECUDA, (std::string("batch tuning: ") + cudaGetErrorString(e)).c_str());
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(phi); cudaFree(rho); cudaFree(scr); cudaFree(idx); cudaFree(ins);
+  return st;
+}
+
+void destroy_batch(px_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->inst_dev) cudaFree(b->inst_dev);
+  if (b->inst_pinned) cudaFreeHost(b->inst_pinned);
+  if (b->idx_dev) cudaFree(b->idx_dev);
+  if (b->scratch) cudaFree(b->scratch);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, double omega,
+                        int report_every, const char* tune_cache, int tune, px_batch** out) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  if (!out) return px::ctx_fail(c, PX_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !grids) return px::ctx_fail(c, PX_EINVAL, "need n > 0 grids");
+  if (nsweeps < 0 || report_every < 0 || !std::isfinite(omega))
+    return px::ctx_fail(c, PX_EINVAL, "bad nsweeps / report_every / omega");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  struct Restore { int p, d; ~Restore() { if (p >= 0 && p != d) cudaSetDevice(p); } } rs{prev, c->device};
+
+  px_batch* b = new (std::nothrow) px_batch();
+  if (!b) return px::ctx_fail(c, PX_ENOMEM, "host allocation failed");
+  b->ctx = c;
+  b->n = n;
+  b->nsweeps = nsweeps;
+  b->every = report_every;
+  b->omega = omega;
+  b->nrep = report_every > 0 ? (nsweeps + report_every - 1) / report_every : 0;
+  b->grids.assign(grids, grids + n);
+  const int C = px::batch_cluster_size();
+
+  // classes and their configuration
+  std::map<std::string, ClassCfg> cfg;
+  std::map<std::string, int> count;
+  for (int i = 0; i < n; ++i) {
+    px::FieldDesc f;
+    px_status s = px::ctx_check_grid(c, &grids[i], &f);
+    if (s != PX_OK) { destroy_batch(b); return s; }
+    const int V = f.dtype == PX_F64 ? 2 : 4;
+    if (f.ghost || f.nx < 1 || f.ny < 1 || f.nx % V || f.ld % V) {
+      destroy_batch(b);
+      return px::ctx_fail(c, PX_EUNSUPPORTED,
+                          "batched instances must be unghosted, non-empty, with nx and ld "
+                          "multiples of 4 (FP32) or 2 (FP64)");
+    }
+    const std::string k = class_key(f.dtype, f.nx, f.ny);
+    count[k]++;
+    if (!cfg.count(k)) {
+      ClassCfg d;
+      d.mode = fits_whole(f.nx, f.ny, f.dtype) ? px::MODE_WHOLE : px::MODE_BANDED;
+      d.ry = 8;
+      d.rate_per_sm = default_rate(f.dtype, d.mode);
+      cfg[k] = d;
+    }
+  }
+  const std::string gpu = gpu_name(c->device);
+  std::map<std::string, ClassCfg> cached;
+  load_cache(tune_cache, gpu, cached);
+  int tuned_now = 0;
+  for (auto& kv : cfg) {
+    auto it = cached.find(kv.first);
+    if (it != cached.end()) {
+      kv.second = it->second;
+      continue;
+    }
+    if (tune) {
+      int dt = kv.first[1] == '6' ? PX_F64 : PX_F32;
+      int nx = 0, ny = 0;
+      sscanf(kv.first.c_str() + 4, "%dx%d", &nx, &ny);
+      ClassCfg t;
+      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, &t);
+      if (s != PX_OK) { destroy_batch(b); return s; }
+      kv.second = t;
+      cached[kv.first] = t;
+      ++tuned_now;
+    }
+  }
+  if (tuned_now) save_cache(tune_cache, gpu, cached);
+
+  // resident clusters
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny)];
+    if (k.mode == px::MODE_WHOLE) smem = std::max(smem, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
+  }
+  smem = (smem + 1023) / 1024 * 1024;
+  int ncl = 0;
+  cudaError_t e = px::batch_max_clusters(&ncl, smem);
+  if (e != cudaSuccess || ncl < 1) {
+    cudaGetLastError();
+    destroy_batch(b);
+    return px::ctx_fail(c, PX_ECUDA, "no cluster of the batch kernel fits on this device");
+  }
+  b->nclusters = ncl;
+  b->smem = smem;
+
+  // schedule: longest first to the least loaded (times in seconds)
+  std::vector<double> cl_load(ncl, 0.0), cta_load(ncl * C, 0.0);
+  std::vector<std::vector<int>> cl_items(ncl), cta_items(ncl * C);
+  std::vector<std::pair<double, int>> banded, whole;
+  size_t scratch_bytes = 0;
+  std::vector<size_t> scr_off(n, 0);
+  b->inst.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const px_grid& g = grids[i];
+    const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny)];
+    px::BInst& I = b->inst[i];
+    I = px::BInst{};
+    I.nx = g.nx; I.ny = g.ny; I.ld = g.ld; I.dtype = g.dtype; I.mode = k.mode; I.ry = k.ry;
+    I.c = omega * g.h * g.h / 4.0;
+    I.ih2 = 1.0 / (g.h * g.h);
+    const double work = (double)g.nx * g.ny * nsweeps / std::max(k.rate_per_sm, 1.0);
+    if (k.mode == px::MODE_BANDED) {
+      banded.push_back({work / C, i});
+      scr_off[i] = scratch_bytes;
+      scratch_bytes += ((size_t)g.ld * g.ny * (g.dtype == PX_F64 ? 8 : 4) + 255) / 256 * 256;
+    } else {
+      whole.push_back({work, i});
+    }
+  }
+  std::sort(banded.begin(), banded.end(), [](auto& a, auto& b2) { return a.first > b2.first; });
+  std::sort(whole.begin(), whole.end(), [](auto& a, auto& b2) { return a.first > b2.first; });
+  for (auto& w : banded) {
+    const int k = (int)(std::min_element(cl_load.begin(), cl_load.end()) - cl_load.begin());
+    cl_load[k] += w.first;
+    cl_items[k].push_back(w.second);
+  }
+  for (int k = 0; k < ncl; ++k)
+    for (int r = 0; r < C; ++r) cta_load[k * C + r] = cl_load[k];
+  for (auto& w : whole) {
+    const int k = (int)(std::min_element(cta_load.begin(), cta_load.end()) - cta_load.begin());
+    cta_load[k] += w.first;
+    cta_items[k].push_back(w.second);
+  }
+  std::vector<int> ix;
+  ix.push_back(0);
+  for (int k = 0; k < ncl; ++k) ix.push_back(ix.back() + (int)cl_items[k].size());
+  const size_t cl_items_at = ix.size();
+  for (int k = 0; k < ncl; ++k) ix.insert(ix.end(), cl_items[k].begin(), cl_items[k].end());
+  const size_t cta_off_at = ix.size();
+  ix.push_back(0);
+  for (int k = 0; k < ncl * C; ++k) ix.push_back(ix.back() + (int)cta_items[k].size());
+  const size_t cta_items_at = ix.size();
+  for (int k = 0; k < ncl * C; ++k) ix.insert(ix.end(), cta_items[k].begin(), cta_items[k].end());
+  ix.push_back(0);  // keep the arrays non-empty
+
+  e = cudaMalloc(&b->idx_dev, ix.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(b->idx_dev, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&b->inst_dev, n * sizeof(px::BInst));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->inst_pinned, n * sizeof(px::BInst));
+  if (e == cudaSuccess && scratch_bytes) e = cudaMalloc(&b->scratch, scratch_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy_batch(b);
+    return px::ctx_fail(c, PX_ENOMEM, "batch plan buffers");
+  }
+  for (int i = 0; i < n; ++i)
+    if (b->inst[i].mode == px::MODE_BANDED) b->inst[i].scratch = (char*)b->scratch + scr_off[i];
+  b->params.inst = b->inst_dev;
+  b->params.cl_off = b->idx_dev;
+  b->params.cl_items = b->idx_dev + cl_items_at;
+  b->params.cta_off = b->idx_dev + cta_off_at;
+  b->params.cta_items = b->idx_dev + cta_items_at;
+  b->params.nsweeps = nsweeps;
+  b->params.every = report_every;
+
+  // The launch is captured once into a graph; runs replay it.
+  e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t el = px::batch_launch(b->params, ncl, smem, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (el != cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    std::string m = std::string("batch graph: ") + cudaGetErrorString(e);
+    destroy_batch(b);
+    return px::ctx_fail(c, PX_ECUDA, m.c_str());
+  }
+
+  // description
+  std::ostringstream os;
+  const double makespan = *std::max_element(cta_load.begin(), cta_load.end());
+  double total = 0;
+  for (double v : cta_load) total += v;
+  os << "{\"clusters\": " << ncl << ", \"cluster_size\": " << C << ", \"smem\": " << smem
+     << ", \"predicted_ms\": " << makespan * 1e3
+     << ", \"balance\": " << (makespan > 0 ? total / (makespan * ncl * C) : 1.0)
+     << ", \"classes\": {";
+  bool first = true;
+  for (auto& kv : cfg) {
+    os << (first ? "" : ", ") << "\"" << kv.first << "\": {\"count\": " << count[kv.first]
+       << ", \"mode\": \"" << (kv.second.mode == px::MODE_WHOLE ? "whole" : "banded")
+       << "\", \"ry\": " << kv.second.ry << ", \"rate_per_sm\": " << kv.second.rate_per_sm
+       << ", \"tuned\": " << (kv.second.tuned ? "true" : "false") << "}";
+    first = false;
+  }
+  os << "}}";
+  b->desc = os.str();
+  *out = b;
+  return PX_OK;
+}
+
+px_status px_batch_run(px_batch* b, void* const* phis, const void* const* rhos,
+                       double* resid_dev, void* stream) {
+  if (!b) return PX_EINVAL;
+  px_ctx* c = b->ctx;
+  c->err.clear();
+  if (!phis || !rhos) return px::ctx_fail(c, PX_EINVAL, "phis / rhos is NULL");
+  for (int i = 0; i < b->n; ++i) {
+    const px_grid& g = b->grids[i];
+    const size_t span = (size_t)((int64_t)(g.ny - 1) * g.ld + g.nx) * (g.dtype == PX_F64 ? 8 : 4);
+    if (!phis[i] || !rhos[i]) return px::ctx_fail(c, PX_EINVAL, "NULL instance pointer");
+    if ((((uintptr_t)phis[i]) & 15) || (((uintptr_t)rhos[i]) & 15))
+      return px::ctx_fail(c, PX_EINVAL, "instance fields must be 16-byte aligned");
+    const uintptr_t a = (uintptr_t)phis[i], r = (uintptr_t)rhos[i];
+    if (a < r + span && r < a + span) return px::ctx_fail(c, PX_EINVAL, "phi overlaps rho");
+  }
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != c->device) cudaSetDevice(c->device);
+  struct Restore { int p, d; ~Restore() { if (p >= 0 && p != d) cudaSetDevice(p); } } rs{prev, c->device};
+  cudaStream_t st = (cudaStream_t)stream;
+  // The previous run may still read the pinned table: wait for it first.
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+    px::BInst I = b->inst[i];
+    I.phi = phis[i];
+    I.rho = rhos[i];
+    I.resid = (resid_dev && b->nrep) ? resid_dev + (size_t)i * b->nrep : nullptr;
+    b->inst_pinned[i] = I;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->inst_dev, b->inst_pinned, b->n * sizeof(px::BInst),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && resid_dev && b->nrep)
+    e = cudaMemsetAsync(resid_dev, 0, (size_t)b->n * b->nrep * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return px::ctx_fail(c, PX_ECUDA, (std::string("batch run: ") + cudaGetErrorString(e)).c_str());
+  }
+  return PX_OK;
+}
+
+const char* px_batch_describe(const px_batch* b) { return b ? b->desc.c_str() : ""; }
+
+px_status px_batch_destroy(px_batch* b) {
+  if (!b) return PX_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != b->ctx->device) cudaSetDevice(b->ctx->device);
+  cudaDeviceSynchronize();
+  const int dev = b->ctx->device;
+  destroy_batch(b);
+  if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+  return PX_OK;
+}
+
+}  // extern "C"

@@ -115,8 +115,22 @@ cudaError_t launch_field_sum(const FieldDesc& f, const void* a, double* partials
 
 }  // namespace px
 
+#include <string>
 #include <vector>
 #include "../../include/protox.h"
+
+// The library context (opaque in the C ABI).
+struct px_ctx {
+  int device = 0;
+  void* scratch = nullptr;   // ping-pong field buffer
+  size_t scratch_bytes = 0;
+  double* red = nullptr;     // device aux block: [0,1] norms, [2] scale, [3] sum, [8..] partials
+  double* red_host = nullptr;  // pinned mirror of red[0..3]
+  void* ws = nullptr;        // solve workspace: FP32 r and e fields
+  size_t ws_bytes = 0;
+  std::string err;
+};
+
 
 namespace px {
 
@@ -128,5 +142,37 @@ size_t field_bytes(const FieldDesc& f);
 bool ranges_overlap(const void* a, const void* b, size_t n);
 std::vector<int> plan_relax_launches(const FieldDesc& f, bool vec, bool inplace, int nsweeps,
                                      int tblock, bool* copy_first);
+// Error reporting and grid validation on a context (api.cu).
+px_status ctx_fail(px_ctx* c, px_status st, const char* msg);
+px_status ctx_check_grid(px_ctx* c, const px_grid* g, FieldDesc* f);
+
+// Batched persistent kernel (batch.cu).
+enum { MODE_WHOLE = 0, MODE_BANDED = 1 };
+
+struct BInst {
+  void* phi;
+  const void* rho;
+  void* scratch;  // BANDED ping-pong partner
+  int nx, ny;
+  int64_t ld;
+  int dtype, mode, ry, pad;
+  double c, ih2;
+  double* resid;  // this instance's reports, or null
+};
+
+struct BParams {
+  BInst* inst;
+  const int* cl_off;
+  const int* cl_items;
+  const int* cta_off;
+  const int* cta_items;
+  int nsweeps, every;
+};
+
+size_t whole_bytes(int nx, int ny, int dtype);
+cudaError_t batch_max_clusters(int* n, size_t smem);
+cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStream_t st);
+int batch_cluster_size();
+size_t batch_whole_smem();
 
 }  // namespace px

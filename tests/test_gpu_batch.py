@@ -1,0 +1,158 @@
+"""GPU parity of the batched persistent relaxation (px_batch_plan / px_batch_run)
+against the FP64 oracle, instance by instance, through the C ABI.
+
+Each instance of a batch is an independent problem, so the oracle of a batch
+is oracle.relax_n per instance. Tolerances are those of the single-grid tests:
+FP64 n * 1e-12 relative, FP32 n * 2e-6 (inputs rounded to FP32 on both sides).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OMEGA = 2.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def px():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as m
+    return m
+
+
+def make_instances(specs, seed):
+    rng = np.random.default_rng(seed)
+    phis, rhos, host = [], [], []
+    for (nx, ny, dt) in specs:
+        tdt = torch.float64 if dt == "f64" else torch.float32
+        rho = synth.random_field(rng, nx, ny)
+        phi = synth.random_field(rng, nx, ny, zero_mean=False)
+        if dt == "f32":
+            rho = rho.astype(np.float32).astype(np.float64)
+            phi = phi.astype(np.float32).astype(np.float64)
+        rhos.append(torch.from_numpy(rho).to(tdt).cuda())
+        phis.append(torch.from_numpy(phi).to(tdt).cuda())
+        host.append((phi, rho))
+    return phis, rhos, host
+
+
+def check(specs, phis, host, resid, nsweeps, every):
+    nrep = (nsweeps + every - 1) // every
+    res = resid.cpu().numpy().reshape(len(specs), nrep)
+    for i, ((nx, ny, dt), (phi0, rho)) in enumerate(zip(specs, host)):
+        h = 1.0 / nx
+        ref, R = oracle.relax_n(phi0, rho, h, OMEGA, nsweeps, every)
+        got = phis[i].double().cpu().numpy()
+        tol = nsweeps * (1e-12 if dt == "f64" else 2e-6)
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err <= tol, (i, nx, ny, dt, err)
+        sc = 8 * max(np.max(np.abs(ref)), np.max(np.abs(phi0))) / h**2 + np.max(np.abs(rho))
+        assert np.max(np.abs(res[i] - R)) <= tol * sc, (i, nx, ny, dt)
+
+
+SPECS = [(32, 32, "f32"), (48, 48, "f64"), (64, 64, "f32"), (96, 96, "f64"), (128, 128, "f32"),
+         (160, 160, "f32"), (112, 112, "f64"), (128, 128, "f64"), (256, 256, "f32"),
+         (80, 48, "f32"), (512, 512, "f64"), (48, 96, "f64"), (1024, 64, "f32")]
+
+
+@pytest.mark.parametrize("nsweeps", [7, 12])
+def test_mixed_batch_matches_oracle(px, nsweeps):
+    every = 2
+    b = px.Batch([px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+                  for nx, ny, dt in SPECS], nsweeps, OMEGA, every)
+    d = b.describe()
+    modes = {k: v["mode"] for k, v in d["classes"].items()}
+    assert modes["f32:32x32"] == "whole" and modes["f64:512x512"] == "banded"
+    nrep = (nsweeps + every - 1) // every
+    for rep in range(2):  # the graph is replayed with new data
+        phis, rhos, host = make_instances(SPECS, 100 * nsweeps + rep)
+        resid = torch.full((len(SPECS) * nrep,), -1.0, dtype=torch.float64, device="cuda")
+        b.run(phis, rhos, resid)
+        torch.cuda.synchronize()
+        check(SPECS, phis, host, resid, nsweeps, every)
+    b.close()
+
+
+def test_autotune_cache_roundtrip(px, tmp_path):
+    specs = [(64, 64, "f32"), (96, 96, "f64"), (256, 256, "f32"), (256, 256, "f64")]
+    grids = [px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+             for nx, ny, dt in specs]
+    cache = str(tmp_path / "tune.json")
+    b = px.Batch(grids, 10, OMEGA, 0, tune_cache=cache, tune=True)
+    d = b.describe()
+    assert all(v["tuned"] for v in d["classes"].values())
+    assert all(v["rate_per_sm"] > 0 for v in d["classes"].values())
+    data = json.load(open(cache))
+    assert data["gpu"] == torch.cuda.get_device_name(0)
+    assert set(data["classes"]) == set(d["classes"])
+    # second plan reads the cache (no measurement) and runs correctly
+    b2 = px.Batch(grids, 10, OMEGA, 1, tune_cache=cache, tune=False)
+    d2 = b2.describe()
+    for k, v in d2["classes"].items():
+        assert v["tuned"] and v["mode"] == d["classes"][k]["mode"]
+    phis, rhos, host = make_instances(specs, 5)
+    resid = torch.zeros(len(specs) * 10, dtype=torch.float64, device="cuda")
+    b2.run(phis, rhos, resid)
+    torch.cuda.synchronize()
+    check(specs, phis, host, resid, 10, 1)
+    b.close()
+    b2.close()
+
+
+def test_batch_rejects_unsupported_layouts(px):
+    with pytest.raises(px.PxError) as ei:
+        px.Batch([px.Grid(30, 30, 30, 0, px.PX_F32, 1 / 30)], 4)
+    assert ei.value.status == px.PX_EUNSUPPORTED
+    with pytest.raises(px.PxError) as ei:
+        px.Batch([px.Grid(32, 32, 34, 1, px.PX_F32, 1 / 32)], 4)
+    assert ei.value.status == px.PX_EUNSUPPORTED
+
+
+def test_batched_workload_full_size(px):
+    """1024 instances, N = 16 j (32..1024) log-uniform, FP64/FP32 by coin,
+    8 modes each, 300 sweeps, one persistent launch. Every instance's state-0
+    report is max|rho| exactly; a sample of instances (the largest of each
+    dtype and small ones) is checked against the oracle."""
+    ns, dts = synth.batch_sizes(1024)
+    specs, phis, rhos, hostr = [], [], [], []
+    for i, (n, dt) in enumerate(zip(ns, dts)):
+        n = int(n)
+        tdt = torch.float64 if dt == 0 else torch.float32
+        rho = synth.batch_rho(n, i)
+        r_t = torch.from_numpy(rho).to(tdt).cuda()
+        specs.append((n, n, "f64" if dt == 0 else "f32"))
+        rhos.append(r_t)
+        phis.append(torch.zeros_like(r_t))
+        hostr.append(rho if dt == 0 else rho.astype(np.float32).astype(np.float64))
+    grids = [px.Grid(n, n, n, 0, px.PX_F64 if d == "f64" else px.PX_F32, 1.0 / n)
+             for n, _, d in specs]
+    b = px.Batch(grids, 300, OMEGA, 100)
+    resid = torch.zeros(1024 * 3, dtype=torch.float64, device="cuda")
+    b.run(phis, rhos, resid)
+    torch.cuda.synchronize()
+    res = resid.cpu().numpy().reshape(1024, 3)
+    for i in range(1024):
+        assert res[i, 0] == np.max(np.abs(hostr[i]))
+    pick = set()
+    for d in ("f64", "f32"):
+        idx = [i for i, s in enumerate(specs) if s[2] == d]
+        idx.sort(key=lambda i: specs[i][0])
+        pick.update([idx[-1], idx[0], idx[len(idx) // 2]])
+    for i in sorted(pick):
+        n, _, d = specs[i]
+        h = 1.0 / n
+        ref, R = oracle.relax_n(np.zeros_like(hostr[i]), hostr[i], h, OMEGA, 300, 100)
+        got = phis[i].double().cpu().numpy()
+        tol = 300 * (1e-12 if d == "f64" else 2e-6)
+        assert np.max(np.abs(got - ref)) <= tol * np.max(np.abs(ref)), (i, n, d)
+        sc = 8 * np.max(np.abs(ref)) / h**2 + np.max(np.abs(hostr[i]))
+        assert np.max(np.abs(res[i] - R)) <= tol * sc, (i, n, d)
+    b.close()
