@@ -32,6 +32,7 @@ METRIC = "fused Jacobi GLUP/s & HBM roofline %; time-to-1e-8 residual vs plain F
 UNIT = "GLUP/s"
 N_DEFAULT = 16384
 SWEEPS = 200
+BATCH_SWEEPS = 300  # sweeps per instance of the batched workload
 OMEGA = 2.0 / 3.0
 ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cell per launch
 # DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
@@ -218,6 +219,81 @@ def time_variant(px, torch, phi0, out, rho, resid, h, tblock, steps, warmup, eve
     return [a.elapsed_time(b) / 1000.0 for a, b in evs]
 
 
+def bench_batched(px, torch, steps: int, warmup: int):
+    """1024 uneven instances (N = 16 j, 32..1024, log-uniform; FP64/FP32 by coin;
+    8 modes each), 300 sweeps each, one persistent launch per step, tuned per size
+    class (tuning time reported separately)."""
+    import tempfile
+    import synth
+    ns, dts = synth.batch_sizes(1024)
+    phis, rhos, grids = [], [], []
+    cells = {0: 0, 1: 0}
+    for i, (n, dt) in enumerate(zip(ns, dts)):
+        n = int(n)
+        tdt = torch.float64 if dt == 0 else torch.float32
+        r = torch.from_numpy(synth.batch_rho(n, i)).to(tdt).cuda()
+        rhos.append(r)
+        phis.append(torch.zeros_like(r))
+        grids.append(px.Grid(n, n, n, 0, px.PX_F64 if dt == 0 else px.PX_F32, 1.0 / n))
+        cells[int(dt)] += n * n
+    cache = os.path.join(tempfile.gettempdir(), "protox_batch_tune.json")
+    t0 = time.perf_counter()
+    b = px.Batch(grids, BATCH_SWEEPS, OMEGA, 0, tune_cache=cache, tune=True)
+    plan_s = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    for _ in range(max(1, min(warmup, 2))):
+        b.run(phis, rhos)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(max(1, min(steps, 3))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        b.run(phis, rhos)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1000.0)
+    t = statistics.median(ts)
+    d = b.describe()
+    b.close()
+    total = (cells[0] + cells[1]) * (BATCH_SWEEPS)
+    whole = sum(v["count"] for v in d["classes"].values() if v["mode"] == "whole")
+    return {"instances": 1024, "sweeps": BATCH_SWEEPS, "cells": cells[0] + cells[1],
+            "fp64_cells": cells[0], "fp32_cells": cells[1], "ms": 1000 * t,
+            "GLUP_s": total / t / 1e9, "launches_per_step": 1,
+            "whole_instances": whole, "banded_instances": 1024 - whole,
+            "clusters": d["clusters"], "predicted_ms": d["predicted_ms"],
+            "plan_and_tune_s": plan_s,
+            "fp64_bound_ms": 1000 * cells[0] * (BATCH_SWEEPS) * 6 / 0.555e12,
+            "note": "FP64 instances are bound by the FP64 pipe (6 ops/update at 0.555e12/s)"}
+
+
+def bench_time_to_tol(px, torch, rtol: float = 1e-8):
+    """Wall time to ||rho - L phi|| <= rtol ||rho|| on one 256^2 learned-guess field
+    (1-32 modes k,l <= 32 plus 0-4 Gaussian blobs), from phi0 = 0: plain FP64
+    sweeps vs FP32 sweeps inside FP64 refinement, both through px_solve."""
+    import synth
+    n = 256
+    rng = np.random.Generator(np.random.PCG64(synth.workload_seed(4)))
+    rho = synth.learned_guess_rho(rng, n)
+    r64 = torch.from_numpy(rho).cuda()
+    out = {"grid": n, "rtol": rtol, "field": "learned-guess recipe, seed 20230721, first draw"}
+    for key, mode, kw in (("plain_f64", "plain", {"check_every": 2000, "tblock": 1}),
+                          ("mixed", "refine", {"inner_sweeps": 2000, "tblock": 8})):
+        best = None
+        for _ in range(2):
+            phi = torch.zeros_like(r64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = px.solve(phi, r64, 1.0 / n, mode, rtol=rtol, max_sweeps=5 * 10**6, **kw)
+            wall = time.perf_counter() - t0
+            if best is None or wall < best[0]:
+                best = (wall, info)
+        out[key] = {"ms": 1000 * best[0], "sweeps": best[1]["sweeps"],
+                    "cycles": best[1]["cycles"], "rel_resid": best[1]["rel_resid"], **kw}
+    out["speedup_mixed_vs_plain_f64"] = out["plain_f64"]["ms"] / out["mixed"]["ms"]
+    return out
+
+
 def launches_per_step(tb):
     return (SWEEPS + tb - 1) // tb
 
@@ -319,6 +395,9 @@ def run_gpu(args, world, rank, local):
     h2d = 2 * cells * 4
     d2h = cells * 4 + SWEEPS * 8
 
+    batched = bench_batched(px, torch, K, W) if not args.quick else None
+    ttt = bench_time_to_tol(px, torch) if not args.quick else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(rho64, n, budget_s=args.cpu_budget)
@@ -357,6 +436,10 @@ def run_gpu(args, world, rank, local):
             "clocks": clk.summary(),
             "last_residual": {"state0": float(last_resid[0]), "state199": float(last_resid[-1])},
         }
+        if batched is not None:
+            line["batched"] = batched
+        if ttt is not None:
+            line["time_to_1e-8"] = ttt
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

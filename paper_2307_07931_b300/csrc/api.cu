@@ -439,6 +439,52 @@ extern "C" px_status px_solve(px_ctx* c, const px_grid* g, void* phi, const void
     e32 = (float*)((char*)c->ws + need / 2);
   }
 
+  // After one plain launch of a block (which allocates any scratch), a full
+  // block (PLAIN: check_every sweeps; REFINE: one cycle) is captured once on a
+  // private stream into a CUDA graph and replayed on the caller's stream.
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int blocks_done = 0;
+  struct GraphGuard {
+    cudaStream_t* s; cudaGraph_t* g; cudaGraphExec_t* x;
+    ~GraphGuard() {
+      if (*x) cudaGraphExecDestroy(*x);
+      if (*g) cudaGraphDestroy(*g);
+      if (*s) cudaStreamDestroy(*s);
+    }
+  } guard{&cap, &graph, &gexec};
+  const int full = o->mode == PX_SOLVE_PLAIN ? o->check_every : o->inner_sweeps;
+  auto enqueue_block = [&](cudaStream_t qs, int n) -> px_status {
+    if (o->mode == PX_SOLVE_PLAIN)
+      return px_relax_n(c, g, phi, phi, rho, o->omega, n, o->tblock, nullptr, 0, qs);
+    cudaError_t e = px::launch_refine_residual(f, phi, rho, c->red, r32, e32, ld32, c->red + 2, qs);
+    if (e != cudaSuccess) return cuda_fail(c, e, "refine residual");
+    px_status s2 = px_relax_n(c, &g32, e32, e32, r32, o->omega, n, o->tblock, nullptr, 0, qs);
+    if (s2 != PX_OK) return s2;
+    e = px::launch_refine_update(f, phi, e32, ld32, c->red + 2, qs);
+    return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "refine update");
+  };
+  auto run_block = [&](int n) -> px_status {
+    if (n != full || blocks_done == 0) {
+      ++blocks_done;
+      return enqueue_block(st, n);
+    }
+    if (!gexec) {
+      cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "solve graph capture");
+      px_status s2 = enqueue_block(cap, n);
+      e = cudaStreamEndCapture(cap, &graph);
+      if (s2 != PX_OK) return s2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "solve graph instantiate");
+    }
+    ++blocks_done;
+    cudaError_t e = cudaGraphLaunch(gexec, st);
+    return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "solve graph launch");
+  };
+
   const double inf_d = std::numeric_limits<double>::infinity();
   for (;;) {
     double R = 0, P = 0;
@@ -459,21 +505,10 @@ extern "C" px_status px_solve(px_ctx* c, const px_grid* g, void* phi, const void
         return finish(fail(c, PX_ETIMEOUT, "timeout after %.0f ms", ms));
     }
     const int64_t left = o->max_sweeps - inf.sweeps;
-    if (o->mode == PX_SOLVE_PLAIN) {
-      const int n = (int)std::min<int64_t>(o->check_every, left);
-      s = px_relax_n(c, g, phi, phi, rho, o->omega, n, o->tblock, nullptr, 0, stream);
-      if (s != PX_OK) return finish(s);
-      inf.sweeps += n;
-    } else {
-      const int n = (int)std::min<int64_t>(o->inner_sweeps, left);
-      cudaError_t e = px::launch_refine_residual(f, phi, rho, c->red, r32, e32, ld32, c->red + 2, st);
-      if (e != cudaSuccess) return finish(cuda_fail(c, e, "refine residual"));
-      s = px_relax_n(c, &g32, e32, e32, r32, o->omega, n, o->tblock, nullptr, 0, stream);
-      if (s != PX_OK) return finish(s);
-      e = px::launch_refine_update(f, phi, e32, ld32, c->red + 2, st);
-      if (e != cudaSuccess) return finish(cuda_fail(c, e, "refine update"));
-      inf.sweeps += n;
-      inf.cycles++;
-    }
+    const int n = (int)std::min<int64_t>(full, left);
+    s = run_block(n);
+    if (s != PX_OK) return finish(s);
+    inf.sweeps += n;
+    if (o->mode == PX_SOLVE_REFINE) inf.cycles++;
   }
 }

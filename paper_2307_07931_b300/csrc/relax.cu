@@ -296,8 +296,11 @@ template <typename T, int V, bool kRep>
 cudaError_t launch_stream_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
                             Coef<T> k, double* slot, cudaStream_t st) {
   constexpr int SW = kWarp * V;
-  const int ry = 32;
   const int nstrips = (f.nx + SW - 1) / SW;
+  // Rows per warp task: 32 on large grids; fewer on small grids so that there
+  // are about four warp tasks per resident warp slot of the device.
+  const int64_t target = (int64_t)device_sm_count() * 32 * 4;
+  const int ry = (int)std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)f.ny * nstrips / target));
   const int nseg = (f.ny + ry - 1) / ry;
   const int64_t ntasks = (int64_t)nstrips * nseg;
   static int blocks_per_sm = 0;
@@ -531,8 +534,8 @@ cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, cons
   const int nstrips = (f.nx + G::OW - 1) / G::OW;
   const int64_t resident = (int64_t)occ * device_sm_count();
   // Segment height: minimise (waves of CTAs) x (steps per CTA).
-  static const int cand[] = {16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
-  int H = 16;
+  static const int cand[] = {8, 16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+  int H = 8;
   double best = 1e300;
   for (int h : cand) {
     const int64_t ctas = (int64_t)nstrips * ((f.ny + h - 1) / h);
