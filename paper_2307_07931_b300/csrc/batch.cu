@@ -8,7 +8,7 @@
 //  * WHOLE: one CTA holds the instance (both ping-pong copies) in shared
 //    memory and runs every sweep there; rho is read through the read-only
 //    cache. No global traffic per sweep.
-//  * BANDED: a thread-block cluster of kCluster CTAs shares the instance; CTA r
+//  * BANDED: a thread-block cluster of csize CTAs shares the instance; CTA r
 //    sweeps rows [r*band, (r+1)*band) from global memory (the instance stays
 //    L2-resident) with warps streaming 32*V-wide strips, and the cluster's
 //    hardware barrier separates sweeps. The caller's phi and a plan-owned
@@ -34,7 +34,7 @@ namespace cg = cooperative_groups;
 namespace px {
 
 constexpr int kBatchThreads = 512;
-constexpr int kCluster = 8;
+constexpr int kMaxCluster = 8;
 constexpr size_t kWholeSmem = 200 * 1024;  // shared bytes for WHOLE instances
 
 namespace {
@@ -135,7 +135,7 @@ template <typename T>
 __device__ void run_banded(const BInst& I, const BParams& p, cg::cluster_group& cl, int rank,
                            typename MaxBits<T>::type* red) {
   using MB = typename MaxBits<T>::type;
-  const int band = (I.ny + kCluster - 1) / kCluster;
+  const int band = (I.ny + p.csize - 1) / p.csize;
   const int ra = min(I.ny, rank * band), rb = min(I.ny, ra + band);
   const T c = (T)I.c, ih2 = (T)I.ih2;
   const T* rho = (const T*)I.rho;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_k(BParams p) {
   __shared__ uint32_t red32[kBatchThreads / 32];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int cid = blockIdx.x / kCluster;
+  const int cid = blockIdx.x / p.csize;
   for (int u = p.cl_off[cid]; u < p.cl_off[cid + 1]; ++u) {
     const BInst& I = p.inst[p.cl_items[u]];
     if (I.dtype == 0) run_banded<double>(I, p, cl, rank, red64);
@@ -243,9 +243,10 @@ cudaError_t batch_attr() {
   return cudaSuccess;
 }
 
-cudaError_t batch_max_clusters(int* n, size_t smem) {
+cudaError_t batch_max_clusters(int* n, size_t smem, int csize) {
   cudaError_t e0 = batch_attr();
   if (e0 != cudaSuccess) return e0;
+  const int kCluster = csize;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(kCluster * 256, 1, 1);
   cfg.blockDim = dim3(kBatchThreads, 1, 1);
@@ -261,6 +262,8 @@ cudaError_t batch_max_clusters(int* n, size_t smem) {
 }
 
 cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStream_t st) {
+  const int kCluster = p.csize;
+  if (kCluster < 1 || kCluster > kMaxCluster) return cudaErrorInvalidValue;
   if (smem > kWholeSmem) return cudaErrorInvalidValue;
   cudaError_t e0 = batch_attr();
   if (e0 != cudaSuccess) return e0;
@@ -279,7 +282,7 @@ cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStrea
   return cudaLaunchKernelEx(&cfg, batch_k, p);
 }
 
-int batch_cluster_size() { return kCluster; }
+int batch_max_cluster_size() { return kMaxCluster; }
 size_t batch_whole_smem() { return kWholeSmem; }
 
 }  // namespace px

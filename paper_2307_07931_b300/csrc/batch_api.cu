@@ -21,9 +21,9 @@ struct ClassCfg {
   bool tuned = false;
 };
 
-std::string class_key(int dtype, int nx, int ny) {
+std::string class_key(int dtype, int nx, int ny, int csize) {
   char b[64];
-  snprintf(b, sizeof b, "%s:%dx%d", dtype == PX_F64 ? "f64" : "f32", nx, ny);
+  snprintf(b, sizeof b, "%s:%dx%d@c%d", dtype == PX_F64 ? "f64" : "f32", nx, ny, csize);
   return b;
 }
 
@@ -122,7 +122,7 @@ namespace {
 // Measures one class on one representative instance: WHOLE (one CTA) and
 // BANDED (one cluster) with rows-per-task 4, 8, 16; keeps the fastest rate
 // per SM. Buffers are zero fields allocated for the measurement.
-px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double omega,
+px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double omega, int C,
                      ClassCfg* out) {
   const int64_t ld = nx;
   const size_t es = dtype == PX_F64 ? 8 : 4;
@@ -130,7 +130,6 @@ px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double om
   void *phi = nullptr, *rho = nullptr, *scr = nullptr, *idx = nullptr, *ins = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   px_status st = PX_OK;
-  const int C = px::batch_cluster_size();
   std::vector<std::pair<int, int>> cands;  // (mode, ry)
   if (fits_whole(nx, ny, dtype)) cands.push_back({px::MODE_WHOLE, 0});
   for (int ry : {4, 8, 16}) cands.push_back({px::MODE_BANDED, ry});
@@ -168,6 +167,7 @@ px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double om
     p.cta_items = (int*)idx + 4 + C;
     p.nsweeps = sweeps;
     p.every = 0;
+    p.csize = C;
     const size_t smem = band ? 0 : px::whole_bytes(nx, ny, dtype);
     e = px::batch_launch(p, 1, smem, 0);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
@@ -236,11 +236,9 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   b->omega = omega;
   b->nrep = report_every > 0 ? (nsweeps + report_every - 1) / report_every : 0;
   b->grids.assign(grids, grids + n);
-  const int C = px::batch_cluster_size();
 
-  // classes and their configuration
-  std::map<std::string, ClassCfg> cfg;
-  std::map<std::string, int> count;
+  // validate, and size the shared memory for every class that can run WHOLE
+  size_t smem = 0;
   for (int i = 0; i < n; ++i) {
     px::FieldDesc f;
     px_status s = px::ctx_check_grid(c, &grids[i], &f);
@@ -252,13 +250,34 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
                           "batched instances must be unghosted, non-empty, with nx and ld "
                           "multiples of 4 (FP32) or 2 (FP64)");
     }
-    const std::string k = class_key(f.dtype, f.nx, f.ny);
+    if (fits_whole(f.nx, f.ny, f.dtype)) smem = std::max(smem, px::whole_bytes(f.nx, f.ny, f.dtype));
+  }
+  smem = (smem + 1023) / 1024 * 1024;
+  // cluster size: the one whose resident clusters cover the most SMs (ties: larger)
+  int C = 0, ncl = 0;
+  for (int cs = px::batch_max_cluster_size(); cs >= 2; cs /= 2) {
+    int m = 0;
+    cudaError_t e = px::batch_max_clusters(&m, smem, cs);
+    if (e != cudaSuccess) { cudaGetLastError(); continue; }
+    if (m * cs > ncl * C) { C = cs; ncl = m; }
+  }
+  if (ncl < 1) {
+    destroy_batch(b);
+    return px::ctx_fail(c, PX_ECUDA, "no cluster of the batch kernel fits on this device");
+  }
+
+  // classes and their configuration
+  std::map<std::string, ClassCfg> cfg;
+  std::map<std::string, int> count;
+  for (int i = 0; i < n; ++i) {
+    const px_grid& g = grids[i];
+    const std::string k = class_key(g.dtype, g.nx, g.ny, C);
     count[k]++;
     if (!cfg.count(k)) {
       ClassCfg d;
-      d.mode = fits_whole(f.nx, f.ny, f.dtype) ? px::MODE_WHOLE : px::MODE_BANDED;
+      d.mode = fits_whole(g.nx, g.ny, g.dtype) ? px::MODE_WHOLE : px::MODE_BANDED;
       d.ry = 8;
-      d.rate_per_sm = default_rate(f.dtype, d.mode);
+      d.rate_per_sm = default_rate(g.dtype, d.mode);
       cfg[k] = d;
     }
   }
@@ -277,7 +296,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
       int nx = 0, ny = 0;
       sscanf(kv.first.c_str() + 4, "%dx%d", &nx, &ny);
       ClassCfg t;
-      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, &t);
+      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, C, &t);
       if (s != PX_OK) { destroy_batch(b); return s; }
       kv.second = t;
       cached[kv.first] = t;
@@ -286,19 +305,18 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   }
   if (tuned_now) save_cache(tune_cache, gpu, cached);
 
-  // resident clusters
-  size_t smem = 0;
+  // WHOLE classes decide the shared memory actually used (less is fine)
+  size_t used = 0;
   for (int i = 0; i < n; ++i) {
-    const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny)];
-    if (k.mode == px::MODE_WHOLE) smem = std::max(smem, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
+    const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
+    if (k.mode == px::MODE_WHOLE) used = std::max(used, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
   }
-  smem = (smem + 1023) / 1024 * 1024;
-  int ncl = 0;
-  cudaError_t e = px::batch_max_clusters(&ncl, smem);
-  if (e != cudaSuccess || ncl < 1) {
+  smem = (used + 1023) / 1024 * 1024;
+  {
+    int m = 0;
+    cudaError_t e = px::batch_max_clusters(&m, smem, C);
+    if (e == cudaSuccess && m > ncl) ncl = m;
     cudaGetLastError();
-    destroy_batch(b);
-    return px::ctx_fail(c, PX_ECUDA, "no cluster of the batch kernel fits on this device");
   }
   b->nclusters = ncl;
   b->smem = smem;
@@ -312,7 +330,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   b->inst.resize(n);
   for (int i = 0; i < n; ++i) {
     const px_grid& g = grids[i];
-    const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny)];
+    const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny, C)];
     px::BInst& I = b->inst[i];
     I = px::BInst{};
     I.nx = g.nx; I.ny = g.ny; I.ld = g.ld; I.dtype = g.dtype; I.mode = k.mode; I.ry = k.ry;
@@ -353,7 +371,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   for (int k = 0; k < ncl * C; ++k) ix.insert(ix.end(), cta_items[k].begin(), cta_items[k].end());
   ix.push_back(0);  // keep the arrays non-empty
 
-  e = cudaMalloc(&b->idx_dev, ix.size() * sizeof(int));
+  cudaError_t e = cudaMalloc(&b->idx_dev, ix.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(b->idx_dev, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&b->inst_dev, n * sizeof(px::BInst));
   if (e == cudaSuccess) e = cudaMallocHost(&b->inst_pinned, n * sizeof(px::BInst));
@@ -372,6 +390,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   b->params.cta_items = b->idx_dev + cta_items_at;
   b->params.nsweeps = nsweeps;
   b->params.every = report_every;
+  b->params.csize = C;
 
   // The launch is captured once into a graph; runs replay it.
   e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);

@@ -167,12 +167,13 @@ struct BParams {
   const int* cta_off;
   const int* cta_items;
   int nsweeps, every;
+  int csize;  // CTAs per cluster
 };
 
 size_t whole_bytes(int nx, int ny, int dtype);
-cudaError_t batch_max_clusters(int* n, size_t smem);
+cudaError_t batch_max_clusters(int* n, size_t smem, int csize);
 cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStream_t st);
-int batch_cluster_size();
+int batch_max_cluster_size();
 size_t batch_whole_smem();
 
 }  // namespace px

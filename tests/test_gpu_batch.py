@@ -69,7 +69,9 @@ def test_mixed_batch_matches_oracle(px, nsweeps):
     b = px.Batch([px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
                   for nx, ny, dt in SPECS], nsweeps, OMEGA, every)
     d = b.describe()
-    modes = {k: v["mode"] for k, v in d["classes"].items()}
+    modes = {k.split("@")[0]: v["mode"] for k, v in d["classes"].items()}
+    assert d["cluster_size"] in (2, 4, 8)
+    assert all(k.endswith(f"@c{d['cluster_size']}") for k in d["classes"])
     assert modes["f32:32x32"] == "whole" and modes["f64:512x512"] == "banded"
     nrep = (nsweeps + every - 1) // every
     for rep in range(2):  # the graph is replayed with new data
