@@ -250,6 +250,52 @@ px_status px_batch_run(px_batch* plan, void* const* phis, const void* const* rho
 const char* px_batch_describe(const px_batch* plan);
 px_status px_batch_destroy(px_batch* plan);
 
+/* ----------------------------------------------------------------------------
+ * Learned initial guess (the paper has no network; this supplies the starting
+ * state of the Sec. IV iteration). A 6-layer CNN of periodic 3x3 convolutions
+ * (cross-correlation, circular padding), widths 1-32-32-32-32-32-1, exact (erf)
+ * GELU after every layer but the last. BF16 weights and activations, FP32
+ * accumulation; the 32 -> 32 layers run on the tensor cores. Trained by MSE
+ * with Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights.
+ *
+ * Scaling: for an image rho with spacing h, s = max|rho h^2|, the network input
+ * is x = rho h^2 / s and its target is t = phi / s (phi the mean-zero solution);
+ * the guess is phi0 = s (y - mean(y)). The map rho -> phi is linear, so the
+ * scaling is exact.
+ *
+ * Images are B x H x W, row-major, x fastest; H a multiple of 4 and W a multiple
+ * of 64 (PX_EUNSUPPORTED otherwise). All image pointers are DEVICE pointers.
+ * Parameters (px_cnn_get/set_params) are the FP32 master weights in the order
+ * W1, b1, ..., W6, b6 with W_l of shape (Cout, Cin, 3, 3); px_cnn_param_count()
+ * floats. The network owns its weights, Adam state and activation workspace
+ * (grown on demand; a call that grows it synchronises the device).
+ */
+typedef struct px_cnn px_cnn;
+
+size_t px_cnn_param_count(void);
+/* He-normal weights (std sqrt(2 / (9 Cin))), zero biases, from `seed`. */
+px_status px_cnn_create(px_ctx* ctx, uint64_t seed, px_cnn** out);
+px_status px_cnn_destroy(px_cnn* net);
+px_status px_cnn_get_params(px_cnn* net, float* host, size_t count);
+px_status px_cnn_set_params(px_cnn* net, const float* host, size_t count);
+/* y (FP32, B x H x W) = network(x) for scaled inputs x (FP32). Asynchronous. */
+px_status px_cnn_forward(px_cnn* net, const float* x, float* y, int B, int H, int W, void* stream);
+/* Forward + backward of the MSE loss against t; gradients (FP32, parameter
+ * order) to grads_host and the loss to loss_host when not NULL (synchronises). */
+px_status px_cnn_grads(px_cnn* net, const float* x, const float* t, int B, int H, int W,
+                       float* grads_host, double* loss_host, void* stream);
+/* One Adam step of learning rate lr on the batch (x, t); loss_host as above. */
+px_status px_cnn_train_step(px_cnn* net, const float* x, const float* t, int B, int H, int W,
+                            float lr, double* loss_host, void* stream);
+/* Training pair from FP64 images: x = rho h^2 / s and, if phi is not NULL,
+ * t = phi / s; per-image s to scales_host when not NULL (synchronises). */
+px_status px_cnn_prepare(px_cnn* net, const double* rho, const double* phi, float* x, float* t,
+                         int B, int H, int W, double h, double* scales_host, void* stream);
+/* Initial guess phi0 (FP64) for FP64 right-hand sides rho: scale, network,
+ * unscale, subtract the mean. Asynchronous. */
+px_status px_cnn_guess(px_cnn* net, const double* rho, double* phi0, int B, int H, int W,
+                       double h, void* stream);
+
 /* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
  * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,
  * *rho_norm_host = ||rho||_inf. Evaluated in FP64 for both dtypes (FP32 fields

@@ -88,6 +88,21 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_batch_describe.argtypes = [_vp]
     lib.px_batch_describe.restype = ctypes.c_char_p
     lib.px_batch_destroy.argtypes = [_vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    lib.px_cnn_param_count.restype = ctypes.c_size_t
+    lib.px_cnn_create.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_vp)]
+    lib.px_cnn_destroy.argtypes = [_vp]
+    lib.px_cnn_get_params.argtypes = [_vp, fp, ctypes.c_size_t]
+    lib.px_cnn_set_params.argtypes = [_vp, fp, ctypes.c_size_t]
+    lib.px_cnn_forward.argtypes = [_vp, _vp, _vp, i, i, i, _vp]
+    lib.px_cnn_grads.argtypes = [_vp, _vp, _vp, i, i, i, fp, dp, _vp]
+    lib.px_cnn_train_step.argtypes = [_vp, _vp, _vp, i, i, i, ctypes.c_float, dp, _vp]
+    lib.px_cnn_prepare.argtypes = [_vp, _vp, _vp, _vp, _vp, i, i, i, d, dp, _vp]
+    lib.px_cnn_guess.argtypes = [_vp, _vp, _vp, i, i, i, d, _vp]
+    for name in ("px_cnn_create", "px_cnn_destroy", "px_cnn_get_params", "px_cnn_set_params",
+                 "px_cnn_forward", "px_cnn_grads", "px_cnn_train_step", "px_cnn_prepare",
+                 "px_cnn_guess"):
+        getattr(lib, name).restype = i
     lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
                              ctypes.POINTER(SolveInfo), _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
@@ -338,3 +353,93 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Cnn:
+    """The learned initial-guess network (px_cnn_*): 6 periodic 3x3 conv layers,
+    BF16 on the tensor cores, trained with Adam by the library's kernels.
+    Images are CUDA tensors (B, H, W); H % 4 == 0 and W % 64 == 0."""
+
+    def __init__(self, seed: int = 0, ctx: Context | None = None):
+        self.ctx = ctx or context()
+        h = _vp()
+        self.ctx.check(load_library().px_cnn_create(self.ctx.handle, int(seed), ctypes.byref(h)))
+        self.handle = h
+        self.nparams = int(load_library().px_cnn_param_count())
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.nparams, dtype=np.float32)
+        self.ctx.check(load_library().px_cnn_get_params(
+            self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.nparams))
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self.ctx.check(load_library().px_cnn_set_params(
+            self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.nparams))
+
+    def forward(self, x, y, stream=None):
+        B, H, W = x.shape
+        self.ctx.check(load_library().px_cnn_forward(self.handle, x.data_ptr(), y.data_ptr(),
+                                                     B, H, W, _stream(stream)))
+        return y
+
+    def grads(self, x, t, stream=None):
+        import numpy as np
+        B, H, W = x.shape
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        self.ctx.check(load_library().px_cnn_grads(
+            self.handle, x.data_ptr(), t.data_ptr(), B, H, W,
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss), _stream(stream)))
+        return g, loss.value
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True, stream=None):
+        B, H, W = x.shape
+        loss = ctypes.c_double()
+        self.ctx.check(load_library().px_cnn_train_step(
+            self.handle, x.data_ptr(), t.data_ptr(), B, H, W, float(lr),
+            ctypes.byref(loss) if want_loss else None, _stream(stream)))
+        return loss.value if want_loss else None
+
+    def prepare(self, rho, phi, x, t, h: float, stream=None):
+        import numpy as np
+        B, H, W = rho.shape
+        sc = np.empty(B, dtype=np.float64)
+        self.ctx.check(load_library().px_cnn_prepare(
+            self.handle, rho.data_ptr(), _ptr(phi), x.data_ptr(), _ptr(t), B, H, W, float(h),
+            sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
+        return sc
+
+    def guess(self, rho, phi0, h: float, stream=None):
+        B, H, W = rho.shape
+        self.ctx.check(load_library().px_cnn_guess(self.handle, rho.data_ptr(), phi0.data_ptr(),
+                                                   B, H, W, float(h), _stream(stream)))
+        return phi0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().px_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cnn_unflatten(p):
+    """Flat parameter vector -> [(W (Cout, Cin, 3, 3), b (Cout,))] per layer."""
+    import numpy as np
+    widths = (1, 32, 32, 32, 32, 32, 1)
+    out, o = [], 0
+    for cin, cout in zip(widths[:-1], widths[1:]):
+        w = np.asarray(p[o:o + cout * cin * 9]).reshape(cout, cin, 3, 3)
+        o += cout * cin * 9
+        b = np.asarray(p[o:o + cout])
+        o += cout
+        out.append((w, b))
+    return out

@@ -1,0 +1,956 @@
+// Learned initial guess: a 6-layer periodic 3x3 CNN (widths 1-32-32-32-32-32-1,
+// GELU after every layer but the last), BF16 weights and activations with FP32
+// accumulation, trained and run by the kernels in this file.
+//
+// Layout: activations NHWC BF16 with 32 channels (64 bytes per pixel); the
+// network input x and output y are single-channel FP32 images. Convolutions
+// are periodic cross-correlations: z[p][o] = b[o] + sum_{dy,dx,c} W[o][c][dy][dx]
+// x[p + (dy - 1, dx - 1)][c].
+//
+// The 32 -> 32 layers are implicit GEMMs on the tensor cores (mma.sync
+// m16n8k16, BF16 in, FP32 accumulate): M = pixels, N = 32 output channels,
+// K = 9 taps x 32 channels. A CTA of 4 warps owns a 4 x 64 output tile; its
+// input patch (6 x 66 pixels, periodic wrap in the loads) and the weight
+// matrix are staged in shared memory by cp.async with a 16-byte-chunk XOR
+// swizzle so that every ldmatrix is conflict-free. Epilogues are fused:
+// bias + GELU (forward, storing the pre-activation for the backward pass) or
+// the product with GELU'(z) of the previous layer (input gradient, which is
+// the same convolution with the weights flipped in both taps and transposed).
+// The weight gradient is a GEMM over pixels (M = 32, N = 288, K = pixels) on
+// the tensor cores as well, accumulated per CTA and reduced in a fixed order.
+// The 1 -> 32 and 32 -> 1 layers have 288 multiply-adds per pixel and run on
+// the CUDA cores.
+#include "px_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <random>
+#include <vector>
+
+namespace px {
+namespace cnn {
+
+constexpr int C = 32;            // channels of the hidden layers
+constexpr int K9 = 9 * C;        // GEMM K of a 32 -> 32 layer
+constexpr int TR = 4, TW = 64;   // output tile: rows x columns (one row per warp)
+constexpr int PR = TR + 2, PW = TW + 2;
+constexpr int WROWB = 592;       // bytes per weight row in shared memory (37 chunks)
+constexpr int kConvThreads = 128;
+constexpr size_t kPatchBytes = (size_t)PR * PW * 64;
+constexpr size_t kConvSmem = kPatchBytes + (size_t)C * WROWB;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Byte offset of (pixel, 16-byte channel chunk) in a swizzled [pixel][32 ch] tile:
+// chunk ^ ((pixel >> 1) & 3) keeps 8 consecutive pixels on 8 distinct bank groups.
+__device__ __forceinline__ int pix_off(int pix, int chunk) {
+  return pix * 64 + ((chunk ^ ((pix >> 1) & 3)) << 4);
+}
+
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// Stage the periodic input patch of an output tile: rows y0-1 .. y0+TR, columns
+// x0-1 .. x0+TW of image b, all 32 channels (4 chunks per pixel).
+__device__ __forceinline__ void load_patch(unsigned char* patch, const __nv_bfloat16* act, int b,
+                                           int y0, int x0, int H, int W) {
+  for (int q = threadIdx.x; q < PR * PW * 4; q += blockDim.x) {
+    const int chunk = q & 3, pix = q >> 2;
+    const int pr = pix / PW, pc = pix - pr * PW;
+    const int gy = wrapn(y0 - 1 + pr, H), gx = wrapn(x0 - 1 + pc, W);
+    const __nv_bfloat16* src = act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8;
+    cp16(patch + pix_off(pix, chunk), src);
+  }
+}
+
+// 32 -> 32 periodic convolution on the tensor cores.
+// kMode 0: forward, out = bias + conv, stores z (if zout) and gelu(z) into aout.
+// kMode 1: input gradient, aout = conv * gelu'(zprev) (weights pre-flipped/transposed).
+template <int kMode>
+__global__ void __launch_bounds__(kConvThreads)
+conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
+           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
+           __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
+           int tiles_x, int tiles_y) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* patch = sm;
+  unsigned char* wsm = sm + kPatchBytes;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x;
+  const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
+  const int x0 = tx * TW, y0 = ty * TR;
+
+  // weights [n][k] (k contiguous, 36 chunks per row, rows padded to 37 chunks)
+  for (int q = threadIdx.x; q < C * (K9 / 8); q += blockDim.x) {
+    const int n = q / (K9 / 8), kc = q - n * (K9 / 8);
+    cp16(wsm + n * WROWB + kc * 16, wk + (size_t)n * K9 + kc * 8);
+  }
+  load_patch(patch, in, b, y0, x0, H, W);
+  cp_wait();
+  __syncthreads();
+
+  float acc[4][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  const uint32_t pbase = smem_u32(patch), wbase = smem_u32(wsm);
+  // ldmatrix lane roles. A (x4): matrices (px 0-7, ch c), (px 8-15, ch c), (px 0-7, ch c+8),
+  // (px 8-15, ch c+8). B (x4): (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15).
+  const int a_px = (lane & 7) + ((lane >> 3) & 1) * 8;
+  const int a_ch = (lane >> 4);              // chunk offset 0/1 (x8 channels)
+  const int b_n = (lane & 7) + ((lane >> 4) << 3);
+  const int b_kc = (lane >> 3) & 1;
+
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {  // 16-channel halves of K within this tap
+      uint32_t bf[2][4];
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        const int n = np * 16 + b_n;
+        const int kchunk = tap * 4 + cc * 2 + b_kc;
+        ldsm4(bf[np], wbase + n * WROWB + kchunk * 16);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 4; ++mt) {
+        const int pix = (warp + dy) * PW + mt * 16 + a_px + dx;
+        uint32_t af[4];
+        ldsm4(af, pbase + pix_off(pix, cc * 2 + a_ch));
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          mma16816(acc[mt][np * 2 + 0], af, bf[np][0], bf[np][1]);
+          mma16816(acc[mt][np * 2 + 1], af, bf[np][2], bf[np][3]);
+        }
+      }
+    }
+  }
+
+  // epilogue: thread holds rows g, g+8 (pixels) and columns 2q, 2q+1 (channels)
+  const int g = lane >> 2, q = lane & 3;
+  const int y = y0 + warp;
+#pragma unroll
+  for (int mt = 0; mt < 4; ++mt) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int x = x0 + mt * 16 + g + half * 8;
+      const int64_t pbase_g = (((int64_t)b * H + y) * W + x) * C;
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        const int co = nt * 8 + 2 * q;
+        float v0 = acc[mt][nt][half * 2 + 0], v1 = acc[mt][nt][half * 2 + 1];
+        if (kMode == 0) {
+          v0 += bias[co];
+          v1 += bias[co + 1];
+          if (zout)
+            *reinterpret_cast<__nv_bfloat162*>(zout + pbase_g + co) = __floats2bfloat162_rn(v0, v1);
+          *reinterpret_cast<__nv_bfloat162*>(aout + pbase_g + co) =
+              __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+        } else {
+          const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162*>(zprev + pbase_g + co);
+          const float2 zf = __bfloat1622float2(zp);
+          *reinterpret_cast<__nv_bfloat162*>(aout + pbase_g + co) =
+              __floats2bfloat162_rn(v0 * gelu_grad_f(zf.x), v1 * gelu_grad_f(zf.y));
+        }
+      }
+    }
+  }
+}
+
+// Weight gradient of a 32 -> 32 layer on the tensor cores:
+//   dW[o][tap*32 + c] = sum_p dz[p][o] * in[p + tap][c],  db[o] = sum_p dz[p][o].
+// Persistent CTAs loop over 4 x 64 tiles and keep their partial sums in
+// registers; each CTA writes its partial (32 x 288 + 32 floats) to `part`.
+// Warp w owns output columns (n-tiles) 9w .. 9w+8 of the 36 (tap, 8-channel) tiles.
+__global__ void __launch_bounds__(kConvThreads)
+wgrad32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
+            float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  unsigned char* patch = sm;
+  unsigned char* dzs = sm + kPatchBytes;  // [TR*TW px][32 ch] swizzled
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float acc[2][9][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 9; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  float dbs = 0.f;  // thread t < 32 sums channel t
+  const uint32_t pbase = smem_u32(patch), dbase = smem_u32(dzs);
+  // A = dz^T (m = channel, k = pixel) via ldmatrix.trans of [px][ch]:
+  //   matrices (px 0-7, ch 0-7) (px 0-7, ch 8-15) (px 8-15, ch 0-7) (px 8-15, ch 8-15)
+  const int ta_px = (lane & 7) + (lane >> 4) * 8;
+  const int ta_ch = (lane >> 3) & 1;
+  // B = shifted input (k = pixel, n = channel) via ldmatrix.trans:
+  //   matrices (px 0-7, ch c) (px 8-15, ch c) (px 0-7, ch c+8) (px 8-15, ch c+8)
+  const int tb_px = (lane & 7) + ((lane >> 3) & 1) * 8;
+  const int tb_ch = lane >> 4;
+
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
+    const int x0 = tx * TW, y0 = ty * TR;
+    __syncthreads();  // previous tile's smem reads are done
+    load_patch(patch, in, b, y0, x0, H, W);
+    for (int qq = threadIdx.x; qq < TR * TW * 4; qq += blockDim.x) {
+      const int chunk = qq & 3, pix = qq >> 2;
+      const int r = pix / TW, c = pix - r * TW;
+      cp16(dzs + pix_off(pix, chunk), dz + (((int64_t)b * H + y0 + r) * W + x0 + c) * C + chunk * 8);
+    }
+    cp_wait();
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      for (int pix = 0; pix < TR * TW; ++pix) {
+        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(
+            dzs + pix_off(pix, threadIdx.x >> 3)) + (threadIdx.x & 7);
+        dbs += __bfloat162float(*p);
+      }
+    }
+#pragma unroll 1
+    for (int ks = 0; ks < TR * (TW / 16); ++ks) {  // 16 pixels per k-step
+      const int r = ks / (TW / 16), seg = ks - r * (TW / 16);
+      uint32_t af[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) {
+        const int pix = r * TW + seg * 16 + ta_px;
+        ldsm4t(af[mt], dbase + pix_off(pix, mt * 2 + ta_ch));
+      }
+#pragma unroll
+      for (int j = 0; j < 9; j += 2) {
+        // n-tiles nt = 9 warp + j (and + j + 1): tap = nt / 4, channel chunk8 = nt % 4
+        uint32_t bf[4];
+        const int nt0 = 9 * warp + j;
+        const int nt1 = (j + 1 < 9) ? nt0 + 1 : nt0;
+        // lanes 0-15 address n-tile nt0, lanes 16-31 n-tile nt1
+        const int nt = (lane < 16) ? nt0 : nt1;
+        const int tap = nt >> 2, c8 = nt & 3;
+        const int dy = tap / 3, dx = tap - dy * 3;
+        const int ppx = (r + dy) * PW + seg * 16 + dx + ((lane & 7) + ((lane >> 3) & 1) * 8);
+        ldsm4t(bf, pbase + pix_off(ppx, c8));
+        (void)tb_px; (void)tb_ch;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma16816(acc[mt][j], af[mt], bf[0], bf[1]);
+          if (j + 1 < 9) mma16816(acc[mt][j + 1], af[mt], bf[2], bf[3]);
+        }
+      }
+    }
+  }
+  // write the CTA partial: rows o (m), columns n = tap*32 + c
+  float* out = part + (size_t)blockIdx.x * (C * K9 + C);
+  const int g = lane >> 2, q = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int nt = 9 * warp + j;
+      const int col = nt * 8 + 2 * q;  // = tap*32 + c8*8 + 2q
+      out[(mt * 16 + g) * K9 + col] = acc[mt][j][0];
+      out[(mt * 16 + g) * K9 + col + 1] = acc[mt][j][1];
+      out[(mt * 16 + g + 8) * K9 + col] = acc[mt][j][2];
+      out[(mt * 16 + g + 8) * K9 + col + 1] = acc[mt][j][3];
+    }
+  if (threadIdx.x < 32) out[C * K9 + threadIdx.x] = dbs;
+}
+
+// First layer (1 -> 32) forward: z = b + sum_tap W1[o][tap] x[p + tap]; a = gelu(z).
+__global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
+                           const float* __restrict__ b1, __nv_bfloat16* __restrict__ zout,
+                           __nv_bfloat16* __restrict__ aout, int B, int H, int W) {
+  __shared__ float ws[C * 9 + C];
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w1[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) ws[C * 9 + i] = b1[i];
+  __syncthreads();
+  const int64_t n = (int64_t)B * H * W;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t img = p / ((int64_t)H * W);
+    float v[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int gy = wrap1(yy + tap / 3 - 1, H), gx = wrap1(xx + tap % 3 - 1, W);
+      v[tap] = x[(img * H + gy) * W + gx];
+    }
+    __nv_bfloat162 zz[C / 2], aa[C / 2];
+#pragma unroll
+    for (int o = 0; o < C; o += 2) {
+      float s0 = ws[C * 9 + o], s1 = ws[C * 9 + o + 1];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        s0 = fmaf(ws[o * 9 + tap], v[tap], s0);
+        s1 = fmaf(ws[(o + 1) * 9 + tap], v[tap], s1);
+      }
+      zz[o / 2] = __floats2bfloat162_rn(s0, s1);
+      aa[o / 2] = __floats2bfloat162_rn(gelu_f(s0), gelu_f(s1));
+    }
+    uint4* zo = reinterpret_cast<uint4*>(zout + p * C);
+    uint4* ao = reinterpret_cast<uint4*>(aout + p * C);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (zout) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
+      ao[k] = reinterpret_cast<const uint4*>(aa)[k];
+    }
+  }
+}
+
+__device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint4 u = q[k];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 t = __bfloat1622float2(h[e]);
+      f[k * 8 + 2 * e] = t.x;
+      f[k * 8 + 2 * e + 1] = t.y;
+    }
+  }
+}
+
+// Last layer (32 -> 1) forward: y = b6 + sum_{tap,c} W6[c][tap] a[p + tap][c] (FP32 out).
+__global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __restrict__ w6,
+                          const float* __restrict__ b6, float* __restrict__ y, int B, int H, int W) {
+  __shared__ float ws[C * 9];
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
+  __syncthreads();
+  const int64_t n = (int64_t)B * H * W;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t img = p / ((int64_t)H * W);
+    float s = b6[0];
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int gy = wrap1(yy + tap / 3 - 1, H), gx = wrap1(xx + tap % 3 - 1, W);
+      float f[C];
+      load_px32(f, a + ((img * H + gy) * W + gx) * C);
+#pragma unroll
+      for (int c = 0; c < C; ++c) s = fmaf(ws[c * 9 + tap], f[c], s);
+    }
+    y[p] = s;
+  }
+}
+
+// Loss: d[p] = y - t; per-block partial sums of d^2; dy = 2 d / n.
+__global__ void mse_grad(const float* __restrict__ y, const float* __restrict__ t,
+                         float* __restrict__ dy, double* __restrict__ part, int64_t n) {
+  double acc = 0.0;
+  const float inv = 2.0f / (float)n;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const float d = y[p] - t[p];
+    dy[p] = d * inv;
+    acc += (double)d * (double)d;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// Backward of the last layer: dz5[q][c] = gelu'(z5[q][c]) * sum_tap W6[c][tap] dy[q - tap].
+__global__ void back_last(const float* __restrict__ dy, const float* __restrict__ w6,
+                          const __nv_bfloat16* __restrict__ z5, __nv_bfloat16* __restrict__ dz5,
+                          int B, int H, int W) {
+  __shared__ float ws[C * 9];
+  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
+  __syncthreads();
+  const int64_t n = (int64_t)B * H * W;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t img = p / ((int64_t)H * W);
+    float g[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int gy = wrap1(yy - (tap / 3 - 1), H), gx = wrap1(xx - (tap % 3 - 1), W);
+      g[tap] = dy[(img * H + gy) * W + gx];
+    }
+    float z[C];
+    load_px32(z, z5 + p * C);
+    __nv_bfloat162 o[C / 2];
+#pragma unroll
+    for (int c = 0; c < C; c += 2) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        s0 = fmaf(ws[c * 9 + tap], g[tap], s0);
+        s1 = fmaf(ws[(c + 1) * 9 + tap], g[tap], s1);
+      }
+      o[c / 2] = __floats2bfloat162_rn(s0 * gelu_grad_f(z[c]), s1 * gelu_grad_f(z[c + 1]));
+    }
+    uint4* out = reinterpret_cast<uint4*>(dz5 + p * C);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[k] = reinterpret_cast<const uint4*>(o)[k];
+  }
+}
+
+// Weight gradient of a single-channel side (first and last layers):
+//   mode 0 (first): dW1[o][tap] = sum_p g32[p][o] * s1[p + tap],   db1[o] = sum_p g32[p][o]
+//   mode 1 (last):  dW6[c][tap] = sum_p s1[p] * g32[p + tap][c],   db6    = sum_p s1[p]
+// One CTA of 288 threads per group of pixels; thread (c, tap). Partials per CTA.
+template <int kMode>
+__global__ void __launch_bounds__(288)
+wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1,
+             float* __restrict__ part, int B, int H, int W, int px_per_cta) {
+  const int c = threadIdx.x / 9, tap = threadIdx.x % 9;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int64_t n = (int64_t)B * H * W;
+  const int64_t p0 = (int64_t)blockIdx.x * px_per_cta;
+  const int64_t p1 = std::min<int64_t>(n, p0 + px_per_cta);
+  float acc = 0.f, accb = 0.f;
+  for (int64_t p = p0; p < p1; ++p) {
+    const int xx = (int)(p % W), yy = (int)((p / W) % H);
+    const int64_t img = p / ((int64_t)H * W);
+    const int64_t ps = (img * H + wrap1(yy + dy, H)) * W + wrap1(xx + dx, W);
+    if (kMode == 0) {
+      const float gv = __bfloat162float(g32[p * C + c]);
+      acc = fmaf(gv, s1[ps], acc);
+      if (tap == 0) accb += gv;
+    } else {
+      const float sv = s1[p];
+      acc = fmaf(sv, __bfloat162float(g32[ps * C + c]), acc);
+      if (threadIdx.x == 0) accb += sv;
+    }
+  }
+  float* out = part + (size_t)blockIdx.x * (C * 9 + C);
+  out[c * 9 + tap] = acc;
+  if (kMode == 0 && tap == 0) out[C * 9 + c] = accb;
+  if (kMode == 1 && threadIdx.x == 0) out[C * 9] = accb;
+}
+
+// Sum partials over CTAs in index order (deterministic): dst[i] += sum_k part[k][i] * scale.
+__global__ void reduce_partials(const float* __restrict__ part, int nparts, int stride, int count,
+                                float* __restrict__ dst) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < nparts; ++k) s += part[(size_t)k * stride + i];
+    dst[i] = s;
+  }
+}
+
+// Adam on the flat FP32 parameter vector, then refresh the kernel-layout copies.
+__global__ void adam_update(float* __restrict__ p, const float* __restrict__ g,
+                            float* __restrict__ m, float* __restrict__ v, int n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// Kernel-layout weights of a 32 -> 32 layer from the FP32 (o, c, dy, dx) tensor:
+// fwd[o][tap*32 + c] = W[o][c][tap]; bwd[c][tap*32 + o] = W[o][c][8 - tap].
+__global__ void pack_weights(const float* __restrict__ Wt, __nv_bfloat16* __restrict__ fwd,
+                             __nv_bfloat16* __restrict__ bwd) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C * C * 9; i += gridDim.x * blockDim.x) {
+    const int o = i / (C * 9), c = (i / 9) % C, tap = i % 9;
+    const __nv_bfloat16 w = __float2bfloat16_rn(Wt[i]);
+    fwd[o * K9 + tap * C + c] = w;
+    bwd[c * K9 + (8 - tap) * C + o] = w;
+  }
+}
+
+// Per-image scaling of the network input and of the returned guess.
+//   prepare: s = max|rho h^2| (per image), x = rho h^2 / s (FP32), optional t = phi / s.
+//   finish:  phi0 = s (y - mean(y)).
+__global__ void prepare_images(const double* __restrict__ rho, const double* __restrict__ phi,
+                               float* __restrict__ x, float* __restrict__ t,
+                               double* __restrict__ scale, int H, int W, double h2) {
+  const int img = blockIdx.x;
+  const int64_t n = (int64_t)H * W, off = (int64_t)img * n;
+  uint64_t mx = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = umax(mx, absbits(rho[off + i] * h2));
+  __shared__ uint64_t sm[32];
+  mx = warp_max(mx);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = umax(m, sm[w]);
+    double s = __longlong_as_double((long long)m);
+    if (!(s > 0.0)) s = 1.0;
+    scale[img] = s;
+    sm[0] = (uint64_t)__double_as_longlong(s);
+  }
+  __syncthreads();
+  const double s = __longlong_as_double((long long)sm[0]);
+  const double is = 1.0 / s;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    x[off + i] = (float)(rho[off + i] * h2 * is);
+    if (t) t[off + i] = (float)(phi[off + i] * is);
+  }
+}
+
+__global__ void finish_images(const float* __restrict__ y, const double* __restrict__ scale,
+                              double* __restrict__ phi0, int H, int W) {
+  const int img = blockIdx.x;
+  const int64_t n = (int64_t)H * W, off = (int64_t)img * n;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += (double)y[off + i];
+  __shared__ double sh[1024];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double mean = sh[0] / (double)n;
+  const double s = scale[img];
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) phi0[off + i] = s * ((double)y[off + i] - mean);
+}
+
+}  // namespace cnn
+}  // namespace px
+
+namespace px {
+namespace cnn {
+// [o][tap*32 + c] partials (plus 32 bias sums) summed over CTAs in index order,
+// written as W[o][c][tap] and b[o].
+__global__ void reduce_w32(const float* __restrict__ part, int nparts, float* __restrict__ dw,
+                           float* __restrict__ db) {
+  const int stride = C * K9 + C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < stride; i += gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int k = 0; k < nparts; ++k) s += part[(size_t)k * stride + i];
+    if (i < C * K9) {
+      const int o = i / K9, rem = i - o * K9, tap = rem / C, c = rem - tap * C;
+      dw[o * K9 + c * 9 + tap] = s;
+    } else {
+      db[i - C * K9] = s;
+    }
+  }
+}
+}  // namespace cnn
+}  // namespace px
+
+// ---------------------------------------------------------------------------
+// Host side.
+namespace {
+
+using namespace px::cnn;
+constexpr int kLayers = 6;
+const int kWidth[kLayers + 1] = {1, 32, 32, 32, 32, 32, 1};
+
+struct Offsets {
+  size_t w[kLayers], b[kLayers], total;
+  Offsets() {
+    size_t o = 0;
+    for (int l = 0; l < kLayers; ++l) {
+      w[l] = o;
+      o += (size_t)kWidth[l + 1] * kWidth[l] * 9;
+      b[l] = o;
+      o += kWidth[l + 1];
+    }
+    total = o;
+  }
+};
+const Offsets kOff;
+
+int grid_1d(int64_t n, int threads) {
+  const int64_t cap = (int64_t)px::device_sm_count() * 16;
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, cap));
+}
+
+}  // namespace
+
+struct px_cnn {
+  px_ctx* ctx = nullptr;
+  float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16* wf[kLayers] = {};
+  __nv_bfloat16* wb[kLayers] = {};
+  int64_t step = 0;
+  int64_t cap_px = 0;
+  __nv_bfloat16* z[kLayers] = {};
+  __nv_bfloat16* a[kLayers] = {};
+  __nv_bfloat16 *g0 = nullptr, *g1 = nullptr;
+  float *y = nullptr, *dy = nullptr, *part = nullptr;
+  double* lpart = nullptr;
+  size_t part_floats = 0;
+  float *xb = nullptr, *tb = nullptr;
+  double* scales = nullptr;
+  double* lpart_host = nullptr;
+  int64_t cap_img = 0;
+};
+
+namespace {
+
+px_status cnn_cuda(px_cnn* n, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return px::ctx_fail(n ? n->ctx : nullptr, e == cudaErrorMemoryAllocation ? PX_ENOMEM : PX_ECUDA,
+                      m.c_str());
+}
+
+void free_work(px_cnn* n) {
+  for (int l = 0; l < kLayers; ++l) {
+    if (n->z[l]) cudaFree(n->z[l]);
+    if (n->a[l]) cudaFree(n->a[l]);
+    n->z[l] = n->a[l] = nullptr;
+  }
+  for (void* p : {(void*)n->g0, (void*)n->g1, (void*)n->y, (void*)n->dy, (void*)n->part,
+                  (void*)n->lpart, (void*)n->xb, (void*)n->tb, (void*)n->scales})
+    if (p) cudaFree(p);
+  n->g0 = n->g1 = nullptr;
+  n->y = n->dy = n->part = n->xb = n->tb = nullptr;
+  n->lpart = n->scales = nullptr;
+  n->cap_px = n->cap_img = 0;
+}
+
+// Workspace for B images of H x W: activations and pre-activations of layers
+// 1..5, two gradient buffers, output, loss and weight-gradient partials.
+px_status ensure_work(px_cnn* n, int64_t px, int64_t imgs) {
+  if (n->cap_px >= px && n->cap_img >= imgs) return PX_OK;
+  free_work(n);
+  const size_t act = (size_t)px * C * sizeof(__nv_bfloat16);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < 5 && e == cudaSuccess; ++l) {
+    e = cudaMalloc(&n->z[l], act);
+    if (e == cudaSuccess) e = cudaMalloc(&n->a[l], act);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&n->g0, act);
+  if (e == cudaSuccess) e = cudaMalloc(&n->g1, act);
+  if (e == cudaSuccess) e = cudaMalloc(&n->y, px * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->dy, px * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->xb, px * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->tb, px * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->scales, std::max<int64_t>(imgs, 1) * sizeof(double));
+  n->part_floats = (size_t)std::max(px::device_sm_count() * 4, 1024) * (C * K9 + C);
+  if (e == cudaSuccess) e = cudaMalloc(&n->part, n->part_floats * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->lpart, 4096 * sizeof(double));
+  if (e != cudaSuccess) {
+    free_work(n);
+    return cnn_cuda(n, e, "network workspace");
+  }
+  n->cap_px = px;
+  n->cap_img = imgs;
+  return PX_OK;
+}
+
+px_status repack(px_cnn* n, cudaStream_t st) {
+  for (int l = 1; l <= 4; ++l)
+    pack_weights<<<36, 256, 0, st>>>(n->params + kOff.w[l], n->wf[l], n->wb[l]);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "pack weights");
+}
+
+px_status check_shape(px_cnn* n, int B, int H, int W) {
+  if (B < 1 || H < 4 || W < 64 || H % TR || W % TW)
+    return px::ctx_fail(n->ctx, PX_EUNSUPPORTED,
+                        "network images need B >= 1, H a multiple of 4, W a multiple of 64");
+  return PX_OK;
+}
+
+px_status set_conv_attrs() {
+  static bool done = false;
+  if (done) return PX_OK;
+  cudaError_t e = cudaFuncSetAttribute(conv32_mma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kPatchBytes + TR * TW * 64));
+  if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
+  done = true;
+  return PX_OK;
+}
+
+// Forward pass into n->a / n->z (z only when training) and output y.
+px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool train,
+                  cudaStream_t st) {
+  const int64_t px = (int64_t)B * H * W;
+  const int tiles_x = W / TW, tiles_y = H / TR;
+  const int tiles = B * tiles_x * tiles_y;
+  conv_first<<<grid_1d(px, 256), 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
+                                               train ? n->z[0] : nullptr, n->a[0], B, H, W);
+  for (int l = 1; l <= 4; ++l)
+    conv32_mma<0><<<tiles, kConvThreads, kConvSmem, st>>>(
+        n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
+        n->a[l], H, W, tiles_x, tiles_y);
+  conv_last<<<grid_1d(px, 256), 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
+                                              n->params + kOff.b[5], y, B, H, W);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network forward");
+}
+
+// Forward + backward: gradients into n->grads, loss partials into n->lpart.
+px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, int* nloss,
+                cudaStream_t st) {
+  px_status s = forward(n, x, n->y, B, H, W, true, st);
+  if (s != PX_OK) return s;
+  const int64_t px = (int64_t)B * H * W;
+  const int tiles_x = W / TW, tiles_y = H / TR;
+  const int tiles = B * tiles_x * tiles_y;
+  const int lblocks = std::min<int64_t>(4096, grid_1d(px, 256));
+  mse_grad<<<lblocks, 256, 0, st>>>(n->y, t, n->dy, n->lpart, px);
+  *nloss = lblocks;
+  // last layer
+  const int spc = 4096;  // pixels per CTA of the single-channel weight gradients
+  const int nsc = (int)((px + spc - 1) / spc);
+  const int nsc_cap = (int)std::min<int64_t>(nsc, n->part_floats / (C * 9 + C));
+  const int spc_eff = (int)((px + nsc_cap - 1) / nsc_cap);
+  wgrad_single<1><<<nsc_cap, 288, 0, st>>>(n->a[4], n->dy, n->part, B, H, W, spc_eff);
+  reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
+  back_last<<<grid_1d(px, 256), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W);
+  __nv_bfloat16* gcur = n->g0;
+  __nv_bfloat16* gnext = n->g1;
+  const int wg_ctas = std::min(tiles, px::device_sm_count() * 4);
+  for (int l = 4; l >= 1; --l) {
+    wgrad32_mma<<<wg_ctas, kConvThreads, kPatchBytes + TR * TW * 64, st>>>(
+        n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles);
+    // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
+    reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
+    conv32_mma<1><<<tiles, kConvThreads, kConvSmem, st>>>(gcur, n->wb[l], nullptr, n->z[l - 1],
+                                                          nullptr, gnext, H, W, tiles_x, tiles_y);
+    std::swap(gcur, gnext);
+  }
+  wgrad_single<0><<<nsc_cap, 288, 0, st>>>(gcur, x, n->part, B, H, W, spc_eff);
+  reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network backward");
+}
+
+px_status read_loss(px_cnn* n, int nloss, int64_t px, double* loss, cudaStream_t st) {
+  std::vector<double> h(nloss);
+  cudaError_t e = cudaMemcpyAsync(h.data(), n->lpart, nloss * sizeof(double),
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cnn_cuda(n, e, "loss readback");
+  double s = 0.0;
+  for (double v : h) s += v;
+  *loss = s / (double)px;
+  return PX_OK;
+}
+
+struct DevScope {
+  int prev = -1, dev;
+  explicit DevScope(int d) : dev(d) {
+    cudaGetDevice(&prev);
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DevScope() { if (prev >= 0 && prev != dev) cudaSetDevice(prev); }
+};
+
+}  // namespace
+
+
+extern "C" {
+
+size_t px_cnn_param_count(void) { return kOff.total; }
+
+px_status px_cnn_create(px_ctx* c, uint64_t seed, px_cnn** out) {
+  if (!c || !out) return PX_EINVAL;
+  c->err.clear();
+  *out = nullptr;
+  DevScope ds(c->device);
+  if (set_conv_attrs() != PX_OK) return px::ctx_fail(c, PX_ECUDA, "conv kernel attributes");
+  px_cnn* n = new (std::nothrow) px_cnn();
+  if (!n) return px::ctx_fail(c, PX_ENOMEM, "host allocation failed");
+  n->ctx = c;
+  const size_t P = kOff.total;
+  cudaError_t e = cudaMalloc(&n->params, P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->grads, P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->m, P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&n->v, P * sizeof(float));
+  for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+    e = cudaMalloc(&n->wf[l], C * K9 * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&n->wb[l], C * K9 * sizeof(__nv_bfloat16));
+  }
+  if (e == cudaSuccess) e = cudaMemset(n->m, 0, P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->v, 0, P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->grads, 0, P * sizeof(float));
+  // He-normal initialisation (std sqrt(2 / (9 Cin))), zero biases; seeded.
+  std::vector<float> h(P, 0.0f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < kLayers; ++l) {
+    std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / (9.0 * kWidth[l])));
+    for (size_t i = 0; i < (size_t)kWidth[l + 1] * kWidth[l] * 9; ++i) h[kOff.w[l] + i] = (float)nd(rng);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(n->params, h.data(), P * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    px_status s = cnn_cuda(n, e, "network parameters");
+    px_cnn_destroy(n);
+    return s;
+  }
+  px_status s = repack(n, 0);
+  if (s == PX_OK && cudaDeviceSynchronize() != cudaSuccess) s = cnn_cuda(n, cudaGetLastError(), "pack");
+  if (s != PX_OK) { px_cnn_destroy(n); return s; }
+  *out = n;
+  return PX_OK;
+}
+
+px_status px_cnn_destroy(px_cnn* n) {
+  if (!n) return PX_OK;
+  DevScope ds(n->ctx->device);
+  cudaDeviceSynchronize();
+  free_work(n);
+  for (int l = 0; l < kLayers; ++l) {
+    if (n->wf[l]) cudaFree(n->wf[l]);
+    if (n->wb[l]) cudaFree(n->wb[l]);
+  }
+  for (void* p : {(void*)n->params, (void*)n->grads, (void*)n->m, (void*)n->v})
+    if (p) cudaFree(p);
+  delete n;
+  return PX_OK;
+}
+
+px_status px_cnn_get_params(px_cnn* n, float* host, size_t count) {
+  if (!n || !host || count != kOff.total) return PX_EINVAL;
+  DevScope ds(n->ctx->device);
+  cudaError_t e = cudaMemcpy(host, n->params, count * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "get params");
+}
+
+px_status px_cnn_set_params(px_cnn* n, const float* host, size_t count) {
+  if (!n || !host || count != kOff.total) return PX_EINVAL;
+  DevScope ds(n->ctx->device);
+  cudaError_t e = cudaMemcpy(n->params, host, count * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cnn_cuda(n, e, "set params");
+  px_status s = repack(n, 0);
+  if (s != PX_OK) return s;
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "set params");
+}
+
+px_status px_cnn_forward(px_cnn* n, const float* x, float* y, int B, int H, int W, void* stream) {
+  if (!n || !x || !y) return PX_EINVAL;
+  n->ctx->err.clear();
+  px_status s = check_shape(n, B, H, W);
+  if (s != PX_OK) return s;
+  DevScope ds(n->ctx->device);
+  s = ensure_work(n, (int64_t)B * H * W, B);
+  if (s != PX_OK) return s;
+  return forward(n, x, y, B, H, W, false, (cudaStream_t)stream);
+}
+
+px_status px_cnn_grads(px_cnn* n, const float* x, const float* t, int B, int H, int W,
+                       float* grads_host, double* loss_host, void* stream) {
+  if (!n || !x || !t) return PX_EINVAL;
+  n->ctx->err.clear();
+  px_status s = check_shape(n, B, H, W);
+  if (s != PX_OK) return s;
+  DevScope ds(n->ctx->device);
+  s = ensure_work(n, (int64_t)B * H * W, B);
+  if (s != PX_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nl = 0;
+  s = grads(n, x, t, B, H, W, &nl, st);
+  if (s != PX_OK) return s;
+  if (loss_host) {
+    s = read_loss(n, nl, (int64_t)B * H * W, loss_host, st);
+    if (s != PX_OK) return s;
+  }
+  if (grads_host) {
+    cudaError_t e = cudaMemcpyAsync(grads_host, n->grads, kOff.total * sizeof(float),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cnn_cuda(n, e, "grads readback");
+  }
+  return PX_OK;
+}
+
+px_status px_cnn_train_step(px_cnn* n, const float* x, const float* t, int B, int H, int W,
+                            float lr, double* loss_host, void* stream) {
+  if (!n || !x || !t || !(lr >= 0.0f)) return PX_EINVAL;
+  n->ctx->err.clear();
+  px_status s = check_shape(n, B, H, W);
+  if (s != PX_OK) return s;
+  DevScope ds(n->ctx->device);
+  s = ensure_work(n, (int64_t)B * H * W, B);
+  if (s != PX_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nl = 0;
+  s = grads(n, x, t, B, H, W, &nl, st);
+  if (s != PX_OK) return s;
+  n->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f - (float)std::pow(0.9, (double)n->step);
+  const float c2 = 1.0f - (float)std::pow(0.999, (double)n->step);
+  adam_update<<<64, 256, 0, st>>>(n->params, n->grads, n->m, n->v, (int)kOff.total, lr, b1, b2,
+                                  1e-8f, c1, c2);
+  s = repack(n, st);
+  if (s != PX_OK) return s;
+  if (loss_host) return read_loss(n, nl, (int64_t)B * H * W, loss_host, st);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "train step");
+}
+
+px_status px_cnn_prepare(px_cnn* n, const double* rho, const double* phi, float* x, float* t,
+                         int B, int H, int W, double h, double* scales_host, void* stream) {
+  if (!n || !rho || !x || (phi && !t) || !(h > 0)) return PX_EINVAL;
+  n->ctx->err.clear();
+  DevScope ds(n->ctx->device);
+  px_status s = ensure_work(n, (int64_t)B * H * W, B);
+  if (s != PX_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  prepare_images<<<B, 512, 0, st>>>(rho, phi, x, phi ? t : nullptr, n->scales, H, W, h * h);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && scales_host) {
+    e = cudaMemcpyAsync(scales_host, n->scales, B * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "prepare images");
+}
+
+px_status px_cnn_guess(px_cnn* n, const double* rho, double* phi0, int B, int H, int W, double h,
+                       void* stream) {
+  if (!n || !rho || !phi0 || !(h > 0)) return PX_EINVAL;
+  n->ctx->err.clear();
+  px_status s = check_shape(n, B, H, W);
+  if (s != PX_OK) return s;
+  DevScope ds(n->ctx->device);
+  s = ensure_work(n, (int64_t)B * H * W, B);
+  if (s != PX_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  prepare_images<<<B, 512, 0, st>>>(rho, nullptr, n->xb, nullptr, n->scales, H, W, h * h);
+  s = forward(n, n->xb, n->y, B, H, W, false, st);
+  if (s != PX_OK) return s;
+  finish_images<<<B, 1024, 0, st>>>(n->y, n->scales, phi0, H, W);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "guess");
+}
+
+}  // extern "C"
