@@ -259,9 +259,10 @@ px_status px_batch_destroy(px_batch* plan);
  * with Adam (beta 0.9 / 0.999, eps 1e-8) on FP32 master weights.
  *
  * Scaling: for an image rho with spacing h, s = max|rho h^2|, the network input
- * is x = rho h^2 / s and its target is t = phi / s (phi the mean-zero solution);
- * the guess is phi0 = s (y - mean(y)). The map rho -> phi is linear, so the
- * scaling is exact.
+ * is x = rho h^2 / s and its target is t = phi 4 pi^2 h^2 / s (phi the mean-zero
+ * solution; the factor makes the lowest mode of a unit-square field order one);
+ * the guess is phi0 = s / (4 pi^2 h^2) (y - mean(y)). The map rho -> phi is
+ * linear, so the scaling is exact.
  *
  * Images are B x H x W, row-major, x fastest; H a multiple of 4 and W a multiple
  * of 64 (PX_EUNSUPPORTED otherwise). All image pointers are DEVICE pointers.
@@ -288,7 +289,7 @@ px_status px_cnn_grads(px_cnn* net, const float* x, const float* t, int B, int H
 px_status px_cnn_train_step(px_cnn* net, const float* x, const float* t, int B, int H, int W,
                             float lr, double* loss_host, void* stream);
 /* Training pair from FP64 images: x = rho h^2 / s and, if phi is not NULL,
- * t = phi / s; per-image s to scales_host when not NULL (synchronises). */
+ * t = phi 4 pi^2 h^2 / s; per-image s to scales_host when not NULL (synchronises). */
 px_status px_cnn_prepare(px_cnn* net, const double* rho, const double* phi, float* x, float* t,
                          int B, int H, int W, double h, double* scales_host, void* stream);
 /* Initial guess phi0 (FP64) for FP64 right-hand sides rho: scale, network,

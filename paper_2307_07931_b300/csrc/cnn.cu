@@ -498,8 +498,11 @@ __global__ void pack_weights(const float* __restrict__ Wt, __nv_bfloat16* __rest
 }
 
 // Per-image scaling of the network input and of the returned guess.
-//   prepare: s = max|rho h^2| (per image), x = rho h^2 / s (FP32), optional t = phi / s.
-//   finish:  phi0 = s (y - mean(y)).
+//   prepare: s = max|rho h^2| (per image), x = rho h^2 / s (FP32), optional
+//            t = phi 4 pi^2 h^2 / s (the lowest mode of a unit-square field then
+//            has a target of order one);
+//   finish:  phi0 = s / (4 pi^2 h^2) (y - mean(y)).
+constexpr double kTargetScale = 39.478417604357434;  // 4 pi^2
 __global__ void prepare_images(const double* __restrict__ rho, const double* __restrict__ phi,
                                float* __restrict__ x, float* __restrict__ t,
                                double* __restrict__ scale, int H, int W, double h2) {
@@ -522,14 +525,15 @@ __global__ void prepare_images(const double* __restrict__ rho, const double* __r
   __syncthreads();
   const double s = __longlong_as_double((long long)sm[0]);
   const double is = 1.0 / s;
+  const double ts = kTargetScale * h2 * is;  // targets: phi * 4 pi^2 h^2 / s
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
     x[off + i] = (float)(rho[off + i] * h2 * is);
-    if (t) t[off + i] = (float)(phi[off + i] * is);
+    if (t) t[off + i] = (float)(phi[off + i] * ts);
   }
 }
 
 __global__ void finish_images(const float* __restrict__ y, const double* __restrict__ scale,
-                              double* __restrict__ phi0, int H, int W) {
+                              double* __restrict__ phi0, int H, int W, double h2) {
   const int img = blockIdx.x;
   const int64_t n = (int64_t)H * W, off = (int64_t)img * n;
   double acc = 0.0;
@@ -542,7 +546,7 @@ __global__ void finish_images(const float* __restrict__ y, const double* __restr
     __syncthreads();
   }
   const double mean = sh[0] / (double)n;
-  const double s = scale[img];
+  const double s = scale[img] / (kTargetScale * h2);
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) phi0[off + i] = s * ((double)y[off + i] - mean);
 }
 
@@ -948,7 +952,7 @@ px_status px_cnn_guess(px_cnn* n, const double* rho, double* phi0, int B, int H,
   prepare_images<<<B, 512, 0, st>>>(rho, nullptr, n->xb, nullptr, n->scales, H, W, h * h);
   s = forward(n, n->xb, n->y, B, H, W, false, st);
   if (s != PX_OK) return s;
-  finish_images<<<B, 1024, 0, st>>>(n->y, n->scales, phi0, H, W);
+  finish_images<<<B, 1024, 0, st>>>(n->y, n->scales, phi0, H, W, h * h);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "guess");
 }

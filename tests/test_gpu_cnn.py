@@ -100,8 +100,9 @@ def test_training_reduces_loss(px):
 
 
 def test_prepare_and_guess_scaling(px):
-    """x = rho h^2 / s, t = phi / s with s = max|rho h^2| per image, and
-    guess = s (y - mean y); the scaling arithmetic is checked in FP64 numpy."""
+    """x = rho h^2 / s, t = phi 4 pi^2 h^2 / s with s = max|rho h^2| per image,
+    and guess = s / (4 pi^2 h^2) (y - mean y); the scaling arithmetic is checked
+    in FP64 numpy."""
     B, H, W = 2, 16, 64
     h = 1.0 / W
     net = px.Cnn(seed=4)
@@ -116,14 +117,15 @@ def test_prepare_and_guess_scaling(px):
     assert np.array_equal(sc, s_ref)
     # one FP32 ulp: the kernel multiplies by 1/s where numpy divides by s
     assert np.allclose(x.cpu().numpy(), (rho * h * h / s_ref[:, None, None]).astype(np.float32), rtol=2.4e-7, atol=0)
-    assert np.allclose(t.cpu().numpy(), (phi / s_ref[:, None, None]).astype(np.float32), rtol=2.4e-7, atol=0)
+    ts = 4 * np.pi**2 * h * h
+    assert np.allclose(t.cpu().numpy(), (phi * ts / s_ref[:, None, None]).astype(np.float32), rtol=2.4e-7, atol=0)
     y = torch.empty_like(x)
     net.forward(x, y)
     g = torch.empty_like(r_t)
     net.guess(r_t, g, h)
     torch.cuda.synchronize()
     yy = y.cpu().numpy().astype(np.float64)
-    ref = s_ref[:, None, None] * (yy - yy.mean(axis=(1, 2), keepdims=True))
+    ref = (s_ref / ts)[:, None, None] * (yy - yy.mean(axis=(1, 2), keepdims=True))
     assert np.max(np.abs(g.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
     net.close()
 
