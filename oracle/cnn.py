@@ -7,9 +7,10 @@ small CNN maps the scaled right-hand side to an initial guess for the sweeps
 of Sec. IV. Definition (all FP64, NCHW numpy arrays):
   layer l: z = conv3x3_periodic(x, W_l) + b_l, x' = gelu(z) except after the
            last layer; widths 1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1;
-  conv3x3_periodic(x, W)[b, o, i, j] =
-      sum_{c, dy, dx} W[o, c, dy, dx] * x[b, c, (i + dy - 1) mod H, (j + dx - 1) mod W]
-  (cross-correlation with circular padding, the convention of conv2d);
+  conv3x3_periodic(x, W; d)[b, o, i, j] =
+      sum_{c, dy, dx} W[o, c, dy, dx] * x[b, c, (i + d(dy - 1)) mod H, (j + d(dx - 1)) mod W]
+  (cross-correlation with circular padding, the convention of conv2d; d is the
+  layer's dilation, 1 for a plain 3x3 layer);
   gelu(z) = z * Phi(z), Phi the standard normal CDF (erf form);
   loss = mean((y - t)^2) over all output elements;
   Adam with bias correction (beta1 0.9, beta2 0.999, eps 1e-8).
@@ -25,33 +26,34 @@ from scipy.special import erf
 WIDTHS = (1, 32, 32, 32, 32, 32, 1)
 
 
-def conv(x, W, b):
-    """Periodic 3x3 cross-correlation: x (B, Cin, H, W), W (Cout, Cin, 3, 3), b (Cout,)."""
+def conv(x, W, b, d=1):
+    """Periodic 3x3 cross-correlation with dilation d: x (B, Cin, H, W),
+    W (Cout, Cin, 3, 3), b (Cout,)."""
     B, _, H, Wd = x.shape
     out = np.zeros((B, W.shape[0], H, Wd))
     for dy in range(3):
         for dx in range(3):
-            xs = np.roll(x, shift=(-(dy - 1), -(dx - 1)), axis=(2, 3))
+            xs = np.roll(x, shift=(-(dy - 1) * d, -(dx - 1) * d), axis=(2, 3))
             out += np.einsum("bchw,oc->bohw", xs, W[:, :, dy, dx])
     return out + b[None, :, None, None]
 
 
-def conv_input_grad(g, W):
+def conv_input_grad(g, W, d=1):
     """d loss / d x of conv for upstream gradient g (B, Cout, H, W)."""
     out = np.zeros((g.shape[0], W.shape[1], g.shape[2], g.shape[3]))
     for dy in range(3):
         for dx in range(3):
             t = np.einsum("bohw,oc->bchw", g, W[:, :, dy, dx])
-            out += np.roll(t, shift=(dy - 1, dx - 1), axis=(2, 3))
+            out += np.roll(t, shift=((dy - 1) * d, (dx - 1) * d), axis=(2, 3))
     return out
 
 
-def conv_weight_grad(g, x):
+def conv_weight_grad(g, x, d=1):
     """(dW, db) of conv for upstream gradient g and input x."""
     dW = np.zeros((g.shape[1], x.shape[1], 3, 3))
     for dy in range(3):
         for dx in range(3):
-            xs = np.roll(x, shift=(-(dy - 1), -(dx - 1)), axis=(2, 3))
+            xs = np.roll(x, shift=(-(dy - 1) * d, -(dx - 1) * d), axis=(2, 3))
             dW[:, :, dy, dx] = np.einsum("bohw,bchw->oc", g, xs)
     return dW, g.sum(axis=(0, 2, 3))
 
@@ -73,12 +75,14 @@ def init_params(rng: np.random.Generator, widths=WIDTHS):
     return ps
 
 
-def forward(params, x):
-    """Returns (y, cache) with cache = per-layer (input, pre-activation)."""
+def forward(params, x, dil=None):
+    """Returns (y, cache) with cache = per-layer (input, pre-activation);
+    dil: per-layer dilations (default all 1)."""
+    dil = dil or (1,) * len(params)
     cache = []
     h = x
     for li, (W, b) in enumerate(params):
-        z = conv(h, W, b)
+        z = conv(h, W, b, dil[li])
         cache.append((h, z))
         h = gelu(z) if li < len(params) - 1 else z
     return h, cache
@@ -89,8 +93,9 @@ def mse(y, t):
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
-def backward(params, cache, dy):
+def backward(params, cache, dy, dil=None):
     """Gradients [(dW, db)] of the loss whose output gradient is dy."""
+    dil = dil or (1,) * len(params)
     grads = [None] * len(params)
     g = dy
     for li in range(len(params) - 1, -1, -1):
@@ -98,8 +103,8 @@ def backward(params, cache, dy):
         h, z = cache[li]
         if li < len(params) - 1:
             g = g * gelu_grad(z)
-        grads[li] = conv_weight_grad(g, h)
-        g = conv_input_grad(g, W)
+        grads[li] = conv_weight_grad(g, h, dil[li])
+        g = conv_input_grad(g, W, dil[li])
     return grads
 
 

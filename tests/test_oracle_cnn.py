@@ -19,6 +19,40 @@ def test_conv_matches_torch_circular():
     assert np.allclose(cnn.conv(x, W, b), ref, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("d", [2, 3, 5])
+def test_dilated_conv_matches_torch_circular(d):
+    rng = np.random.default_rng(d)
+    x = rng.standard_normal((2, 3, 16, 13))
+    W = rng.standard_normal((4, 3, 3, 3))
+    b = rng.standard_normal(4)
+    ref = F.conv2d(F.pad(torch.from_numpy(x), (d, d, d, d), mode="circular"),
+                   torch.from_numpy(W), torch.from_numpy(b), dilation=d).numpy()
+    assert np.allclose(cnn.conv(x, W, b, d), ref, rtol=0, atol=1e-12)
+
+
+def test_dilated_backward_matches_autograd():
+    rng = np.random.default_rng(4)
+    widths, dil = (1, 3, 3, 1), (1, 3, 2)
+    params = [(W, rng.standard_normal(b.shape) * 0.1) for W, b in cnn.init_params(rng, widths)]
+    x = rng.standard_normal((2, 1, 12, 12))
+    t = rng.standard_normal((2, 1, 12, 12))
+    y, cache = cnn.forward(params, x, dil)
+    L, dy = cnn.mse(y, t)
+    grads = cnn.backward(params, cache, dy, dil)
+    tp = [(torch.from_numpy(W).requires_grad_(True), torch.from_numpy(b).requires_grad_(True))
+          for W, b in params]
+    h = torch.from_numpy(x)
+    for li, (W, b) in enumerate(tp):
+        d = dil[li]
+        h = F.conv2d(F.pad(h, (d, d, d, d), mode="circular"), W, b, dilation=d)
+        if li < len(tp) - 1:
+            h = F.gelu(h)
+    ((h - torch.from_numpy(t)) ** 2).mean().backward()
+    for (dW, db), (W, b) in zip(grads, tp):
+        assert np.allclose(dW, W.grad.numpy(), rtol=1e-10, atol=1e-12)
+        assert np.allclose(db, b.grad.numpy(), rtol=1e-10, atol=1e-12)
+
+
 def test_gelu_matches_torch():
     z = np.linspace(-6, 6, 1001)
     ref = F.gelu(torch.from_numpy(z)).numpy()
@@ -88,7 +122,7 @@ def test_pins_catch_planted_mistakes(name, monkeypatch):
     """Plant a mistake in the oracle (CPU) and check a pin fails."""
     if name == "tap":
         orig = cnn.conv
-        monkeypatch.setattr(cnn, "conv", lambda x, W, b: orig(x, W[:, :, ::-1, :].copy(), b))
+        monkeypatch.setattr(cnn, "conv", lambda x, W, b, d=1: orig(x, W[:, :, ::-1, :].copy(), b, d))
         with pytest.raises(AssertionError):
             test_conv_matches_torch_circular()
     elif name == "gelu_prime":
@@ -97,8 +131,8 @@ def test_pins_catch_planted_mistakes(name, monkeypatch):
             test_backward_matches_autograd_and_finite_differences()
     else:
         orig = cnn.conv_weight_grad
-        def bad(g, x):
-            dW, db = orig(g, x)
+        def bad(g, x, d=1):
+            dW, db = orig(g, x, d)
             return dW[:, :, ::-1, ::-1].copy(), db
         monkeypatch.setattr(cnn, "conv_weight_grad", bad)
         with pytest.raises(AssertionError):
