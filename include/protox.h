@@ -274,8 +274,11 @@ px_status px_batch_destroy(px_batch* plan);
 typedef struct px_cnn px_cnn;
 
 size_t px_cnn_param_count(void);
-/* He-normal weights (std sqrt(2 / (9 Cin))), zero biases, from `seed`. */
-px_status px_cnn_create(px_ctx* ctx, uint64_t seed, px_cnn** out);
+/* He-normal weights (std sqrt(2 / (9 Cin))), zero biases, from `seed`.
+ * dilations: NULL (plain 3x3 layers) or 6 per-layer dilations d in 1..4096; a
+ * layer of dilation d reads x[p + d (dy - 1, dx - 1)], so dilations 1, 3, 9,
+ * 27, 81, 1 give a receptive field of 245 cells instead of 13. */
+px_status px_cnn_create(px_ctx* ctx, uint64_t seed, const int32_t* dilations, px_cnn** out);
 px_status px_cnn_destroy(px_cnn* net);
 px_status px_cnn_get_params(px_cnn* net, float* host, size_t count);
 px_status px_cnn_set_params(px_cnn* net, const float* host, size_t count);

@@ -90,7 +90,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_batch_destroy.argtypes = [_vp]
     fp = ctypes.POINTER(ctypes.c_float)
     lib.px_cnn_param_count.restype = ctypes.c_size_t
-    lib.px_cnn_create.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(_vp)]
+    lib.px_cnn_create.argtypes = [_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(_vp)]
     lib.px_cnn_destroy.argtypes = [_vp]
     lib.px_cnn_get_params.argtypes = [_vp, fp, ctypes.c_size_t]
     lib.px_cnn_set_params.argtypes = [_vp, fp, ctypes.c_size_t]
@@ -360,10 +361,13 @@ class Cnn:
     BF16 on the tensor cores, trained with Adam by the library's kernels.
     Images are CUDA tensors (B, H, W); H % 4 == 0 and W % 64 == 0."""
 
-    def __init__(self, seed: int = 0, ctx: Context | None = None):
+    def __init__(self, seed: int = 0, dilations=None, ctx: Context | None = None):
         self.ctx = ctx or context()
         h = _vp()
-        self.ctx.check(load_library().px_cnn_create(self.ctx.handle, int(seed), ctypes.byref(h)))
+        self.dilations = tuple(dilations) if dilations is not None else (1,) * 6
+        dil = (ctypes.c_int32 * 6)(*self.dilations)
+        self.ctx.check(load_library().px_cnn_create(self.ctx.handle, int(seed), dil,
+                                                    ctypes.byref(h)))
         self.handle = h
         self.nparams = int(load_library().px_cnn_param_count())
 

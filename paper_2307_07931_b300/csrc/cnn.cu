@@ -36,11 +36,11 @@ namespace cnn {
 constexpr int C = 32;            // channels of the hidden layers
 constexpr int K9 = 9 * C;        // GEMM K of a 32 -> 32 layer
 constexpr int TR = 4, TW = 64;   // output tile: rows x columns (one row per warp)
-constexpr int PR = TR + 2, PW = TW + 2;
 constexpr int WROWB = 592;       // bytes per weight row in shared memory (37 chunks)
 constexpr int kConvThreads = 128;
-constexpr size_t kPatchBytes = (size_t)PR * PW * 64;
-constexpr size_t kConvSmem = kPatchBytes + (size_t)C * WROWB;
+constexpr size_t kTileBytes = (size_t)TR * TW * 64;             // one [TR*TW px][32 ch] tile
+constexpr size_t kConvSmem = 2 * kTileBytes + (size_t)C * WROWB;  // tap double buffer + weights
+constexpr size_t kWgradSmem = 3 * kTileBytes;                     // dz tile + tap double buffer
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -49,6 +49,11 @@ __device__ __forceinline__ void cp16(void* s, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 __device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t addr) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -81,31 +86,34 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
          z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-// Stage the periodic input patch of an output tile: rows y0-1 .. y0+TR, columns
-// x0-1 .. x0+TW of image b, all 32 channels (4 chunks per pixel).
-__device__ __forceinline__ void load_patch(unsigned char* patch, const __nv_bfloat16* act, int b,
-                                           int y0, int x0, int H, int W) {
-  for (int q = threadIdx.x; q < PR * PW * 4; q += blockDim.x) {
+// Stage the input tile seen by one tap: pixels (y0 + r + oy, x0 + c + ox) of
+// image b for r < TR, c < TW, periodic, all 32 channels (4 chunks per pixel).
+__device__ __forceinline__ void load_tap_tile(unsigned char* dst, const __nv_bfloat16* act, int b,
+                                              int y0, int x0, int oy, int ox, int H, int W) {
+  for (int q = threadIdx.x; q < TR * TW * 4; q += blockDim.x) {
     const int chunk = q & 3, pix = q >> 2;
-    const int pr = pix / PW, pc = pix - pr * PW;
-    const int gy = wrapn(y0 - 1 + pr, H), gx = wrapn(x0 - 1 + pc, W);
-    const __nv_bfloat16* src = act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8;
-    cp16(patch + pix_off(pix, chunk), src);
+    const int r = pix / TW, c = pix - r * TW;
+    const int gy = wrapn(y0 + r + oy, H), gx = wrapn(x0 + c + ox, W);
+    cp16(dst + pix_off(pix, chunk), act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
   }
 }
 
-// 32 -> 32 periodic convolution on the tensor cores.
+__device__ __forceinline__ int tap_dy(int tap, int d) { return (tap / 3 - 1) * d; }
+__device__ __forceinline__ int tap_dx(int tap, int d) { return (tap % 3 - 1) * d; }
+
+// 32 -> 32 periodic convolution (dilation d) on the tensor cores.
 // kMode 0: forward, out = bias + conv, stores z (if zout) and gelu(z) into aout.
 // kMode 1: input gradient, aout = conv * gelu'(zprev) (weights pre-flipped/transposed).
+// The shifted input tile of tap t + 1 streams into shared memory while tap t computes.
 template <int kMode>
 __global__ void __launch_bounds__(kConvThreads)
 conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
            __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
-           int tiles_x, int tiles_y) {
+           int tiles_x, int tiles_y, int dil) {
   extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* patch = sm;
-  unsigned char* wsm = sm + kPatchBytes;
+  unsigned char* tiles = sm;                  // 2 x kTileBytes
+  unsigned char* wsm = sm + 2 * kTileBytes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = blockIdx.x;
   const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
@@ -116,9 +124,8 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
     const int n = q / (K9 / 8), kc = q - n * (K9 / 8);
     cp16(wsm + n * WROWB + kc * 16, wk + (size_t)n * K9 + kc * 8);
   }
-  load_patch(patch, in, b, y0, x0, H, W);
-  cp_wait();
-  __syncthreads();
+  load_tap_tile(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
+  cp_commit();
 
   float acc[4][4][4];
 #pragma unroll
@@ -128,7 +135,7 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
 
-  const uint32_t pbase = smem_u32(patch), wbase = smem_u32(wsm);
+  const uint32_t tbase = smem_u32(tiles), wbase = smem_u32(wsm);
   // ldmatrix lane roles. A (x4): matrices (px 0-7, ch c), (px 8-15, ch c), (px 0-7, ch c+8),
   // (px 8-15, ch c+8). B (x4): (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15).
   const int a_px = (lane & 7) + ((lane >> 3) & 1) * 8;
@@ -138,7 +145,16 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
 
 #pragma unroll 1
   for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3, dx = tap - dy * 3;
+    if (tap < 8) {
+      load_tap_tile(tiles + ((tap + 1) & 1) * kTileBytes, in, b, y0, x0, tap_dy(tap + 1, dil),
+                    tap_dx(tap + 1, dil), H, W);
+      cp_commit();
+      cp_wait_group<1>();
+    } else {
+      cp_wait_group<0>();
+    }
+    __syncthreads();
+    const uint32_t cur = tbase + (tap & 1) * (uint32_t)kTileBytes;
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {  // 16-channel halves of K within this tap
       uint32_t bf[2][4];
@@ -150,9 +166,9 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
       }
 #pragma unroll
       for (int mt = 0; mt < 4; ++mt) {
-        const int pix = (warp + dy) * PW + mt * 16 + a_px + dx;
+        const int pix = warp * TW + mt * 16 + a_px;
         uint32_t af[4];
-        ldsm4(af, pbase + pix_off(pix, cc * 2 + a_ch));
+        ldsm4(af, cur + pix_off(pix, cc * 2 + a_ch));
 #pragma unroll
         for (int np = 0; np < 2; ++np) {
           mma16816(acc[mt][np * 2 + 0], af, bf[np][0], bf[np][1]);
@@ -160,6 +176,7 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
         }
       }
     }
+    __syncthreads();  // this buffer is refilled two taps later
   }
 
   // epilogue: thread holds rows g, g+8 (pixels) and columns 2q, 2q+1 (channels)
@@ -193,98 +210,98 @@ conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict
   }
 }
 
-// Weight gradient of a 32 -> 32 layer on the tensor cores:
-//   dW[o][tap*32 + c] = sum_p dz[p][o] * in[p + tap][c],  db[o] = sum_p dz[p][o].
-// Persistent CTAs loop over 4 x 64 tiles and keep their partial sums in
-// registers; each CTA writes its partial (32 x 288 + 32 floats) to `part`.
-// Warp w owns output columns (n-tiles) 9w .. 9w+8 of the 36 (tap, 8-channel) tiles.
+// Weight gradient of a 32 -> 32 layer (dilation d) on the tensor cores:
+//   dW[o][tap*32 + c] = sum_p dz[p][o] * in[p + off(tap)][c],  db[o] = sum_p dz[p][o].
+// GEMM with M = 32 output channels (A = dz^T), N = 288 (B = shifted input),
+// K = pixels. Persistent CTAs loop over 4 x 64 tiles; for each tile the taps
+// stream through a shared double buffer and warp w accumulates the 8 input
+// channels 8w..8w+7 of every tap in registers. Each CTA writes its partial
+// (32 x 288 + 32 floats) to `part`.
 __global__ void __launch_bounds__(kConvThreads)
 wgrad32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
-            float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles) {
+            float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
+            int dil) {
   extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* patch = sm;
-  unsigned char* dzs = sm + kPatchBytes;  // [TR*TW px][32 ch] swizzled
+  unsigned char* dzs = sm;                  // [TR*TW px][32 ch]
+  unsigned char* tiles = sm + kTileBytes;   // 2 x [TR*TW px][32 ch]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float acc[2][9][4];
+  float acc[9][2][4];
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 9; ++i)
 #pragma unroll
-    for (int j = 0; j < 9; ++j)
+    for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
   float dbs = 0.f;  // thread t < 32 sums channel t
-  const uint32_t pbase = smem_u32(patch), dbase = smem_u32(dzs);
+  const uint32_t dbase = smem_u32(dzs), tbase = smem_u32(tiles);
   // A = dz^T (m = channel, k = pixel) via ldmatrix.trans of [px][ch]:
   //   matrices (px 0-7, ch 0-7) (px 0-7, ch 8-15) (px 8-15, ch 0-7) (px 8-15, ch 8-15)
   const int ta_px = (lane & 7) + (lane >> 4) * 8;
   const int ta_ch = (lane >> 3) & 1;
-  // B = shifted input (k = pixel, n = channel) via ldmatrix.trans:
-  //   matrices (px 0-7, ch c) (px 8-15, ch c) (px 0-7, ch c+8) (px 8-15, ch c+8)
-  const int tb_px = (lane & 7) + ((lane >> 3) & 1) * 8;
-  const int tb_ch = lane >> 4;
+  // B = shifted input (k = pixel, n = channel) via ldmatrix.trans, two k-steps:
+  //   matrices (px 0-7) (px 8-15) (px 16-23) (px 24-31), channel chunk = warp
+  const int tb_px = lane;
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
     const int x0 = tx * TW, y0 = ty * TR;
-    __syncthreads();  // previous tile's smem reads are done
-    load_patch(patch, in, b, y0, x0, H, W);
+    __syncthreads();  // previous tile's shared reads are done
     for (int qq = threadIdx.x; qq < TR * TW * 4; qq += blockDim.x) {
       const int chunk = qq & 3, pix = qq >> 2;
       const int r = pix / TW, c = pix - r * TW;
       cp16(dzs + pix_off(pix, chunk), dz + (((int64_t)b * H + y0 + r) * W + x0 + c) * C + chunk * 8);
     }
-    cp_wait();
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      for (int pix = 0; pix < TR * TW; ++pix) {
-        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(
-            dzs + pix_off(pix, threadIdx.x >> 3)) + (threadIdx.x & 7);
-        dbs += __bfloat162float(*p);
+    load_tap_tile(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
+    cp_commit();
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      if (tap < 8) {
+        load_tap_tile(tiles + ((tap + 1) & 1) * kTileBytes, in, b, y0, x0, tap_dy(tap + 1, dil),
+                      tap_dx(tap + 1, dil), H, W);
+        cp_commit();
+        cp_wait_group<1>();
+      } else {
+        cp_wait_group<0>();
       }
-    }
-#pragma unroll 1
-    for (int ks = 0; ks < TR * (TW / 16); ++ks) {  // 16 pixels per k-step
-      const int r = ks / (TW / 16), seg = ks - r * (TW / 16);
-      uint32_t af[2][4];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int pix = r * TW + seg * 16 + ta_px;
-        ldsm4t(af[mt], dbase + pix_off(pix, mt * 2 + ta_ch));
-      }
-#pragma unroll
-      for (int j = 0; j < 9; j += 2) {
-        // n-tiles nt = 9 warp + j (and + j + 1): tap = nt / 4, channel chunk8 = nt % 4
-        uint32_t bf[4];
-        const int nt0 = 9 * warp + j;
-        const int nt1 = (j + 1 < 9) ? nt0 + 1 : nt0;
-        // lanes 0-15 address n-tile nt0, lanes 16-31 n-tile nt1
-        const int nt = (lane < 16) ? nt0 : nt1;
-        const int tap = nt >> 2, c8 = nt & 3;
-        const int dy = tap / 3, dx = tap - dy * 3;
-        const int ppx = (r + dy) * PW + seg * 16 + dx + ((lane & 7) + ((lane >> 3) & 1) * 8);
-        ldsm4t(bf, pbase + pix_off(ppx, c8));
-        (void)tb_px; (void)tb_ch;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          mma16816(acc[mt][j], af[mt], bf[0], bf[1]);
-          if (j + 1 < 9) mma16816(acc[mt][j + 1], af[mt], bf[2], bf[3]);
+      __syncthreads();
+      if (tap == 0 && threadIdx.x < 32) {
+        for (int pix = 0; pix < TR * TW; ++pix) {
+          const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(
+              dzs + pix_off(pix, threadIdx.x >> 3)) + (threadIdx.x & 7);
+          dbs += __bfloat162float(*p);
         }
       }
+      const uint32_t cur = tbase + (tap & 1) * (uint32_t)kTileBytes;
+#pragma unroll 1
+      for (int k2 = 0; k2 < TR * TW / 32; ++k2) {  // 32 pixels = two k-steps
+        uint32_t bf[4];
+        ldsm4t(bf, cur + pix_off(k2 * 32 + tb_px, warp));
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int pix = k2 * 32 + h2 * 16 + ta_px;
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            uint32_t af[4];
+            ldsm4t(af, dbase + pix_off(pix, mt * 2 + ta_ch));
+            mma16816(acc[tap][mt], af, bf[h2 * 2], bf[h2 * 2 + 1]);
+          }
+        }
+      }
+      __syncthreads();  // this buffer is refilled two taps later
     }
   }
-  // write the CTA partial: rows o (m), columns n = tap*32 + c
+  // write the CTA partial: rows o (m), columns n = tap*32 + 8 warp + 2q
   float* out = part + (size_t)blockIdx.x * (C * K9 + C);
   const int g = lane >> 2, q = lane & 3;
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+  for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const int nt = 9 * warp + j;
-      const int col = nt * 8 + 2 * q;  // = tap*32 + c8*8 + 2q
-      out[(mt * 16 + g) * K9 + col] = acc[mt][j][0];
-      out[(mt * 16 + g) * K9 + col + 1] = acc[mt][j][1];
-      out[(mt * 16 + g + 8) * K9 + col] = acc[mt][j][2];
-      out[(mt * 16 + g + 8) * K9 + col + 1] = acc[mt][j][3];
+    for (int mt = 0; mt < 2; ++mt) {
+      const int col = tap * C + warp * 8 + 2 * q;
+      out[(mt * 16 + g) * K9 + col] = acc[tap][mt][0];
+      out[(mt * 16 + g) * K9 + col + 1] = acc[tap][mt][1];
+      out[(mt * 16 + g + 8) * K9 + col] = acc[tap][mt][2];
+      out[(mt * 16 + g + 8) * K9 + col + 1] = acc[tap][mt][3];
     }
   if (threadIdx.x < 32) out[C * K9 + threadIdx.x] = dbs;
 }
@@ -292,7 +309,7 @@ wgrad32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
 // First layer (1 -> 32) forward: z = b + sum_tap W1[o][tap] x[p + tap]; a = gelu(z).
 __global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
                            const float* __restrict__ b1, __nv_bfloat16* __restrict__ zout,
-                           __nv_bfloat16* __restrict__ aout, int B, int H, int W) {
+                           __nv_bfloat16* __restrict__ aout, int B, int H, int W, int dil) {
   __shared__ float ws[C * 9 + C];
   for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w1[i];
   for (int i = threadIdx.x; i < C; i += blockDim.x) ws[C * 9 + i] = b1[i];
@@ -305,7 +322,7 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
     float v[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrap1(yy + tap / 3 - 1, H), gx = wrap1(xx + tap % 3 - 1, W);
+      const int gy = wrapn(yy + tap_dy(tap, dil), H), gx = wrapn(xx + tap_dx(tap, dil), W);
       v[tap] = x[(img * H + gy) * W + gx];
     }
     __nv_bfloat162 zz[C / 2], aa[C / 2];
@@ -347,7 +364,8 @@ __device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p)
 
 // Last layer (32 -> 1) forward: y = b6 + sum_{tap,c} W6[c][tap] a[p + tap][c] (FP32 out).
 __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __restrict__ w6,
-                          const float* __restrict__ b6, float* __restrict__ y, int B, int H, int W) {
+                          const float* __restrict__ b6, float* __restrict__ y, int B, int H, int W,
+                          int dil) {
   __shared__ float ws[C * 9];
   for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
   __syncthreads();
@@ -359,7 +377,7 @@ __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __re
     float s = b6[0];
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrap1(yy + tap / 3 - 1, H), gx = wrap1(xx + tap % 3 - 1, W);
+      const int gy = wrapn(yy + tap_dy(tap, dil), H), gx = wrapn(xx + tap_dx(tap, dil), W);
       float f[C];
       load_px32(f, a + ((img * H + gy) * W + gx) * C);
 #pragma unroll
@@ -393,7 +411,7 @@ __global__ void mse_grad(const float* __restrict__ y, const float* __restrict__ 
 // Backward of the last layer: dz5[q][c] = gelu'(z5[q][c]) * sum_tap W6[c][tap] dy[q - tap].
 __global__ void back_last(const float* __restrict__ dy, const float* __restrict__ w6,
                           const __nv_bfloat16* __restrict__ z5, __nv_bfloat16* __restrict__ dz5,
-                          int B, int H, int W) {
+                          int B, int H, int W, int dil) {
   __shared__ float ws[C * 9];
   for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
   __syncthreads();
@@ -405,7 +423,7 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
     float g[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrap1(yy - (tap / 3 - 1), H), gx = wrap1(xx - (tap % 3 - 1), W);
+      const int gy = wrapn(yy - tap_dy(tap, dil), H), gx = wrapn(xx - tap_dx(tap, dil), W);
       g[tap] = dy[(img * H + gy) * W + gx];
     }
     float z[C];
@@ -434,9 +452,9 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
 template <int kMode>
 __global__ void __launch_bounds__(288)
 wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1,
-             float* __restrict__ part, int B, int H, int W, int px_per_cta) {
+             float* __restrict__ part, int B, int H, int W, int px_per_cta, int dil) {
   const int c = threadIdx.x / 9, tap = threadIdx.x % 9;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int dy = tap_dy(tap, dil), dx = tap_dx(tap, dil);
   const int64_t n = (int64_t)B * H * W;
   const int64_t p0 = (int64_t)blockIdx.x * px_per_cta;
   const int64_t p1 = std::min<int64_t>(n, p0 + px_per_cta);
@@ -444,7 +462,7 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
   for (int64_t p = p0; p < p1; ++p) {
     const int xx = (int)(p % W), yy = (int)((p / W) % H);
     const int64_t img = p / ((int64_t)H * W);
-    const int64_t ps = (img * H + wrap1(yy + dy, H)) * W + wrap1(xx + dx, W);
+    const int64_t ps = (img * H + wrapn(yy + dy, H)) * W + wrapn(xx + dx, W);
     if (kMode == 0) {
       const float gv = __bfloat162float(g32[p * C + c]);
       acc = fmaf(gv, s1[ps], acc);
@@ -606,6 +624,7 @@ int grid_1d(int64_t n, int threads) {
 
 struct px_cnn {
   px_ctx* ctx = nullptr;
+  int dil[kLayers] = {1, 1, 1, 1, 1, 1};  // per-layer dilation
   float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16* wf[kLayers] = {};
   __nv_bfloat16* wb[kLayers] = {};
@@ -696,7 +715,7 @@ px_status set_conv_attrs() {
   if (done) return PX_OK;
   cudaError_t e = cudaFuncSetAttribute(conv32_mma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kPatchBytes + TR * TW * 64));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
   return PX_OK;
@@ -709,13 +728,14 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
   const int tiles_x = W / TW, tiles_y = H / TR;
   const int tiles = B * tiles_x * tiles_y;
   conv_first<<<grid_1d(px, 256), 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
-                                               train ? n->z[0] : nullptr, n->a[0], B, H, W);
+                                               train ? n->z[0] : nullptr, n->a[0], B, H, W,
+                                               n->dil[0]);
   for (int l = 1; l <= 4; ++l)
     conv32_mma<0><<<tiles, kConvThreads, kConvSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y);
+        n->a[l], H, W, tiles_x, tiles_y, n->dil[l]);
   conv_last<<<grid_1d(px, 256), 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
-                                              n->params + kOff.b[5], y, B, H, W);
+                                              n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network forward");
 }
@@ -736,22 +756,24 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   const int nsc = (int)((px + spc - 1) / spc);
   const int nsc_cap = (int)std::min<int64_t>(nsc, n->part_floats / (C * 9 + C));
   const int spc_eff = (int)((px + nsc_cap - 1) / nsc_cap);
-  wgrad_single<1><<<nsc_cap, 288, 0, st>>>(n->a[4], n->dy, n->part, B, H, W, spc_eff);
+  wgrad_single<1><<<nsc_cap, 288, 0, st>>>(n->a[4], n->dy, n->part, B, H, W, spc_eff, n->dil[5]);
   reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
-  back_last<<<grid_1d(px, 256), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W);
+  back_last<<<grid_1d(px, 256), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W,
+                                              n->dil[5]);
   __nv_bfloat16* gcur = n->g0;
   __nv_bfloat16* gnext = n->g1;
   const int wg_ctas = std::min(tiles, px::device_sm_count() * 4);
   for (int l = 4; l >= 1; --l) {
-    wgrad32_mma<<<wg_ctas, kConvThreads, kPatchBytes + TR * TW * 64, st>>>(
-        n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles);
+    wgrad32_mma<<<wg_ctas, kConvThreads, kWgradSmem, st>>>(
+        n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles, n->dil[l]);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     conv32_mma<1><<<tiles, kConvThreads, kConvSmem, st>>>(gcur, n->wb[l], nullptr, n->z[l - 1],
-                                                          nullptr, gnext, H, W, tiles_x, tiles_y);
+                                                          nullptr, gnext, H, W, tiles_x, tiles_y,
+                                                          n->dil[l]);
     std::swap(gcur, gnext);
   }
-  wgrad_single<0><<<nsc_cap, 288, 0, st>>>(gcur, x, n->part, B, H, W, spc_eff);
+  wgrad_single<0><<<nsc_cap, 288, 0, st>>>(gcur, x, n->part, B, H, W, spc_eff, n->dil[0]);
   reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network backward");
@@ -785,15 +807,21 @@ extern "C" {
 
 size_t px_cnn_param_count(void) { return kOff.total; }
 
-px_status px_cnn_create(px_ctx* c, uint64_t seed, px_cnn** out) {
+px_status px_cnn_create(px_ctx* c, uint64_t seed, const int32_t* dilations, px_cnn** out) {
   if (!c || !out) return PX_EINVAL;
   c->err.clear();
   *out = nullptr;
+  if (dilations)
+    for (int l = 0; l < kLayers; ++l)
+      if (dilations[l] < 1 || dilations[l] > 4096)
+        return px::ctx_fail(c, PX_EINVAL, "dilations must be in 1..4096");
   DevScope ds(c->device);
   if (set_conv_attrs() != PX_OK) return px::ctx_fail(c, PX_ECUDA, "conv kernel attributes");
   px_cnn* n = new (std::nothrow) px_cnn();
   if (!n) return px::ctx_fail(c, PX_ENOMEM, "host allocation failed");
   n->ctx = c;
+  if (dilations)
+    for (int l = 0; l < kLayers; ++l) n->dil[l] = dilations[l];
   const size_t P = kOff.total;
   cudaError_t e = cudaMalloc(&n->params, P * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&n->grads, P * sizeof(float));

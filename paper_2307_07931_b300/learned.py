@@ -157,6 +157,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--timed", type=int, default=32)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--dilations", default="1,3,9,27,81,1",
+                    help="per-layer dilations of the 3x3 layers ('1,1,1,1,1,1' = plain)")
     a = ap.parse_args()
     os.makedirs(a.out, exist_ok=True)
     logf = open(os.path.join(a.out, "learned_log.txt"), "w")
@@ -185,7 +187,8 @@ def main():
     log(f"labels: {a.label_sweeps} FP64 sweeps in {res['label_s']:.1f}s, rel resid "
         f"median {np.median(rel):.2e} max {rel.max():.2e}")
 
-    net = px.Cnn(seed=a.seed)
+    dil = tuple(int(v) for v in a.dilations.split(","))
+    net = px.Cnn(seed=a.seed, dilations=dil)
     X = torch.empty(a.train, N, N, dtype=torch.float32, device="cuda")
     T = torch.empty_like(X)
     for s0 in range(0, a.train, 256):

@@ -36,33 +36,38 @@ def bf16_round(a):
     return torch.from_numpy(np.asarray(a, dtype=np.float32)).bfloat16().float().numpy().astype(np.float64)
 
 
-@pytest.mark.parametrize("B,H,W", [(2, 8, 64), (1, 12, 128), (1, 256, 256)])
-def test_forward_matches_oracle(px, B, H, W):
-    net = px.Cnn(seed=3)
+DIL = (1, 3, 9, 27, 81, 1)
+
+
+@pytest.mark.parametrize("B,H,W,dil", [(2, 8, 64, None), (1, 12, 128, None), (1, 256, 256, None),
+                                       (2, 8, 64, DIL), (1, 256, 256, DIL), (1, 32, 192, (1, 2, 5, 7, 3, 2))])
+def test_forward_matches_oracle(px, B, H, W, dil):
+    net = px.Cnn(seed=3, dilations=dil)
     rng = np.random.default_rng(B * 1000 + H)
     x = rng.standard_normal((B, H, W)).astype(np.float32)
     xt = torch.from_numpy(x).cuda()
     y = torch.empty_like(xt)
     net.forward(xt, y)
     torch.cuda.synchronize()
-    ref, _ = ocnn.forward(oracle_params(px, net), x.astype(np.float64)[:, None])
+    ref, _ = ocnn.forward(oracle_params(px, net), x.astype(np.float64)[:, None], dil)
     ref = ref[:, 0]
     got = y.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(got - ref)) <= 3e-2 * np.max(np.abs(ref))
     net.close()
 
 
-def test_gradients_match_oracle(px):
+@pytest.mark.parametrize("dil", [None, DIL])
+def test_gradients_match_oracle(px, dil):
     B, H, W = 2, 8, 64
-    net = px.Cnn(seed=5)
+    net = px.Cnn(seed=5, dilations=dil)
     rng = np.random.default_rng(7)
     x = rng.standard_normal((B, H, W)).astype(np.float32)
     t = rng.standard_normal((B, H, W)).astype(np.float32)
     g, loss = net.grads(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
     P = oracle_params(px, net)
-    y, cache = ocnn.forward(P, x.astype(np.float64)[:, None])
+    y, cache = ocnn.forward(P, x.astype(np.float64)[:, None], dil)
     L, dy = ocnn.mse(y, t.astype(np.float64)[:, None])
-    ref = ocnn.backward(P, cache, dy)
+    ref = ocnn.backward(P, cache, dy, dil)
     assert abs(loss - L) <= 2e-2 * L
     gl = px.cnn_unflatten(g)
     for li, ((dW, db), (gw, gb)) in enumerate(zip(ref, gl)):
@@ -131,6 +136,9 @@ def test_prepare_and_guess_scaling(px):
 
 
 def test_unsupported_shapes(px):
+    with pytest.raises(px.PxError) as ei:
+        px.Cnn(seed=0, dilations=(1, 0, 1, 1, 1, 1))
+    assert ei.value.status == px.PX_EINVAL
     net = px.Cnn(seed=0)
     x = torch.zeros(1, 8, 100, device="cuda")
     with pytest.raises(px.PxError) as ei:
