@@ -20,9 +20,11 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 
 // Non-negative floats / doubles (and +NaN) order like their bit patterns read
 // as unsigned integers, so a max-norm reduces with integer max.
-__device__ __forceinline__ uint32_t absbits(float v) { return __float_as_uint(fabsf(v)); }
+// |v| as bits by clearing the sign bit on the integer pipe (keeps the FP64 pipe,
+// the bound of the FP64 sweep, free of the residual's absolute value).
+__device__ __forceinline__ uint32_t absbits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
 __device__ __forceinline__ uint64_t absbits(double v) {
-  return (uint64_t)__double_as_longlong(fabs(v));
+  return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
 __device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
 __device__ __forceinline__ uint64_t umax(uint64_t a, uint64_t b) { return a > b ? a : b; }

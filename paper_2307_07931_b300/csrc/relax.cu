@@ -29,6 +29,7 @@
 #include "px_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace px {
 
@@ -517,6 +518,236 @@ relaxW_f32(const float* __restrict__ phi, float* __restrict__ out, const float* 
   }
 }
 
+// ---------------------------------------------------------------------------
+// relaxW2_f32: the wavefront kernel with two rows per step per stage. Stage t
+// computes level-t rows r, r+1 with r = 2s - 3t at step s (one pair behind
+// stage t-1 by two steps), from level t-1 rows r-1 .. r+2: rows r-1, r are
+// kept from the previous step and r+1, r+2 come from a 4-row shared ring (a
+// stage reads its first window during its last idle step, while those rows'
+// slots are not being rewritten). The loader brings row pairs kW2Prefetch
+// steps ahead; the rho ring holds exactly the 3 TB + 2 P + 2 live rows.
+// Half the barriers of relaxW_f32 and twice the independent work per warp.
+constexpr int kW2Prefetch = 3;  // row pairs loaded ahead
+
+template <int TB>
+struct W2Geom {
+  static constexpr int P = kW2Prefetch;
+  static constexpr int HX = ((TB + 3) / 4) * 4;
+  static constexpr int OW = kWStrip - 2 * HX;
+  static constexpr int R0 = 16;                  // >= 2P + 4 (power of two: mask)
+  static constexpr int RR = 3 * TB + 2 * P + 2;  // rho rows live at once (slot counters)
+  static constexpr int RL = 4;                   // rows per level ring (power of two: mask)
+  static constexpr int kThreads = (TB + 1) * kWarp;
+  static constexpr size_t smem = sizeof(float) * kWStrip * (size_t)(R0 + RR + RL * (TB - 1));
+  static_assert(R0 >= 2 * P + 4 && RR >= 3 * TB + 2 * P + 2, "ring sizes");
+};
+
+template <int TB>
+__global__ void __launch_bounds__(W2Geom<TB>::kThreads)
+relaxW2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
+            int nx, int ny, int64_t ld, int H, int nstrips, Coef<float> k, Reports rep) {
+  using G = W2Geom<TB>;
+  extern __shared__ __align__(16) float wsm[];
+  float* L0 = wsm;
+  float* RH = L0 + G::R0 * kWStrip;
+  float* LV = RH + G::RR * kWStrip;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+  const int y0 = seg * H;
+  const int base = y0 - TB;
+  const int npairs = (H + 2 * TB) / 2;    // H is even
+  const int gx0 = strip * G::OW - G::HX;
+  const int steps = H / 2 + 2 * TB;
+  const int c0 = lane * 4, c1 = 128 + lane * 4;
+
+  if (warp == TB) {
+    const int gxa = wrapn(gx0 + c0, nx), gxb = wrapn(gx0 + c1, nx);
+    int grow = wrapn(base, ny);
+    int i = 0;   // next load index (row)
+    int ri = 0;  // its rho ring slot, i mod RR
+    auto issue_pair = [&]() {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (i < 2 * npairs) {
+          const int64_t row = (int64_t)grow * ld;
+          float* d0 = L0 + (i & (G::R0 - 1)) * kWStrip;
+          float* d1 = RH + ri * kWStrip;
+          cp_async16(d0 + c0, phi + row + gxa);
+          cp_async16(d0 + c1, phi + row + gxb);
+          cp_async16(d1 + c0, rho + row + gxa);
+          cp_async16(d1 + c1, rho + row + gxb);
+          grow = (grow + 1 == ny) ? 0 : grow + 1;
+        }
+        ++i;
+        ri = (ri + 1 == G::RR) ? 0 : ri + 1;
+      }
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+#pragma unroll 1
+    for (int q = 0; q < G::P; ++q) issue_pair();
+#pragma unroll 1
+    for (int st = 0; st < steps; ++st) {
+      issue_pair();
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(G::P) : "memory");  // pair st complete
+      __syncthreads();
+    }
+    return;
+  }
+
+  const int t = warp + 1;
+  const float* src = (t == 1) ? L0 : LV + (t - 2) * G::RL * kWStrip;
+  const int smask = (t == 1) ? G::R0 - 1 : G::RL - 1;
+  float* dstL = LV + (t - 1) * G::RL * kWStrip;
+  const bool rep_t = rep.due(t - 1);
+  const bool own0 = c0 >= G::HX && c0 < kWStrip - G::HX && gx0 + c0 < nx;
+  const bool own1 = c1 >= G::HX && c1 < kWStrip - G::HX && gx0 + c1 < nx;
+  const int own_hi = min(TB + H, TB + ny - y0);
+  float* const orow0 = out + gx0;
+  const int first = t;                          // first row (load index) of level t
+  const int npair_t = (H + 2 * TB - 2 * t) / 2;  // pairs of level t
+  uint32_t mx = 0;
+
+  // Idle steps 0 .. 2t-1; the first window (level t-1 rows t-1, t, written by
+  // stage t-1 at step 2t-2) is read during step 2t-1.
+#pragma unroll 1
+  for (int st = 0; st < 2 * t - 1; ++st) __syncthreads();
+  float X[16], Y[16];  // row pairs: [0..7] = lower row, [8..15] = upper row
+  {
+    const float* ra = src + ((first - 1) & smask) * kWStrip;
+    const float* rb = src + (first & smask) * kWStrip;
+    lds4(X, ra + c0); lds4(X + 4, ra + c1);
+    lds4(X + 8, rb + c0); lds4(X + 12, rb + c1);
+  }
+  __syncthreads();
+  int r = first;
+  int rs = first % G::RR;  // rho ring slot of row r
+
+  // rows r, r+1 of level t from input rows up = r-1, cu = r (in P), r+1, r+2 (into Q)
+  auto pair = [&](const float* Pp, float* Q) {
+    const float* s1 = src + ((r + 1) & smask) * kWStrip;
+    const float* s2 = src + ((r + 2) & smask) * kWStrip;
+    lds4(Q, s1 + c0); lds4(Q + 4, s1 + c1);
+    lds4(Q + 8, s2 + c0); lds4(Q + 12, s2 + c1);
+    float rh[16];
+    const int rs1 = (rs + 1 == G::RR) ? 0 : rs + 1;
+    const float* h0 = RH + rs * kWStrip;
+    const float* h1 = RH + rs1 * kWStrip;
+    lds4(rh, h0 + c0); lds4(rh + 4, h0 + c1);
+    lds4(rh + 8, h1 + c0); lds4(rh + 12, h1 + c1);
+    float o[16], rr[16];
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const float* up = row == 0 ? Pp : Pp + 8;
+      const float* cu = row == 0 ? Pp + 8 : Q;
+      const float* dn = row == 0 ? Q : Q + 8;
+      const float l0 = __shfl_sync(0xffffffffu, cu[3], (lane + 31) & 31);
+      const float l1 = __shfl_sync(0xffffffffu, lane == 31 ? cu[3] : cu[7], (lane + 31) & 31);
+      const float r0 = __shfl_sync(0xffffffffu, lane == 0 ? cu[4] : cu[0], (lane + 1) & 31);
+      const float r1 = __shfl_sync(0xffffffffu, cu[4], (lane + 1) & 31);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float w = (i == 0) ? l0 : (i == 4) ? l1 : cu[i - 1];
+        const float e = (i == 3) ? r0 : (i == 7) ? r1 : cu[i + 1];
+        const float q = (w + e) + (up[i] + dn[i]);
+        const float sv = fmaf(-4.0f, cu[i], q);
+        rr[row * 8 + i] = fmaf(sv, k.ih2, -rh[row * 8 + i]);
+        o[row * 8 + i] = fmaf(k.c, rr[row * 8 + i], cu[i]);
+      }
+    }
+    if (rep_t) {
+#pragma unroll
+      for (int row = 0; row < 2; ++row) {
+        const bool own_row = (r + row) >= TB && (r + row) < own_hi;
+        const uint32_t m0 = (own_row && own0) ? 0x7fffffffu : 0u;
+        const uint32_t m1 = (own_row && own1) ? 0x7fffffffu : 0u;
+        const float* v = rr + row * 8;
+        mx = __vimax3_u32(mx, __float_as_uint(v[0]) & m0, __float_as_uint(v[1]) & m0);
+        mx = __vimax3_u32(mx, __float_as_uint(v[2]) & m0, __float_as_uint(v[3]) & m0);
+        mx = __vimax3_u32(mx, __float_as_uint(v[4]) & m1, __float_as_uint(v[5]) & m1);
+        mx = __vimax3_u32(mx, __float_as_uint(v[6]) & m1, __float_as_uint(v[7]) & m1);
+      }
+    }
+    if (t < TB) {
+      float* d0 = dstL + (r & (G::RL - 1)) * kWStrip;
+      float* d1 = dstL + ((r + 1) & (G::RL - 1)) * kWStrip;
+      sts4(d0 + c0, o); sts4(d0 + c1, o + 4);
+      sts4(d1 + c0, o + 8); sts4(d1 + c1, o + 12);
+    } else {
+#pragma unroll
+      for (int row = 0; row < 2; ++row) {
+        const int gy = base + r + row;
+        if (gy < ny) {
+          float* orow = orow0 + (int64_t)gy * ld;
+          if (own0) sts4(orow + c0, o + row * 8);
+          if (own1) sts4(orow + c1, o + row * 8 + 4);
+        }
+      }
+    }
+    r += 2;
+    rs = (rs1 + 1 == G::RR) ? 0 : rs1 + 1;
+    __syncthreads();
+  };
+
+  int n = npair_t;
+#pragma unroll 1
+  while (n >= 2) {
+    pair(X, Y);
+    pair(Y, X);
+    n -= 2;
+  }
+  if (n == 1) pair(X, Y);
+
+#pragma unroll 1
+  for (int st = 2 * t + npair_t; st < steps; ++st) __syncthreads();
+
+  if (rep_t) {
+    mx = warp_max(mx);
+    if (lane == 0) atomic_max_bits(rep.slot(t - 1), to_f64_bits(mx));
+  }
+}
+
+template <int TB>
+cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
+                           Coef<float> k, Reports rep, cudaStream_t st) {
+  using G = W2Geom<TB>;
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(relaxW2_f32<TB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)G::smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxW2_f32<TB>, G::kThreads, G::smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  const int nstrips = (f.nx + G::OW - 1) / G::OW;
+  const int64_t resident = (int64_t)occ * device_sm_count();
+  static const int cand[] = {8, 16, 32, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+  int H = 8;
+  double best = 1e300;
+  for (int h : cand) {
+    const int64_t ctas = (int64_t)nstrips * ((f.ny + h - 1) / h);
+    const double cost = (double)((ctas + resident - 1) / resident) * (h / 2 + 2 * TB);
+    if (cost <= best) { best = cost; H = h; }
+    if (h >= f.ny) break;
+  }
+  const int64_t blocks = (int64_t)nstrips * ((f.ny + H - 1) / H);
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  relaxW2_f32<TB><<<(unsigned)blocks, G::kThreads, G::smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
+                                                                   H, nstrips, k, rep);
+  return cudaGetLastError();
+}
+
+// 2 = relaxW2_f32 (default), 1 = relaxW_f32; PX_WAVE_ROWS selects for A/B timing.
+int wave_rows() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = getenv("PX_WAVE_ROWS");
+    v = (e && e[0] == '1') ? 1 : 2;
+  }
+  return v;
+}
+
 template <int TB>
 cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, cudaStream_t st) {
@@ -568,6 +799,18 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
              : launch_stream_t<T, 1, false>(f, src, dst, rho, k, slot, st);
   }
   if constexpr (sizeof(T) == 4) {
+    if (wave_rows() == 2) {
+      switch (tb) {
+        case 2: return launch_wave2_t<2>(f, src, dst, rho, k, rep, st);
+        case 3: return launch_wave2_t<3>(f, src, dst, rho, k, rep, st);
+        case 4: return launch_wave2_t<4>(f, src, dst, rho, k, rep, st);
+        case 5: return launch_wave2_t<5>(f, src, dst, rho, k, rep, st);
+        case 6: return launch_wave2_t<6>(f, src, dst, rho, k, rep, st);
+        case 7: return launch_wave2_t<7>(f, src, dst, rho, k, rep, st);
+        case 8: return launch_wave2_t<8>(f, src, dst, rho, k, rep, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
     switch (tb) {
       case 2: return launch_wave_t<2>(f, src, dst, rho, k, rep, st);
       case 3: return launch_wave_t<3>(f, src, dst, rho, k, rep, st);
