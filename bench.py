@@ -36,14 +36,14 @@ BATCH_SWEEPS = 300  # sweeps per instance of the batched workload
 OMEGA = 2.0 / 3.0
 ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cell per launch
 # DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
-# (profiles/relaxW_f32_6144.md: dram read + write of one 6144^2 launch / cells).
-MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (312.119296e6 + 121.245184e6) / 6144**2}
+# (profiles/relaxW2_f32_6144.md: dram read + write of one 6144^2 launch / cells).
+MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (325.220608e6 + 120.491776e6) / 6144**2}
 
 
 def kernel_name(dt: str, tb: int) -> str:
     if tb == 1:
         return "relax1_stream<float,4>" if dt == "f32" else "relax1_stream<double,2>"
-    return f"relaxW_f32<{tb}>" if dt == "f32" else f"relaxT_tile<double,{tb}>"
+    return f"relaxW2_f32<{tb}>" if dt == "f32" else f"relaxT_tile<double,{tb}>"
 
 
 def peaks():
@@ -267,30 +267,58 @@ def bench_batched(px, torch, steps: int, warmup: int):
             "note": "FP64 instances are bound by the FP64 pipe (6 ops/update at 0.555e12/s)"}
 
 
+def load_trained_network(px):
+    """The learned-guess network trained by paper_2307_07931_b300.learned, if its
+    weights ship with the package (data/learned_guess_params.npy)."""
+    d = os.path.join(ROOT, "paper_2307_07931_b300", "data")
+    pfile, mfile = os.path.join(d, "learned_guess_params.npy"), os.path.join(d, "learned_guess.json")
+    if not (os.path.exists(pfile) and os.path.exists(mfile)):
+        return None, None
+    meta = json.load(open(mfile))
+    net = px.Cnn(seed=0, dilations=tuple(meta["dilations"]))
+    net.set_params(np.load(pfile))
+    return net, meta
+
+
 def bench_time_to_tol(px, torch, rtol: float = 1e-8):
     """Wall time to ||rho - L phi|| <= rtol ||rho|| on one 256^2 learned-guess field
-    (1-32 modes k,l <= 32 plus 0-4 Gaussian blobs), from phi0 = 0: plain FP64
-    sweeps vs FP32 sweeps inside FP64 refinement, both through px_solve."""
+    (1-32 modes k,l <= 32 plus 0-4 Gaussian blobs; the first held-out draw), all
+    through px_solve: plain FP64 sweeps from phi0 = 0, FP32 sweeps inside FP64
+    refinement from 0, and (with trained weights) the network's guess followed
+    by either solver, the guess inside the timed region."""
     import synth
     n = 256
-    rng = np.random.Generator(np.random.PCG64(synth.workload_seed(4)))
+    h = 1.0 / n
+    rng = np.random.Generator(np.random.PCG64(synth.workload_seed(4) + 1000))
     rho = synth.learned_guess_rho(rng, n)
     r64 = torch.from_numpy(rho).cuda()
-    out = {"grid": n, "rtol": rtol, "field": "learned-guess recipe, seed 20230721, first draw"}
-    for key, mode, kw in (("plain_f64", "plain", {"check_every": 2000, "tblock": 1}),
-                          ("mixed", "refine", {"inner_sweeps": 2000, "tblock": 8})):
+    net, meta = load_trained_network(px)
+    out = {"grid": n, "rtol": rtol, "field": "learned-guess recipe, held-out seed stream, first draw"}
+    runs = [("plain_f64", "plain", False, {"check_every": 1000, "tblock": 1}),
+            ("mixed", "refine", False, {"inner_sweeps": 1000, "tblock": 8})]
+    if net is not None:
+        runs += [("cnn_plain_f64", "plain", True, {"check_every": 1000, "tblock": 1}),
+                 ("cnn_mixed", "refine", True, {"inner_sweeps": 1000, "tblock": 8})]
+        out["network"] = {"dilations": meta["dilations"], "trained": meta.get("summary")}
+    for key, mode, guess, kw in runs:
         best = None
-        for _ in range(2):
+        for _ in range(3):
             phi = torch.zeros_like(r64)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            info = px.solve(phi, r64, 1.0 / n, mode, rtol=rtol, max_sweeps=5 * 10**6, **kw)
+            if guess:
+                net.guess(r64[None], phi[None], h)
+            info = px.solve(phi, r64, h, mode, rtol=rtol, max_sweeps=10**7, **kw)
             wall = time.perf_counter() - t0
             if best is None or wall < best[0]:
                 best = (wall, info)
         out[key] = {"ms": 1000 * best[0], "sweeps": best[1]["sweeps"],
                     "cycles": best[1]["cycles"], "rel_resid": best[1]["rel_resid"], **kw}
-    out["speedup_mixed_vs_plain_f64"] = out["plain_f64"]["ms"] / out["mixed"]["ms"]
+    base = out["plain_f64"]["ms"]
+    out["speedup_vs_plain_f64"] = {k: base / out[k]["ms"] for k in out
+                                   if isinstance(out[k], dict) and "ms" in out[k]}
+    if net is not None:
+        net.close()
     return out
 
 

@@ -36,6 +36,7 @@ namespace cnn {
 constexpr int C = 32;            // channels of the hidden layers
 constexpr int K9 = 9 * C;        // GEMM K of a 32 -> 32 layer
 constexpr int TR = 4, TW = 64;   // output tile: rows x columns (one row per warp)
+static_assert(TW == 64, "load_tap_tile splits pixel indices with shifts");
 constexpr int WROWB = 592;       // bytes per weight row in shared memory (37 chunks)
 constexpr int kConvThreads = 128;
 constexpr size_t kTileBytes = (size_t)TR * TW * 64;             // one [TR*TW px][32 ch] tile
@@ -87,13 +88,18 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // Stage the input tile seen by one tap: pixels (y0 + r + oy, x0 + c + ox) of
-// image b for r < TR, c < TW, periodic, all 32 channels (4 chunks per pixel).
+// image b for r < TR, c < TW, periodic, all 32 channels. Consecutive threads
+// copy consecutive 16-byte chunks (a warp covers 8 whole pixels, 512 bytes).
+// The wrap is a conditional add or subtract when the tap offset is smaller
+// than the image (decided once per tap), a full modulo otherwise.
 __device__ __forceinline__ void load_tap_tile(unsigned char* dst, const __nv_bfloat16* act, int b,
                                               int y0, int x0, int oy, int ox, int H, int W) {
+  const bool near = oy > -H && oy < H && ox > -W && ox < W;
   for (int q = threadIdx.x; q < TR * TW * 4; q += blockDim.x) {
     const int chunk = q & 3, pix = q >> 2;
-    const int r = pix / TW, c = pix - r * TW;
-    const int gy = wrapn(y0 + r + oy, H), gx = wrapn(x0 + c + ox, W);
+    const int r = pix >> 6, c = pix & (TW - 1);  // TW == 64
+    const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
+    const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
     cp16(dst + pix_off(pix, chunk), act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
   }
 }
@@ -248,7 +254,7 @@ wgrad32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restric
     __syncthreads();  // previous tile's shared reads are done
     for (int qq = threadIdx.x; qq < TR * TW * 4; qq += blockDim.x) {
       const int chunk = qq & 3, pix = qq >> 2;
-      const int r = pix / TW, c = pix - r * TW;
+      const int r = pix >> 6, c = pix & (TW - 1);
       cp16(dzs + pix_off(pix, chunk), dz + (((int64_t)b * H + y0 + r) * W + x0 + c) * C + chunk * 8);
     }
     load_tap_tile(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
