@@ -129,11 +129,13 @@ def barrier(world):
 
 
 def max_over_ranks(x: float, world: int) -> float:
+    """Max of a per-rank time over all ranks (NCCL on CUDA, gloo on the CPU)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -162,7 +164,8 @@ def cpu_baseline(rho64: np.ndarray, n: int, budget_s: float = 12.0):
 
 def run_reference(args, world, rank):
     """Reference arm: the FP64 CPU oracle as it stands, timed on the host cores on
-    a bounded sample of the same workload (each step = S sweeps of the field)."""
+    a bounded sample of the same workload (each step = S sweeps of the field).
+    Under torchrun only rank 0 runs it; the other ranks exit without work."""
     if rank != 0:
         return
     import oracle
@@ -479,7 +482,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--grid", "--n", dest="n", type=int, default=N_DEFAULT,
+                    help="grid side (the workload is grid x grid)")
     ap.add_argument("--quick", action="store_true", help="fewer depth variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
