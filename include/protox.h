@@ -282,6 +282,13 @@ px_status px_cnn_create(px_ctx* ctx, uint64_t seed, const int32_t* dilations, px
 px_status px_cnn_destroy(px_cnn* net);
 px_status px_cnn_get_params(px_cnn* net, float* host, size_t count);
 px_status px_cnn_set_params(px_cnn* net, const float* host, size_t count);
+/* Checkpoint state: parameters, Adam first and second moments (3 x
+ * px_cnn_param_count() floats, px_cnn_state_count()) and the Adam step count.
+ * Restoring a state and continuing training reproduces an uninterrupted run
+ * bit for bit (every reduction of the training step has a fixed order). */
+size_t px_cnn_state_count(void);
+px_status px_cnn_get_state(px_cnn* net, float* host, size_t count, int64_t* step);
+px_status px_cnn_set_state(px_cnn* net, const float* host, size_t count, int64_t step);
 /* y (FP32, B x H x W) = network(x) for scaled inputs x (FP32). Asynchronous. */
 px_status px_cnn_forward(px_cnn* net, const float* x, float* y, int B, int H, int W, void* stream);
 /* Forward + backward of the MSE loss against t; gradients (FP32, parameter

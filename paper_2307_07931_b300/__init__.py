@@ -96,11 +96,15 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_cnn_get_params.argtypes = [_vp, fp, ctypes.c_size_t]
     lib.px_cnn_set_params.argtypes = [_vp, fp, ctypes.c_size_t]
     lib.px_cnn_forward.argtypes = [_vp, _vp, _vp, i, i, i, _vp]
+    lib.px_cnn_state_count.restype = ctypes.c_size_t
+    lib.px_cnn_get_state.argtypes = [_vp, fp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]
+    lib.px_cnn_set_state.argtypes = [_vp, fp, ctypes.c_size_t, ctypes.c_int64]
     lib.px_cnn_grads.argtypes = [_vp, _vp, _vp, i, i, i, fp, dp, _vp]
     lib.px_cnn_train_step.argtypes = [_vp, _vp, _vp, i, i, i, ctypes.c_float, dp, _vp]
     lib.px_cnn_prepare.argtypes = [_vp, _vp, _vp, _vp, _vp, i, i, i, d, dp, _vp]
     lib.px_cnn_guess.argtypes = [_vp, _vp, _vp, i, i, i, d, _vp]
-    for name in ("px_cnn_create", "px_cnn_destroy", "px_cnn_get_params", "px_cnn_set_params",
+    for name in ("px_cnn_get_state", "px_cnn_set_state",
+                 "px_cnn_create", "px_cnn_destroy", "px_cnn_get_params", "px_cnn_set_params",
                  "px_cnn_forward", "px_cnn_grads", "px_cnn_train_step", "px_cnn_prepare",
                  "px_cnn_guess"):
         getattr(lib, name).restype = i
@@ -383,6 +387,22 @@ class Cnn:
         p = np.ascontiguousarray(p, dtype=np.float32)
         self.ctx.check(load_library().px_cnn_set_params(
             self.handle, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), self.nparams))
+
+    def state(self):
+        """(flat FP32 parameters + Adam moments, step) for checkpoints."""
+        import numpy as np
+        n = int(load_library().px_cnn_state_count())
+        out = np.empty(n, dtype=np.float32)
+        step = ctypes.c_int64()
+        self.ctx.check(load_library().px_cnn_get_state(
+            self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n, ctypes.byref(step)))
+        return out, step.value
+
+    def set_state(self, flat, step: int):
+        import numpy as np
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self.ctx.check(load_library().px_cnn_set_state(
+            self.handle, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), flat.size, int(step)))
 
     def forward(self, x, y, stream=None):
         B, H, W = x.shape

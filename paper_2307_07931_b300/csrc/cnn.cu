@@ -893,6 +893,37 @@ px_status px_cnn_set_params(px_cnn* n, const float* host, size_t count) {
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "set params");
 }
 
+size_t px_cnn_state_count(void) { return 3 * kOff.total; }
+
+// Training state for checkpoints: FP32 parameters, Adam first and second
+// moments (each px_cnn_param_count() floats, in that order) and the step.
+px_status px_cnn_get_state(px_cnn* n, float* host, size_t count, int64_t* step) {
+  if (!n || !host || !step || count != 3 * kOff.total) return PX_EINVAL;
+  DevScope ds(n->ctx->device);
+  const size_t P = kOff.total;
+  cudaError_t e = cudaMemcpy(host, n->params, P * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(host + P, n->m, P * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(host + 2 * P, n->v, P * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cnn_cuda(n, e, "get state");
+  *step = n->step;
+  return PX_OK;
+}
+
+px_status px_cnn_set_state(px_cnn* n, const float* host, size_t count, int64_t step) {
+  if (!n || !host || count != 3 * kOff.total || step < 0) return PX_EINVAL;
+  DevScope ds(n->ctx->device);
+  const size_t P = kOff.total;
+  cudaError_t e = cudaMemcpy(n->params, host, P * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(n->m, host + P, P * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(n->v, host + 2 * P, P * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cnn_cuda(n, e, "set state");
+  n->step = step;
+  px_status s = repack(n, 0);
+  if (s != PX_OK) return s;
+  e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "set state");
+}
+
 px_status px_cnn_forward(px_cnn* n, const float* x, float* y, int B, int H, int W, void* stream) {
   if (!n || !x || !y) return PX_EINVAL;
   n->ctx->err.clear();

@@ -97,12 +97,40 @@ def augment(torch, x, t, rng):
     return x, t
 
 
-def train(px, torch, net, X, T, steps: int, batch: int, lr0: float, seed: int, log):
+def save_checkpoint(path: str, net, step: int, rng, hist):
+    """Parameters, Adam moments and step of the network, the data-order RNG
+    state and the loss history, written atomically."""
+    state, adam_step = net.state()
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, state=state, adam_step=adam_step, step=step,
+             rng=json.dumps(rng.bit_generator.state), hist=np.array(hist, dtype=np.float64))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path: str, net, rng):
+    z = np.load(path)
+    net.set_state(z["state"], int(z["adam_step"]))
+    rng.bit_generator.state = json.loads(str(z["rng"]))
+    hist = [tuple(v) for v in z["hist"].tolist()]
+    return int(z["step"]), hist
+
+
+def train(px, torch, net, X, T, steps: int, batch: int, lr0: float, seed: int, log,
+          ckpt: str | None = None, ckpt_every: int = 0, stop_at: int | None = None):
+    """Adam with cosine decay. With `ckpt`, the full training state is written
+    every `ckpt_every` steps and an existing checkpoint is resumed; a resumed run
+    continues bit for bit as the uninterrupted one (fixed-order reductions, the
+    same batch indices and augmentations from the restored RNG). `stop_at` ends
+    the run early at that step (an interrupted run)."""
     rng = np.random.default_rng(seed)
     ntrain = X.shape[0]
     hist = []
+    start = 0
+    if ckpt and os.path.exists(ckpt):
+        start, hist = load_checkpoint(ckpt, net, rng)
+        log(f"resumed from {ckpt} at step {start}")
     t0 = time.perf_counter()
-    for s in range(steps):
+    for s in range(start, steps):
         idx = torch.from_numpy(rng.integers(0, ntrain, batch)).cuda()
         xb, tb = augment(torch, X.index_select(0, idx), T.index_select(0, idx), rng)
         lr = 1e-5 + 0.5 * (lr0 - 1e-5) * (1 + math.cos(math.pi * s / max(1, steps)))
@@ -111,6 +139,10 @@ def train(px, torch, net, X, T, steps: int, batch: int, lr0: float, seed: int, l
         if want:
             hist.append((s, loss))
             log(f"step {s} loss {loss:.4e} lr {lr:.2e} {time.perf_counter() - t0:.1f}s")
+        if ckpt and ckpt_every > 0 and (s + 1) % ckpt_every == 0:
+            save_checkpoint(ckpt, net, s + 1, rng, hist)
+        if stop_at is not None and s + 1 >= stop_at:
+            break
     torch.cuda.synchronize()
     return hist, time.perf_counter() - t0
 
@@ -157,6 +189,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--timed", type=int, default=32)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--ckpt", default=None, help="checkpoint file (.npz); resumed if present")
+    ap.add_argument("--ckpt-every", type=int, default=1000)
     ap.add_argument("--dilations", default="1,3,9,27,81,1",
                     help="per-layer dilations of the 3x3 layers ('1,1,1,1,1,1' = plain)")
     a = ap.parse_args()
@@ -197,7 +231,8 @@ def main():
     # Jacobi from 0 keeps the mean of phi at 0 (the zero mode has gain 1 and
     # rho is mean-zero), so the targets are already the mean-zero solution.
     del phi_tr
-    hist, tsec = train(px, torch, net, X, T, a.steps, a.batch, a.lr, a.seed, log)
+    hist, tsec = train(px, torch, net, X, T, a.steps, a.batch, a.lr, a.seed, log,
+                       ckpt=a.ckpt, ckpt_every=a.ckpt_every)
     res["train"] = {"steps": a.steps, "batch": a.batch, "seconds": tsec,
                     "ms_per_step": 1000 * tsec / max(1, a.steps), "loss_history": hist}
     np.save(os.path.join(a.out, "learned_guess_params.npy"), net.params())

@@ -158,3 +158,16 @@ def test_batched_workload_full_size(px):
         sc = 8 * np.max(np.abs(ref)) / h**2 + np.max(np.abs(hostr[i]))
         assert np.max(np.abs(res[i] - R)) <= tol * sc, (i, n, d)
     b.close()
+
+
+def test_plan_reports_allocation_failure(px):
+    """A plan whose BANDED scratch cannot be allocated returns PX_ENOMEM at plan
+    time, before anything is launched (the allocation failure is made on the
+    host side by the size of the request)."""
+    n = 1 << 29
+    with pytest.raises(px.PxError) as ei:
+        px.Batch([px.Grid(n, n, n, 0, px.PX_F32, 1.0 / n)], 2)
+    assert ei.value.status == px.PX_ENOMEM
+    # the context stays usable
+    b = px.Batch([px.Grid(64, 64, 64, 0, px.PX_F32, 1 / 64)], 2)
+    b.close()

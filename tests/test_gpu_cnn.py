@@ -145,3 +145,29 @@ def test_unsupported_shapes(px):
         net.forward(x, torch.empty_like(x))
     assert ei.value.status == px.PX_EUNSUPPORTED
     net.close()
+
+
+def test_checkpoint_resume_is_bitwise(px, tmp_path):
+    """Training interrupted after 3 of 6 steps and resumed from its checkpoint
+    (parameters, Adam moments, step, data-order RNG) ends in exactly the state
+    of an uninterrupted 6-step run."""
+    from paper_2307_07931_b300 import learned
+    rng = np.random.default_rng(31)
+    X = torch.from_numpy(rng.standard_normal((8, 64, 64)).astype(np.float32)).cuda()
+    T = torch.from_numpy(0.1 * rng.standard_normal((8, 64, 64)).astype(np.float32)).cuda()
+    dil = (1, 2, 3, 2, 1, 1)
+    ck = str(tmp_path / "ck.npz")
+    log = lambda m: None
+    a = px.Cnn(seed=1, dilations=dil)
+    learned.train(px, torch, a, X, T, 6, 4, 1e-3, 5, log, ckpt=ck, ckpt_every=3, stop_at=3)
+    a.close()
+    b = px.Cnn(seed=99, dilations=dil)  # different init: everything comes from the checkpoint
+    learned.train(px, torch, b, X, T, 6, 4, 1e-3, 5, log, ckpt=ck, ckpt_every=3)
+    c = px.Cnn(seed=1, dilations=dil)
+    learned.train(px, torch, c, X, T, 6, 4, 1e-3, 5, log)
+    sb, stb = b.state()
+    sc, stc = c.state()
+    assert stb == stc == 6
+    assert np.array_equal(sb, sc)
+    b.close()
+    c.close()
