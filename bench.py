@@ -36,14 +36,16 @@ BATCH_SWEEPS = 300  # sweeps per instance of the batched workload
 OMEGA = 2.0 / 3.0
 ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cell per launch
 # DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
-# (profiles/relaxW2_f32_6144.md: dram read + write of one 6144^2 launch / cells).
-MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (325.220608e6 + 120.491776e6) / 6144**2}
+# (empty until the current kernel has been captured: traffic is then null).
+MEASURED_TRAFFIC_PER_CELL = {}
 
 
 def kernel_name(dt: str, tb: int) -> str:
     if tb == 1:
         return "relax1_stream<float,4>" if dt == "f32" else "relax1_stream<double,2>"
-    return f"relaxW2_f32<{tb}>" if dt == "f32" else f"relaxT_tile<double,{tb}>"
+    if dt == "f64":
+        return f"relaxT_tile<double,{tb}>"
+    return f"relaxR_f32<{tb},4>" if tb in (3, 4) else f"relaxW2_f32<{tb}>"
 
 
 def peaks():

@@ -33,7 +33,11 @@
  *    launched and px_last_error() holds a one-line message. Asynchronous
  *    device errors surface as PX_ECUDA from the next synchronising call.
  *  - A ctx is bound to the device given at creation. It is not thread-safe:
- *    one host thread at a time per ctx.
+ *    one host thread at a time per ctx. Work enqueued through one ctx must
+ *    not overlap on the GPU (several streams at once): calls share its
+ *    scratch field, reduction slots and the small array through which the
+ *    warps of one relaxation launch balance their work. Use one ctx per
+ *    concurrently running stream.
  */
 #ifndef PROTOX_H
 #define PROTOX_H

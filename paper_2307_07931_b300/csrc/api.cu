@@ -90,6 +90,12 @@ bool overlap(const void* a, const void* b, size_t n) {
   return n > 0 && x < y + n && y < x + n;
 }
 
+// Whether [a, a + na) and [b, b + nb) share a byte.
+bool overlap2(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na > 0 && nb > 0 && x < y + nb && y < x + na;
+}
+
 px_status ensure_scratch(px_ctx* c, size_t bytes) {
   if (c->scratch_bytes >= bytes) return PX_OK;
   if (c->scratch) cudaFree(c->scratch);
@@ -150,6 +156,9 @@ px_status unbound_check_grid(const px_grid* g, FieldDesc* f) { return check_grid
 px_status unbound_fail(px_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
 size_t field_bytes(const FieldDesc& f) { return field_span(f); }
 bool ranges_overlap(const void* a, const void* b, size_t n) { return overlap(a, b, n); }
+bool ranges_overlap2(const void* a, size_t na, const void* b, size_t nb) {
+  return overlap2(a, na, b, nb);
+}
 std::vector<int> plan_relax_launches(const FieldDesc& f, bool vec, bool inplace, int nsweeps,
                                      int tblock, bool* copy_first) {
   return plan_launches(f, vec, inplace, nsweeps, tblock, copy_first);
@@ -190,9 +199,20 @@ px_status px_create(px_ctx** out, int device) {
   c->device = device;
   e = cudaMalloc(&c->red, (8 + (size_t)px::sum_partials_count()) * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, 4 * sizeof(double));
+  // load-balance words: one per resident warp at most (64 warps per SM)
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    c->sched_cap = 64 * sms;
+    e = cudaMalloc(&c->sched, sizeof(unsigned long long) * (size_t)c->sched_cap);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemset(c->sched, 0, sizeof(unsigned long long) * (size_t)c->sched_cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->red) cudaFree(c->red);
+    if (c->red_host) cudaFreeHost(c->red_host);
+    if (c->sched) cudaFree(c->sched);
     delete c;
     return fail(nullptr, PX_ENOMEM, "context buffers: %s", cudaGetErrorString(e));
   }
@@ -208,6 +228,7 @@ px_status px_destroy(px_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->red) cudaFree(c->red);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->sched) cudaFree(c->sched);
   delete c;
   return PX_OK;
 }
@@ -245,21 +266,24 @@ px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
   if (!std::isfinite(omega)) return fail(c, PX_EINVAL, "omega must be finite");
   const bool reports = resid_dev && report_every > 0 && nsweeps > 0;
   const int nrep = reports ? (nsweeps + report_every - 1) / report_every : 0;
+  const bool empty = f.nx == 0 || f.ny == 0;
+  const size_t span = field_span(f);
+  const bool inplace = phi_in == phi_out;
+  if (!empty) {
+    if (!phi_in || !phi_out || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
+    if (!inplace && overlap(phi_in, phi_out, span))
+      return fail(c, PX_EINVAL, "phi_in and phi_out overlap without being equal");
+    if (overlap(rho, phi_out, span)) return fail(c, PX_EINVAL, "rho overlaps phi_out");
+    if (reports && overlap2(resid_dev, sizeof(double) * (size_t)nrep, phi_out, span))
+      return fail(c, PX_EINVAL, "resid_dev overlaps phi_out");
+  }
   DeviceScope ds(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   if (reports) {
     cudaError_t e = cudaMemsetAsync(resid_dev, 0, sizeof(double) * (size_t)nrep, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "clear resid_dev");
   }
-  if (f.nx == 0 || f.ny == 0) return PX_OK;
-  if (!phi_in || !phi_out || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
-  const size_t span = field_span(f);
-  const bool inplace = phi_in == phi_out;
-  if (!inplace && overlap(phi_in, phi_out, span))
-    return fail(c, PX_EINVAL, "phi_in and phi_out overlap without being equal");
-  if (overlap(rho, phi_out, span)) return fail(c, PX_EINVAL, "rho overlaps phi_out");
-  if (reports && overlap(resid_dev, phi_out, span))
-    return fail(c, PX_EINVAL, "resid_dev overlaps phi_out");
+  if (empty) return PX_OK;
 
   if (nsweeps == 0) {
     if (inplace) return PX_OK;
@@ -289,7 +313,8 @@ px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
   for (size_t k = 0; k < L; ++k) {
     void* dst = ((L - 1 - k) % 2 == 0) ? phi_out : scratch;
     cudaError_t e = px::launch_relax(f, src, dst, rho, omega, sizes[k], vec_all,
-                                     reports ? resid_dev : nullptr, s0, report_every, st);
+                                     reports ? resid_dev : nullptr, s0, report_every,
+                                     c->sched, c->sched_cap, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "relax launch");
     s0 += sizes[k];
     src = dst;

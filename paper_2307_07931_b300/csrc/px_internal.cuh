@@ -88,9 +88,13 @@ struct FieldDesc {
 bool vector_ok(const FieldDesc& f, const void* a, const void* b, const void* c);
 
 // One launch of `tb` fused sweeps (tb in 1..8) reading src, writing dst.
+// sched: sched_cap zero-initialised 64-bit words for the dynamic load balance
+// of the FP32 depth-3/4 kernel (left all-exhausted on exit, so reusable by the
+// next launch in stream order), or NULL for static shares.
 cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst,
                          const void* rho, double omega, int tb, bool vec,
-                         double* resid, int s0, int every, cudaStream_t st);
+                         double* resid, int s0, int every, unsigned long long* sched,
+                         int sched_cap, cudaStream_t st);
 
 cudaError_t launch_apply_stencil(const FieldDesc& f, const void* phi, void* out,
                                  cudaStream_t st);
@@ -130,6 +134,8 @@ struct px_ctx {
   double* red_host = nullptr;  // pinned mirror of red[0..3]
   void* ws = nullptr;        // solve workspace: FP32 r and e fields
   size_t ws_bytes = 0;
+  unsigned long long* sched = nullptr;  // load-balance words of the relax kernels
+  int sched_cap = 0;
   std::string err;
 };
 
@@ -142,6 +148,7 @@ px_status unbound_check_grid(const px_grid* g, FieldDesc* f);
 px_status unbound_fail(px_status s, const char* msg);
 size_t field_bytes(const FieldDesc& f);
 bool ranges_overlap(const void* a, const void* b, size_t n);
+bool ranges_overlap2(const void* a, size_t na, const void* b, size_t nb);
 std::vector<int> plan_relax_launches(const FieldDesc& f, bool vec, bool inplace, int nsweeps,
                                      int tblock, bool* copy_first);
 // Error reporting and grid validation on a context (api.cu).

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 namespace px {
 
@@ -739,14 +740,377 @@ cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, con
 }
 
 // 2 = relaxW2_f32 (default), 1 = relaxW_f32; PX_WAVE_ROWS selects for A/B timing.
-int wave_rows() {
-  static int v = 0;
-  if (v == 0) {
-    const char* e = getenv("PX_WAVE_ROWS");
-    v = (e && e[0] == '1') ? 1 : 2;
+// FP32 kernel family for depth >= 2, from PX_FP32_WAVE: "w1" the one-row
+// wavefront, "w2" the two-row wavefront, anything else (the default) the
+// fastest measured per depth (16384^2, a report every sweep): the register
+// wavefront for depths 3 and 4, the one-row wavefront for 6 and 7, the
+// two-row wavefront for 2, 5 and 8.
+int wave_kernel() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("PX_FP32_WAVE");
+    v = (e && !strcmp(e, "w1")) ? 1 : (e && !strcmp(e, "w2")) ? 2 : 0;
   }
   return v;
 }
+
+// ---------------------------------------------------------------------------
+// relaxR2_f32: register wavefront, TB = 3 or 4 sweeps per launch, no shared
+// tiles and no CTA barriers.
+//
+// One warp owns a strip of 128 cells (4 per lane, periodic columns x0 - 4 ..
+// x0 + 123) and a range of output rows, and runs every stage itself. Step s
+// brings level-0 rows r0 = 2s and r0 + 1 into registers; stage t (t = 1..TB,
+// in order) then computes level-t rows r0 - t and r0 - t + 1 from level t-1
+// rows r0 - t - 1 .. r0 - t + 2, the newest two of which stage t-1 produced
+// in this step. Each level keeps a four-row window in registers (slot = row
+// mod 4) and the step loop is unrolled by two, so the window rotation is
+// register renaming; the per-step work that is not arithmetic (ring slots,
+// cp.async, waits, addresses, predicates) is shared by two rows. x neighbours
+// come from shuffles. Rows and columns outside the valid cone (one cell and
+// one row smaller per stage) are computed and discarded: the strip owns its
+// central 120 columns (lanes 1..30) and the range's own rows.
+//
+// phi and rho rows stream through per-warp shared-memory rings filled by
+// cp.async kR2Ahead row pairs ahead; each lane copies and reads back only its
+// own 16 bytes, so the thread's own cp.async.wait_group is the only wait.
+//
+// Residual. The state t-1 residual of a row is exact once level t-1 is exact
+// on the row and its two neighbours: from row index t on at the top, and at
+// the bottom always (stage t reads no row beyond the newest loaded one).
+// Exact values of rows and wrapped columns outside the owned ones are
+// residuals of real cells, so including them leaves the max unchanged; only
+// the two edge lanes, whose x neighbours are garbage from the first stage on,
+// are dropped, once, before the warp reduction.
+//
+// Load balance. SMs run this kernel at different speeds (how many warps share
+// the SM, where its GPC sits), so equal static shares leave fast warps idle.
+// Each warp starts with one static range of output rows of one strip and
+// publishes it as one 64-bit word (strip, end, cur) in `sched`; it claims its
+// rows kRClaim at a time with atomicAdd on cur. A warp whose range is done
+// samples 32 words, picks the one with the most unclaimed rows and, with a
+// bounded atomicCAS loop, lowers that range's end to its midpoint and takes
+// the upper half as its own new range (a fresh wavefront: 2 TB extra rows).
+// The owner sees the lower end at its next claim. Nothing waits on another
+// warp: every loop is bounded, and a failed steal ends the warp. Without
+// `sched` the static ranges are used as they are.
+constexpr int kRHalo = 4;                       // halo columns per side (one lane)
+constexpr int kRStrip = 128, kROwned = kRStrip - 2 * kRHalo;
+constexpr int kRPhiRing = 8, kRRhoRing = 16;    // ring rows (powers of two)
+constexpr int kRWarps = 8;                      // warps per CTA
+constexpr int kRWarpFloats = (kRPhiRing + kRRhoRing) * kRStrip;
+constexpr size_t kRSmem = (size_t)kRWarps * kRWarpFloats * sizeof(float);
+
+__device__ __forceinline__ void cp16(float* sdst, const float* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// max(m, |a|, |b|) with NaN propagation (any NaN input gives NaN).
+__device__ __forceinline__ float max3_nan_abs(float m, float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(m), "f"(fabsf(a)), "f"(fabsf(b)));
+  return r;
+}
+
+constexpr int kR2Ahead = 3;     // row pairs in flight ahead of the step
+constexpr int kRClaim = 16;     // output rows per claim (even)
+constexpr int kRStealMin = 64;  // steal only ranges with this many rows unclaimed
+static_assert(2 * kR2Ahead + 2 <= kRPhiRing && 2 * kR2Ahead + 2 + 4 <= kRRhoRing,
+              "two-row prefetch depth exceeds the rings");
+static_assert(kRClaim % 2 == 0, "claims keep the row-pair parity");
+
+// Range word: bits 0..21 cur (next unclaimed row), 22..43 end, 44..63 strip.
+constexpr int kRRowBits = 22, kRStripBits = 20;
+__device__ __forceinline__ unsigned long long range_pack(int s, int e, int c) {
+  return ((unsigned long long)s << 44) | ((unsigned long long)e << 22) | (unsigned long long)c;
+}
+__device__ __forceinline__ int range_cur(unsigned long long w) { return (int)(w & 0x3fffffu); }
+__device__ __forceinline__ int range_end(unsigned long long w) { return (int)((w >> 22) & 0x3fffffu); }
+__device__ __forceinline__ int range_strip(unsigned long long w) { return (int)(w >> 44); }
+
+template <int TB>
+struct R2State {
+  float win[TB][4][4];  // level l (input of stage l+1): slot = row mod 4
+  float mx[TB];         // running max |residual| of state t (NaN-sticky)
+  int rl;               // global row of the next row to load
+};
+
+// One task's bounds: output rows y0 .. lim-1 are claimed; level-0 load
+// indices up to lmax may be loaded (rows up to the known end + TB).
+struct R2Task {
+  int y0, lim, lmax;
+};
+
+template <int TB, int P, bool kEdge>
+__device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
+                                       const float* __restrict__ rho, float* __restrict__ out,
+                                       float* ring, int ny, int64_t ld, int gx, bool own,
+                                       const R2Task& T, Coef<float> k, const bool (&due)[TB]) {
+  constexpr int W = 128;                      // strip floats per ring row
+  float* const pr = ring;                     // phi ring, this lane's columns
+  float* const rr_ = ring + kRPhiRing * W;    // rho ring
+  const int la = r0 + 2 * kR2Ahead;           // first row of the pair to load
+  if (la <= T.lmax) {
+    const int64_t g0 = (int64_t)S.rl * ld + gx;
+    S.rl = S.rl + 1 == ny ? 0 : S.rl + 1;
+    const int64_t g1 = (int64_t)S.rl * ld + gx;
+    S.rl = S.rl + 1 == ny ? 0 : S.rl + 1;
+    cp16(pr + (la & (kRPhiRing - 1)) * W, phi + g0);
+    cp16(pr + ((la + 1) & (kRPhiRing - 1)) * W, phi + g1);
+    cp16(rr_ + (la & (kRRhoRing - 1)) * W, rho + g0);
+    cp16(rr_ + ((la + 1) & (kRRhoRing - 1)) * W, rho + g1);
+  }
+  cp_commit();
+  cp_wait<kR2Ahead>();
+  lds4(S.win[0][2 * P], pr + (r0 & (kRPhiRing - 1)) * W);
+  lds4(S.win[0][2 * P + 1], pr + ((r0 + 1) & (kRPhiRing - 1)) * W);
+#pragma unroll
+  for (int t = 1; t <= TB; ++t) {
+    // level t-1 rows r0-t-1 .. r0-t+2; r0 mod 4 = 2P
+    const float* a = S.win[t - 1][(2 * P - t - 1 + 8) & 3];
+    const float* b = S.win[t - 1][(2 * P - t + 8) & 3];
+    const float* c = S.win[t - 1][(2 * P - t + 1 + 8) & 3];
+    const float* d = S.win[t - 1][(2 * P - t + 2 + 8) & 3];
+    float rh0[4], rh1[4];
+    lds4(rh0, rr_ + ((r0 - t) & (kRRhoRing - 1)) * W);
+    lds4(rh1, rr_ + ((r0 - t + 1) & (kRRhoRing - 1)) * W);
+    const float bl = __shfl_up_sync(0xffffffffu, b[3], 1);
+    const float br = __shfl_down_sync(0xffffffffu, b[0], 1);
+    const float cl = __shfl_up_sync(0xffffffffu, c[3], 1);
+    const float cr = __shfl_down_sync(0xffffffffu, c[0], 1);
+    float o0[4], o1[4], q0[4], q1[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const float w0 = x == 0 ? bl : b[x - 1], e0 = x == 3 ? br : b[x + 1];
+      const float w1 = x == 0 ? cl : c[x - 1], e1 = x == 3 ? cr : c[x + 1];
+      const float s0 = fmaf(-4.0f, b[x], (w0 + e0) + (a[x] + c[x]));
+      const float s1 = fmaf(-4.0f, c[x], (w1 + e1) + (b[x] + d[x]));
+      q0[x] = fmaf(s0, k.ih2, -rh0[x]);
+      q1[x] = fmaf(s1, k.ih2, -rh1[x]);
+      o0[x] = fmaf(k.c, q0[x], b[x]);
+      o1[x] = fmaf(k.c, q1[x], c[x]);
+    }
+    // Residual of state t-1 at rows r0-t, r0-t+1: exact once the row index
+    // is >= t (level t-1 is exact from index t-1 on, and at the bottom every
+    // computed row is exact because stage t reads rows up to r0 + 1 only).
+    // Exact values of rows outside the task are residuals of real cells, so
+    // including them leaves the max unchanged.
+    if (due[t - 1]) {
+      if (!kEdge || r0 >= 2 * t) {
+        S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q0[0], q0[1]);
+        S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q0[2], q0[3]);
+      }
+      if (!kEdge || r0 + 1 >= 2 * t) {
+        S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q1[0], q1[1]);
+        S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q1[2], q1[3]);
+      }
+    }
+    if (t < TB) {
+      float* d0 = S.win[t][(2 * P - t + 8) & 3];      // level-t row r0 - t
+      float* d1 = S.win[t][(2 * P - t + 1 + 8) & 3];  // level-t row r0 - t + 1
+#pragma unroll
+      for (int x = 0; x < 4; ++x) { d0[x] = o0[x]; d1[x] = o1[x]; }
+    } else if (own) {
+      // level-TB row index j is global row y0 + j - TB
+      const int yo = T.y0 + r0 - 2 * TB;
+      if (yo >= T.y0 && yo < T.lim)
+        *reinterpret_cast<float4*>(out + (int64_t)yo * ld + gx) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+      if (yo + 1 >= T.y0 && yo + 1 < T.lim)
+        *reinterpret_cast<float4*>(out + (int64_t)(yo + 1) * ld + gx) =
+            make_float4(o1[0], o1[1], o1[2], o1[3]);
+    }
+  }
+}
+
+// Claims the next kRClaim output rows of the warp's own range; false when the
+// range is exhausted. Updates the claimed bound and the known end.
+template <int TB>
+__device__ __forceinline__ bool r2_claim(unsigned long long* word, R2Task& T) {
+  unsigned long long old = 0;
+  if ((threadIdx.x & 31) == 0) old = atomicAdd(word, (unsigned long long)kRClaim);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  const int c = range_cur(old), e = range_end(old);
+  if (c >= e) return false;
+  T.lim = min(c + kRClaim, e);
+  T.lmax = e - T.y0 + 2 * TB;
+  return true;
+}
+
+// Steals the upper half of the unclaimed rows of some other warp's range.
+__device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips, int ny, int& s,
+                         int& y0, int& e) {
+  const int lane = threadIdx.x & 31;
+  const int stride = (nw + 31) / 32;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    const int v = (int)(((int64_t)me + 1 + (int64_t)lane * stride + 7 * attempt) % nw);
+    const unsigned long long wv = *reinterpret_cast<volatile unsigned long long*>(sched + v);
+    int best = range_end(wv) - range_cur(wv), bl = lane;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const int r2 = __shfl_xor_sync(0xffffffffu, best, o), l2 = __shfl_xor_sync(0xffffffffu, bl, o);
+      if (r2 > best || (r2 == best && l2 < bl)) { best = r2; bl = l2; }
+    }
+    if (best < kRStealMin) continue;
+    const int vb = __shfl_sync(0xffffffffu, v, bl);
+    int ok = 0, ns = 0, nb = 0, ne = 0;
+    if (lane == 0) {
+      unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(sched + vb);
+      for (int tries = 0; tries < 8; ++tries) {
+        const int c = range_cur(old), en = range_end(old), st = range_strip(old);
+        // a range from another geometry (never expected) is left alone
+        if (en - c < kRStealMin || st >= nstrips || en > ny) break;
+        const int mid = c + (((en - c) / 2) & ~1);  // even offset keeps the pair parity
+        const unsigned long long got = atomicCAS(sched + vb, old, range_pack(st, mid, c));
+        if (got == old) { ok = 1; ns = st; nb = mid; ne = en; break; }
+        old = got;
+      }
+      if (ok) atomicExch(sched + me, range_pack(ns, ne, nb));
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+      s = __shfl_sync(0xffffffffu, ns, 0);
+      y0 = __shfl_sync(0xffffffffu, nb, 0);
+      e = __shfl_sync(0xffffffffu, ne, 0);
+      return true;
+    }
+  }
+  return false;
+}
+
+template <int TB>
+__global__ void __launch_bounds__(kRWarps * 32)
+relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
+            int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
+            unsigned long long* sched) {
+  extern __shared__ __align__(16) float rsm[];
+  const int lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  float* const ring = rsm + (threadIdx.x >> 5) * kRWarpFloats + lane * 4;
+  bool due[TB];
+#pragma unroll
+  for (int t = 0; t < TB; ++t) due[t] = rep.due(t);
+  R2State<TB> S;
+#pragma unroll
+  for (int t = 0; t < TB; ++t) S.mx[t] = 0.f;
+  const int ntasks = nstrips * nseg;
+  int task = gw, s = 0, y0 = 0, e = 0;
+  bool have = task < ntasks;
+  if (have) { s = task % nstrips; y0 = (task / nstrips) * H; e = min(y0 + H, ny); }
+  // with sched, every warp publishes its range (empty if none) before anything else
+  if (sched && lane == 0) atomicExch(sched + gw, have ? range_pack(s, e, y0) : 0ull);
+  for (int guard = 0; guard < (1 << 24); ++guard) {
+    if (!have) {
+      if (sched) {
+        have = r2_steal(sched, gw, nw, nstrips, ny, s, y0, e);
+      } else if ((task += nw) < ntasks) {  // static grid stride
+        s = task % nstrips; y0 = (task / nstrips) * H; e = min(y0 + H, ny); have = true;
+      }
+      if (!have) break;
+    }
+    const int col = s * kROwned - kRHalo + lane * 4;
+    const int gx = wrapn(col, nx);
+    const bool own = lane > 0 && lane < 31 && col < nx;
+    R2Task T;
+    T.y0 = y0;
+    T.lim = sched ? y0 : e;  // with sched, rows are claimed as the wavefront reaches them
+    T.lmax = e - y0 + 2 * TB;
+#pragma unroll
+    for (int t = 0; t < TB; ++t)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int x = 0; x < 4; ++x) S.win[t][a][x] = 0.f;
+    int rl = wrapn(y0 - TB, ny);
+#pragma unroll
+    for (int q = 0; q < 2 * kR2Ahead; q += 2) {
+      if (q <= T.lmax) {
+        const int64_t g0 = (int64_t)rl * ld + gx;
+        rl = rl + 1 == ny ? 0 : rl + 1;
+        const int64_t g1 = (int64_t)rl * ld + gx;
+        rl = rl + 1 == ny ? 0 : rl + 1;
+        cp16(ring + (q & (kRPhiRing - 1)) * 128, phi + g0);
+        cp16(ring + ((q + 1) & (kRPhiRing - 1)) * 128, phi + g1);
+        cp16(ring + kRPhiRing * 128 + (q & (kRRhoRing - 1)) * 128, rho + g0);
+        cp16(ring + kRPhiRing * 128 + ((q + 1) & (kRRhoRing - 1)) * 128, rho + g1);
+      }
+      cp_commit();
+    }
+    S.rl = rl;
+    unsigned long long* const word = sched ? sched + gw : nullptr;
+    // a step at r0 outputs rows y0 + r0 - 2 TB (+1); claim before passing lim
+    auto ready = [&](int r0) -> bool {
+      const int yo = y0 + r0 - 2 * TB;
+      if (yo < T.lim) return true;
+      return word != nullptr && r2_claim<TB>(word, T);
+    };
+    constexpr int kPro = 2 * TB;  // r0 < 2 TB: residual rows not yet all exact
+    int r0 = 0;
+#pragma unroll 1
+    for (; r0 < kPro; r0 += 4) {
+      if (!ready(r0)) goto task_done;
+      rstep2<TB, 0, true>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      if (!ready(r0 + 2)) goto task_done;
+      rstep2<TB, 1, true>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+    }
+#pragma unroll 1
+    for (;; r0 += 4) {
+      if (!ready(r0)) break;
+      rstep2<TB, 0, false>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      if (!ready(r0 + 2)) break;
+      rstep2<TB, 1, false>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+    }
+  task_done:
+    cp_wait<0>();  // the next task's prologue reuses the ring slots
+    have = false;
+  }
+  const bool edge_lane = lane == 0 || lane == 31;
+#pragma unroll
+  for (int t = 0; t < TB; ++t) {
+    if (due[t]) {
+      const uint32_t m = warp_max(edge_lane ? 0u : __float_as_uint(S.mx[t]));
+      if (lane == 0) atomic_max_bits(rep.slot(t), to_f64_bits(m));
+    }
+  }
+}
+
+template <int TB>
+cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
+                          Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
+                          cudaStream_t st) {
+  static int occ = 0;
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB>, kRWarps * 32, kRSmem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int nstrips = (f.nx + kROwned - 1) / kROwned;
+  const int64_t resident = (int64_t)occ * device_sm_count();
+  const int64_t warps = resident * kRWarps;
+  // Dynamic balance needs one range per warp at most and rows that fit the
+  // range word; otherwise ranges are static (grid stride over tasks).
+  const bool dyn = sched != nullptr && warps <= sched_cap && nstrips <= warps &&
+                   nstrips < (1 << kRStripBits) && (int64_t)f.ny + kRClaim < (1 << kRRowBits);
+  // One range per resident warp, at least 32 rows (the ramp costs 2 TB rows).
+  const int64_t segs = std::max<int64_t>(1, warps / nstrips);
+  int64_t H = std::max<int64_t>(32, (f.ny + segs - 1) / segs);
+  if (!dyn) H = std::min<int64_t>(1024, H);
+  const int nseg = (int)((f.ny + H - 1) / H);
+  const int64_t tasks = (int64_t)nstrips * nseg;
+  const int blocks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((tasks + kRWarps - 1) / kRWarps, resident));
+  relaxR2_f32<TB><<<blocks, kRWarps * 32, kRSmem, st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
+                                                        nstrips, nseg, k, rep, dyn ? sched : nullptr);
+  return cudaGetLastError();
+}
+
 
 template <int TB>
 cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
@@ -783,7 +1147,8 @@ cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, cons
 
 template <typename T>
 cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
-                           double omega, int tb, bool vec, Reports rep, cudaStream_t st) {
+                           double omega, int tb, bool vec, Reports rep,
+                           unsigned long long* sched, int sched_cap, cudaStream_t st) {
   Coef<T> k;
   k.c = (T)(omega * f.h * f.h / 4.0);
   k.ih2 = (T)(1.0 / (f.h * f.h));
@@ -799,7 +1164,11 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
              : launch_stream_t<T, 1, false>(f, src, dst, rho, k, slot, st);
   }
   if constexpr (sizeof(T) == 4) {
-    if (wave_rows() == 2) {
+    const int fam = wave_kernel();
+    if (fam == 0 && (tb == 3 || tb == 4))
+      return tb == 3 ? launch_reg2_t<3>(f, src, dst, rho, k, rep, sched, sched_cap, st)
+                     : launch_reg2_t<4>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    if (fam == 2 || (fam == 0 && tb != 6 && tb != 7)) {
       switch (tb) {
         case 2: return launch_wave2_t<2>(f, src, dst, rho, k, rep, st);
         case 3: return launch_wave2_t<3>(f, src, dst, rho, k, rep, st);
@@ -858,7 +1227,7 @@ bool vector_ok(const FieldDesc& f, const void* a, const void* b, const void* c) 
 
 cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst, const void* rho,
                          double omega, int tb, bool vec, double* resid, int s0,
-                         int every, cudaStream_t st) {
+                         int every, unsigned long long* sched, int sched_cap, cudaStream_t st) {
   Reports rep;
   rep.resid = (resid && every > 0) ? resid : nullptr;
   rep.s0 = s0;
@@ -866,9 +1235,9 @@ cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst, const v
   if (!vec) tb = 1;
   if (f.dtype == 0)
     return launch_relax_t<double>(f, (const double*)src, (double*)dst, (const double*)rho,
-                                  omega, tb, vec, rep, st);
+                                  omega, tb, vec, rep, sched, sched_cap, st);
   return launch_relax_t<float>(f, (const float*)src, (float*)dst, (const float*)rho, omega,
-                               tb, vec, rep, st);
+                               tb, vec, rep, sched, sched_cap, st);
 }
 
 }  // namespace px

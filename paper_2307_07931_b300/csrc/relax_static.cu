@@ -89,6 +89,19 @@ extern "C" px_status px_relax_n_static(const px_grid* g, const void* phi_in, voi
                             "tblock in 0..8 and a finite omega");
   const bool reports = resid_dev && report_every > 0 && nsweeps > 0;
   const int nrep = reports ? (nsweeps + report_every - 1) / report_every : 0;
+  const bool empty = f.nx == 0 || f.ny == 0;
+  const bool inplace = phi_in == phi_out;
+  if (!empty) {
+    if (!phi_in || !phi_out || !rho)
+      return px::unbound_fail(PX_EINVAL, "px_relax_n_static: NULL field pointer");
+    if (!inplace && px::ranges_overlap(phi_in, phi_out, span))
+      return px::unbound_fail(PX_EINVAL,
+                              "px_relax_n_static: phi_in and phi_out overlap without being equal");
+    if (px::ranges_overlap(rho, phi_out, span))
+      return px::unbound_fail(PX_EINVAL, "px_relax_n_static: rho overlaps phi_out");
+    if (reports && px::ranges_overlap2(resid_dev, sizeof(double) * (size_t)nrep, phi_out, span))
+      return px::unbound_fail(PX_EINVAL, "px_relax_n_static: resid_dev overlaps phi_out");
+  }
   void* scratch = nullptr;
   s = static_scratch(&scratch);
   if (s != PX_OK) return s;
@@ -97,17 +110,7 @@ extern "C" px_status px_relax_n_static(const px_grid* g, const void* phi_in, voi
     cudaError_t e = cudaMemsetAsync(resid_dev, 0, sizeof(double) * (size_t)nrep, st);
     if (e != cudaSuccess) return launch_error(e, "clear resid_dev");
   }
-  if (f.nx == 0 || f.ny == 0) return PX_OK;
-  if (!phi_in || !phi_out || !rho)
-    return px::unbound_fail(PX_EINVAL, "px_relax_n_static: NULL field pointer");
-  const bool inplace = phi_in == phi_out;
-  if (!inplace && px::ranges_overlap(phi_in, phi_out, span))
-    return px::unbound_fail(PX_EINVAL,
-                            "px_relax_n_static: phi_in and phi_out overlap without being equal");
-  if (px::ranges_overlap(rho, phi_out, span))
-    return px::unbound_fail(PX_EINVAL, "px_relax_n_static: rho overlaps phi_out");
-  if (reports && px::ranges_overlap(resid_dev, phi_out, span))
-    return px::unbound_fail(PX_EINVAL, "px_relax_n_static: resid_dev overlaps phi_out");
+  if (empty) return PX_OK;
 
   if (nsweeps == 0) {
     if (inplace) return PX_OK;
@@ -134,7 +137,8 @@ extern "C" px_status px_relax_n_static(const px_grid* g, const void* phi_in, voi
   for (size_t k = 0; k < L; ++k) {
     void* dst = ((L - 1 - k) % 2 == 0) ? phi_out : scratch;
     cudaError_t e = px::launch_relax(f, src, dst, rho, omega, sizes[k], vec,
-                                     reports ? resid_dev : nullptr, s0, report_every, st);
+                                     reports ? resid_dev : nullptr, s0, report_every,
+                                     nullptr, 0, st);
     if (e != cudaSuccess) return launch_error(e, "relax launch");
     s0 += sizes[k];
     src = dst;

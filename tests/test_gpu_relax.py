@@ -311,6 +311,33 @@ def test_invalid_arguments(px):
                           OMEGA, 1, 0, None, 0, None) == px.PX_EINVAL
 
 
+def test_report_buffer_next_to_field(px):
+    """A report buffer directly below phi_out in one allocation is accepted
+    (the check measures each range by its own length); one that overlaps
+    phi_out is rejected before anything is written. Both entry points."""
+    nx = ny = 64
+    phi, rho = fields(nx, ny, 21)
+    for entry in ("relax_n", "relax_n_static"):
+        fn = getattr(px, entry)
+        buf = torch.zeros(256 + nx * ny * 4, dtype=torch.uint8, device="cuda")
+        resid = buf[0:32].view(torch.float64)              # 4 reports, then a gap
+        out = buf[256:].view(torch.float32).view(ny, nx)   # phi_out right after
+        a, r = dev(phi, torch.float32), dev(rho, torch.float32)
+        fn(a, out, r, 1.0 / nx, OMEGA, 4, 4, resid, 1)
+        torch.cuda.synchronize()
+        ref, R = oracle.relax_n(host(a), host(r), 1.0 / nx, OMEGA, 4, 1)
+        assert np.max(np.abs(host(out) - ref)) <= 4 * 2e-6 * np.max(np.abs(ref))
+        assert np.all(host(resid) > 0)
+        # a report buffer inside phi_out: rejected, phi_out untouched
+        before = out.clone()
+        bad = buf[256 + 64:256 + 96].view(torch.float64)
+        with pytest.raises(px.PxError) as ei:
+            fn(a, out, r, 1.0 / nx, OMEGA, 4, 4, bad, 1)
+        assert ei.value.status == px.PX_EINVAL
+        torch.cuda.synchronize()
+        assert torch.equal(out, before)
+
+
 # ------------------------------------------------------------ full size, sampled
 def _window(a, j0, i0, size):
     ny, nx = a.shape
