@@ -36,8 +36,8 @@ BATCH_SWEEPS = 300  # sweeps per instance of the batched workload
 OMEGA = 2.0 / 3.0
 ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cell per launch
 # DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
-# (empty until the current kernel has been captured: traffic is then null).
-MEASURED_TRAFFIC_PER_CELL = {}
+# (profiles/relaxR2_f32_8192.md: mean dram read + write of two 16384^2 launches / cells).
+MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (2226466688 + 1045071360) / 16384**2}
 
 
 def kernel_name(dt: str, tb: int) -> str:
@@ -45,7 +45,9 @@ def kernel_name(dt: str, tb: int) -> str:
         return "relax1_stream<float,4>" if dt == "f32" else "relax1_stream<double,2>"
     if dt == "f64":
         return f"relaxT_tile<double,{tb}>"
-    return f"relaxR_f32<{tb},4>" if tb in (3, 4) else f"relaxW2_f32<{tb}>"
+    if tb in (3, 4):
+        return f"relaxR2_f32<{tb}>"
+    return f"relaxW_f32<{tb}>" if tb in (6, 7) else f"relaxW2_f32<{tb}>"
 
 
 def peaks():
@@ -457,8 +459,8 @@ def run_gpu(args, world, rank, local):
                              if ("f32", auto_tb) in MEASURED_TRAFFIC_PER_CELL else None)),
                 "note": f"algorithmic bytes 12 B/cell per launch of {auto_tb} sweeps over "
                         f"{cells} cells / mean launch time (step time / {lps} launches); "
-                        f"peak {peak_kind}; traffic = ncu DRAM bytes per cell of a 6144^2 "
-                        f"launch scaled by the cell count",
+                        f"peak {peak_kind}; traffic = ncu DRAM bytes per cell of a 16384^2 "
+                        f"launch times the cell count",
             },
             "variants": variants,
             "fp64_note": "FP64 sweep is bound by the FP64 pipe (0.555 T DFMA/s measured), "
