@@ -253,32 +253,38 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     if (fits_whole(f.nx, f.ny, f.dtype)) smem = std::max(smem, px::whole_bytes(f.nx, f.ny, f.dtype));
   }
   smem = (smem + 1023) / 1024 * 1024;
-  // cluster size: the one whose resident clusters cover the most SMs (ties: larger)
-  int C = 0, ncl = 0;
+  // Candidate cluster sizes: every size of which one cluster fits. Each is
+  // tuned (or read from the cache) and scheduled; the plan keeps the one with
+  // the smallest predicted makespan. The largest BANDED instances matter most
+  // here: one of them runs on a single cluster, so small clusters can leave it
+  // as the critical path even when they cover more SMs.
+  std::vector<std::pair<int, int>> cands;  // (cluster size, resident clusters)
   for (int cs = px::batch_max_cluster_size(); cs >= 2; cs /= 2) {
     int m = 0;
     cudaError_t e = px::batch_max_clusters(&m, smem, cs);
     if (e != cudaSuccess) { cudaGetLastError(); continue; }
-    if (m * cs > ncl * C) { C = cs; ncl = m; }
+    if (m >= 1) cands.push_back({cs, m});
   }
-  if (ncl < 1) {
+  if (cands.empty()) {
     destroy_batch(b);
     return px::ctx_fail(c, PX_ECUDA, "no cluster of the batch kernel fits on this device");
   }
 
-  // classes and their configuration
+  // classes and their configuration, per candidate cluster size
   std::map<std::string, ClassCfg> cfg;
   std::map<std::string, int> count;
-  for (int i = 0; i < n; ++i) {
-    const px_grid& g = grids[i];
-    const std::string k = class_key(g.dtype, g.nx, g.ny, C);
-    count[k]++;
-    if (!cfg.count(k)) {
-      ClassCfg d;
-      d.mode = fits_whole(g.nx, g.ny, g.dtype) ? px::MODE_WHOLE : px::MODE_BANDED;
-      d.ry = 8;
-      d.rate_per_sm = default_rate(g.dtype, d.mode);
-      cfg[k] = d;
+  for (auto& cand : cands) {
+    for (int i = 0; i < n; ++i) {
+      const px_grid& g = grids[i];
+      const std::string k = class_key(g.dtype, g.nx, g.ny, cand.first);
+      count[k]++;
+      if (!cfg.count(k)) {
+        ClassCfg d;
+        d.mode = fits_whole(g.nx, g.ny, g.dtype) ? px::MODE_WHOLE : px::MODE_BANDED;
+        d.ry = 8;
+        d.rate_per_sm = default_rate(g.dtype, d.mode);
+        cfg[k] = d;
+      }
     }
   }
   const std::string gpu = gpu_name(c->device);
@@ -293,10 +299,10 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     }
     if (tune) {
       int dt = kv.first[1] == '6' ? PX_F64 : PX_F32;
-      int nx = 0, ny = 0;
-      sscanf(kv.first.c_str() + 4, "%dx%d", &nx, &ny);
+      int nx = 0, ny = 0, cs = 0;
+      sscanf(kv.first.c_str() + 4, "%dx%d@c%d", &nx, &ny, &cs);
       ClassCfg t;
-      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, C, &t);
+      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, cs, &t);
       if (s != PX_OK) { destroy_batch(b); return s; }
       kv.second = t;
       cached[kv.first] = t;
@@ -305,26 +311,70 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   }
   if (tuned_now) save_cache(tune_cache, gpu, cached);
 
-  // WHOLE classes decide the shared memory actually used (less is fine)
-  size_t used = 0;
-  for (int i = 0; i < n; ++i) {
-    const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
-    if (k.mode == px::MODE_WHOLE) used = std::max(used, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
-  }
-  smem = (used + 1023) / 1024 * 1024;
-  {
+  // schedule every candidate: longest first to the least loaded (seconds)
+  struct Sched {
+    int C = 0, ncl = 0;
+    size_t smem = 0;
+    double makespan = 0, total = 0;
+    std::vector<std::vector<int>> cl_items, cta_items;
+  };
+  auto schedule = [&](int C, int ncl_full) {
+    Sched S;
+    S.C = C;
+    // WHOLE classes decide the shared memory actually used (less is fine)
+    size_t used = 0;
+    for (int i = 0; i < n; ++i) {
+      const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
+      if (k.mode == px::MODE_WHOLE)
+        used = std::max(used, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
+    }
+    S.smem = (used + 1023) / 1024 * 1024;
+    S.ncl = ncl_full;
     int m = 0;
-    cudaError_t e = px::batch_max_clusters(&m, smem, C);
-    if (e == cudaSuccess && m > ncl) ncl = m;
+    if (px::batch_max_clusters(&m, S.smem, C) == cudaSuccess && m > S.ncl) S.ncl = m;
     cudaGetLastError();
-  }
+    std::vector<double> cl_load(S.ncl, 0.0), cta_load((size_t)S.ncl * C, 0.0);
+    S.cl_items.assign(S.ncl, {});
+    S.cta_items.assign((size_t)S.ncl * C, {});
+    std::vector<std::pair<double, int>> banded, whole;
+    for (int i = 0; i < n; ++i) {
+      const px_grid& g = grids[i];
+      const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny, C)];
+      const double work = (double)g.nx * g.ny * nsweeps / std::max(k.rate_per_sm, 1.0);
+      if (k.mode == px::MODE_BANDED) banded.push_back({work / C, i});
+      else whole.push_back({work, i});
+    }
+    std::sort(banded.begin(), banded.end(), [](auto& x, auto& y) { return x.first > y.first; });
+    std::sort(whole.begin(), whole.end(), [](auto& x, auto& y) { return x.first > y.first; });
+    for (auto& w : banded) {
+      const int k = (int)(std::min_element(cl_load.begin(), cl_load.end()) - cl_load.begin());
+      cl_load[k] += w.first;
+      S.cl_items[k].push_back(w.second);
+    }
+    for (int k = 0; k < S.ncl; ++k)
+      for (int r = 0; r < C; ++r) cta_load[(size_t)k * C + r] = cl_load[k];
+    for (auto& w : whole) {
+      const int k = (int)(std::min_element(cta_load.begin(), cta_load.end()) - cta_load.begin());
+      cta_load[k] += w.first;
+      S.cta_items[k].push_back(w.second);
+    }
+    S.makespan = *std::max_element(cta_load.begin(), cta_load.end());
+    for (double v : cta_load) S.total += v;
+    return S;
+  };
+  std::vector<Sched> scheds;
+  for (auto& cand : cands) scheds.push_back(schedule(cand.first, cand.second));
+  size_t pick = 0;
+  for (size_t k = 1; k < scheds.size(); ++k)
+    if (scheds[k].makespan < scheds[pick].makespan * (1 - 1e-9)) pick = k;
+  Sched& S = scheds[pick];
+  const int C = S.C, ncl = S.ncl;
+  smem = S.smem;
   b->nclusters = ncl;
   b->smem = smem;
+  std::vector<std::vector<int>>& cl_items = S.cl_items;
+  std::vector<std::vector<int>>& cta_items = S.cta_items;
 
-  // schedule: longest first to the least loaded (times in seconds)
-  std::vector<double> cl_load(ncl, 0.0), cta_load(ncl * C, 0.0);
-  std::vector<std::vector<int>> cl_items(ncl), cta_items(ncl * C);
-  std::vector<std::pair<double, int>> banded, whole;
   size_t scratch_bytes = 0;
   std::vector<size_t> scr_off(n, 0);
   b->inst.resize(n);
@@ -336,28 +386,10 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     I.nx = g.nx; I.ny = g.ny; I.ld = g.ld; I.dtype = g.dtype; I.mode = k.mode; I.ry = k.ry;
     I.c = omega * g.h * g.h / 4.0;
     I.ih2 = 1.0 / (g.h * g.h);
-    const double work = (double)g.nx * g.ny * nsweeps / std::max(k.rate_per_sm, 1.0);
     if (k.mode == px::MODE_BANDED) {
-      banded.push_back({work / C, i});
       scr_off[i] = scratch_bytes;
       scratch_bytes += ((size_t)g.ld * g.ny * (g.dtype == PX_F64 ? 8 : 4) + 255) / 256 * 256;
-    } else {
-      whole.push_back({work, i});
     }
-  }
-  std::sort(banded.begin(), banded.end(), [](auto& a, auto& b2) { return a.first > b2.first; });
-  std::sort(whole.begin(), whole.end(), [](auto& a, auto& b2) { return a.first > b2.first; });
-  for (auto& w : banded) {
-    const int k = (int)(std::min_element(cl_load.begin(), cl_load.end()) - cl_load.begin());
-    cl_load[k] += w.first;
-    cl_items[k].push_back(w.second);
-  }
-  for (int k = 0; k < ncl; ++k)
-    for (int r = 0; r < C; ++r) cta_load[k * C + r] = cl_load[k];
-  for (auto& w : whole) {
-    const int k = (int)(std::min_element(cta_load.begin(), cta_load.end()) - cta_load.begin());
-    cta_load[k] += w.first;
-    cta_items[k].push_back(w.second);
   }
   std::vector<int> ix;
   ix.push_back(0);
@@ -410,15 +442,21 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
 
   // description
   std::ostringstream os;
-  const double makespan = *std::max_element(cta_load.begin(), cta_load.end());
-  double total = 0;
-  for (double v : cta_load) total += v;
+  const double makespan = S.makespan, total = S.total;
   os << "{\"clusters\": " << ncl << ", \"cluster_size\": " << C << ", \"smem\": " << smem
      << ", \"predicted_ms\": " << makespan * 1e3
      << ", \"balance\": " << (makespan > 0 ? total / (makespan * ncl * C) : 1.0)
-     << ", \"classes\": {";
+     << ", \"candidates\": [";
+  for (size_t k = 0; k < scheds.size(); ++k)
+    os << (k ? ", " : "") << "{\"cluster_size\": " << scheds[k].C << ", \"clusters\": "
+       << scheds[k].ncl << ", \"predicted_ms\": " << scheds[k].makespan * 1e3 << "}";
+  os << "], \"classes\": {";
+  const std::string suffix = "@c" + std::to_string(C);
   bool first = true;
   for (auto& kv : cfg) {
+    if (kv.first.size() < suffix.size() ||
+        kv.first.compare(kv.first.size() - suffix.size(), suffix.size(), suffix) != 0)
+      continue;
     os << (first ? "" : ", ") << "\"" << kv.first << "\": {\"count\": " << count[kv.first]
        << ", \"mode\": \"" << (kv.second.mode == px::MODE_WHOLE ? "whole" : "banded")
        << "\", \"ry\": " << kv.second.ry << ", \"rate_per_sm\": " << kv.second.rate_per_sm

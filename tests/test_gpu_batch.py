@@ -94,7 +94,7 @@ def test_autotune_cache_roundtrip(px, tmp_path):
     assert all(v["rate_per_sm"] > 0 for v in d["classes"].values())
     data = json.load(open(cache))
     assert data["gpu"] == torch.cuda.get_device_name(0)
-    assert set(data["classes"]) == set(d["classes"])
+    assert set(d["classes"]) <= set(data["classes"])  # every candidate cluster size is cached
     # second plan reads the cache (no measurement) and runs correctly
     b2 = px.Batch(grids, 10, OMEGA, 1, tune_cache=cache, tune=False)
     d2 = b2.describe()
@@ -170,4 +170,28 @@ def test_plan_reports_allocation_failure(px):
     assert ei.value.status == px.PX_ENOMEM
     # the context stays usable
     b = px.Batch([px.Grid(64, 64, 64, 0, px.PX_F32, 1 / 64)], 2)
+    b.close()
+
+
+def test_plan_picks_cluster_size_by_makespan(px):
+    """One large FP64 instance among small ones: on 2-CTA clusters it alone would
+    set the makespan, so the plan takes the candidate cluster size with the
+    smallest predicted makespan (a larger one), and still matches the oracle."""
+    specs = [(512, 512, "f64")] + [(32, 32, "f32")] * 40 + [(64, 64, "f64")] * 8
+    b = px.Batch([px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+                  for nx, ny, dt in specs], 6, OMEGA, 3)
+    d = b.describe()
+    cands = d["candidates"]
+    assert len(cands) >= 1
+    best = min(c["predicted_ms"] for c in cands)
+    assert abs(d["predicted_ms"] - best) <= 1e-9 * max(1.0, best)
+    chosen = [c for c in cands if c["cluster_size"] == d["cluster_size"]][0]
+    assert chosen["predicted_ms"] == best
+    if any(c["cluster_size"] > 2 for c in cands):
+        assert d["cluster_size"] > 2, cands
+    phis, rhos, host = make_instances(specs, 77)
+    resid = torch.full((len(specs) * 2,), -1.0, dtype=torch.float64, device="cuda")
+    b.run(phis, rhos, resid)
+    torch.cuda.synchronize()
+    check(specs, phis, host, resid, 6, 3)
     b.close()
