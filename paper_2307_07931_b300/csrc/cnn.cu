@@ -37,10 +37,8 @@ constexpr int C = 32;            // channels of the hidden layers
 constexpr int K9 = 9 * C;        // GEMM K of a 32 -> 32 layer
 constexpr int TR = 4, TW = 64;   // output tile: rows x columns (one row per warp)
 static_assert(TW == 64, "load_tap_tile splits pixel indices with shifts");
-constexpr int WROWB = 592;       // bytes per weight row in shared memory (37 chunks)
 constexpr int kConvThreads = 128;
 constexpr size_t kTileBytes = (size_t)TR * TW * 64;             // one [TR*TW px][32 ch] tile
-constexpr size_t kConvSmem = 2 * kTileBytes + (size_t)C * WROWB;  // tap double buffer + weights
 constexpr size_t kWgradSmem = 3 * kTileBytes;                     // dz tile + tap double buffer
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -104,115 +102,243 @@ __device__ __forceinline__ void load_tap_tile(unsigned char* dst, const __nv_bfl
   }
 }
 
+__device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p) {
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    uint4 u = q[k];
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 t = __bfloat1622float2(h[e]);
+      f[k * 8 + 2 * e] = t.x;
+      f[k * 8 + 2 * e + 1] = t.y;
+    }
+  }
+}
+
+// Index of element (n, k) of an N = 32 x K = 288 K-major operand in the
+// tensor cores' no-swizzle core-matrix order: [k / 8][n][k % 8].
+__host__ __device__ __forceinline__ int cm_index(int n, int k) { return (k / 8) * (C * 8) + n * 8 + (k % 8); }
+
 __device__ __forceinline__ int tap_dy(int tap, int d) { return (tap / 3 - 1) * d; }
 __device__ __forceinline__ int tap_dx(int tap, int d) { return (tap % 3 - 1) * d; }
 
-// 32 -> 32 periodic convolution (dilation d) on the tensor cores.
-// kMode 0: forward, out = bias + conv, stores z (if zout) and gelu(z) into aout.
-// kMode 1: input gradient, aout = conv * gelu'(zprev) (weights pre-flipped/transposed).
-// The shifted input tile of tap t + 1 streams into shared memory while tap t computes.
+// ---------------------------------------------------------------------------
+// 32 -> 32 periodic convolution (dilation d) on the 5th-generation tensor
+// cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in tensor
+// memory). The 4 x 64 output tile is two M = 128 pixel halves, each with a
+// 128-lane x 32-column FP32 accumulator in TMEM (64 columns per CTA). Per tap
+// the shifted input tile [256 px][32 ch] is staged by cp.async into shared
+// memory in the no-swizzle K-major core-matrix layout (8 pixels x 16 bytes per
+// core matrix; chunk c of 8 channels at c * 4096 B, pixel p at p * 16 B), and
+// one thread issues 4 MMAs (2 halves x 2 x K = 16) and commits them to the
+// tap buffer's mbarrier. Three tap buffers rotate, filled two taps ahead: the
+// buffer of tap t + 2 last fed tap t - 1, so before the CTA barrier of tap t
+// the issuing thread (alone) checks that the MMAs of tap t - 1 are done, and
+// the other threads never spin. Weights come pre-packed in the same layout
+// ([k / 8][n][k % 8], 18 KB). The epilogue reads each pixel's 32 channels from
+// TMEM (tcgen05.ld 32x32b.x32: warp w owns lanes 32w..32w+31) and applies
+// bias + GELU (forward) or the product with GELU'(z) (input gradient).
+// Every wait is bounded; on timeout the CTA raises *fault, waits once more
+// (bounded) for its MMAs, frees its tensor memory and returns.
+constexpr int kUmmaM = 128;                               // pixels per MMA = TMEM lanes
+constexpr uint32_t kTmemCols = 64;                        // two 128 x 32 FP32 accumulators
+constexpr uint32_t kCmChunk = TR * TW * 16;               // 4096 B: next 8-channel chunk of a tile
+constexpr size_t kCmTile = (size_t)4 * kCmChunk;          // 16 KB: one tap tile
+constexpr uint32_t kCmWChunk = C * 16;                    // 512 B: next 8-k chunk of the weights
+constexpr size_t kWBytes = (size_t)(K9 / 8) * kCmWChunk;  // 18 KB
+constexpr int kTapBufs = 3;                              // tap tiles in flight or in use
+constexpr size_t kUmmaSmem = kTapBufs * kCmTile + kWBytes + 64;  // tap ring, weights, barriers
+constexpr uint32_t kSpinLimit = 1u << 26;
+__device__ unsigned g_conv_fault;  // set by a conv CTA whose bounded wait ran out
+// instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 32, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
+                            ((uint32_t)(kUmmaM >> 4) << 24);
+static_assert(TR * TW == 2 * kUmmaM, "two M = 128 halves per tile");
+
+// shared-memory matrix descriptor, no swizzle (start, leading = K-direction
+// and stride = M/N-direction byte offsets between core matrices)
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+               ::"r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kSpinLimit && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+               "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                 "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                 "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                 "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                 "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                 "=r"(v[30]), "=r"(v[31])
+               : "r"(taddr) : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Stage one tap's input tile in the core-matrix layout (same thread mapping as
+// load_tap_tile: a warp copies 8 whole pixels, 512 contiguous global bytes,
+// into four 128-byte shared rows).
+__device__ __forceinline__ void load_tap_cm(unsigned char* dst, const __nv_bfloat16* act, int b,
+                                            int y0, int x0, int oy, int ox, int H, int W) {
+  const bool near = oy > -H && oy < H && ox > -W && ox < W;
+  for (int q = threadIdx.x; q < TR * TW * 4; q += blockDim.x) {
+    const int chunk = q & 3, pix = q >> 2;
+    const int r = pix >> 6, c = pix & (TW - 1);
+    const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
+    const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
+    cp16(dst + chunk * kCmChunk + pix * 16, act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
+  }
+}
+
 template <int kMode>
 __global__ void __launch_bounds__(kConvThreads)
-conv32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
-           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
-           __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
-           int tiles_x, int tiles_y, int dil) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* tiles = sm;                  // 2 x kTileBytes
-  unsigned char* wsm = sm + 2 * kTileBytes;
+conv32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
+            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
+            __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
+            int tiles_x, int tiles_y, int dil, unsigned* __restrict__ fault) {
+  extern __shared__ __align__(128) unsigned char usm[];
+  unsigned char* tiles = usm;                                 // kTapBufs x kCmTile
+  unsigned char* wsm = usm + kTapBufs * kCmTile;              // kWBytes
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + kWBytes);  // one mbarrier per tap buffer
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kTapBufs);
+  // The kernel declares no static shared variables: the core matrices must
+  // start on 128-byte boundaries, and a static variable would move the
+  // dynamic block off that alignment (MMAs would then read shifted operands).
+  volatile int& s_ok = *reinterpret_cast<int*>(tslot + 1);  // 0 once a wait ran out
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = blockIdx.x;
   const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
   const int x0 = tx * TW, y0 = ty * TR;
 
-  // weights [n][k] (k contiguous, 36 chunks per row, rows padded to 37 chunks)
-  for (int q = threadIdx.x; q < C * (K9 / 8); q += blockDim.x) {
-    const int n = q / (K9 / 8), kc = q - n * (K9 / 8);
-    cp16(wsm + n * WROWB + kc * 16, wk + (size_t)n * K9 + kc * 8);
-  }
-  load_tap_tile(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
+  for (int q = threadIdx.x; q < (int)(kWBytes / 16); q += blockDim.x) cp16(wsm + q * 16, wk + q * 8);
+  load_tap_cm(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
   cp_commit();
-
-  float acc[4][4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
+  load_tap_cm(tiles + kCmTile, in, b, y0, x0, tap_dy(1, dil), tap_dx(1, dil), H, W);
+  cp_commit();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < kTapBufs; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_ok = (smem_u32(usm) & 127u) == 0;  // misaligned operands: no MMA, raise the fault
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
   const uint32_t tbase = smem_u32(tiles), wbase = smem_u32(wsm);
-  // ldmatrix lane roles. A (x4): matrices (px 0-7, ch c), (px 8-15, ch c), (px 0-7, ch c+8),
-  // (px 8-15, ch c+8). B (x4): (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15).
-  const int a_px = (lane & 7) + ((lane >> 3) & 1) * 8;
-  const int a_ch = (lane >> 4);              // chunk offset 0/1 (x8 channels)
-  const int b_n = (lane & 7) + ((lane >> 4) << 3);
-  const int b_kc = (lane >> 3) & 1;
 
 #pragma unroll 1
   for (int tap = 0; tap < 9; ++tap) {
-    if (tap < 8) {
-      load_tap_tile(tiles + ((tap + 1) & 1) * kTileBytes, in, b, y0, x0, tap_dy(tap + 1, dil),
-                    tap_dx(tap + 1, dil), H, W);
-      cp_commit();
-      cp_wait_group<1>();
-    } else {
-      cp_wait_group<0>();
+    const int buf = tap % kTapBufs;
+    if (tap < 8) cp_wait_group<1>();
+    else cp_wait_group<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor core
+    if (threadIdx.x == 0 && tap >= 1 && tap + 2 <= 8) {
+      // the buffer about to take tap + 2 fed tap - 1: its MMAs must be done
+      const int pt = tap - 1;
+      if (!mbar_wait(smem_u32(bars + pt % kTapBufs), (pt / kTapBufs) & 1)) s_ok = 0;
     }
     __syncthreads();
-    const uint32_t cur = tbase + (tap & 1) * (uint32_t)kTileBytes;
+    const bool ok = s_ok != 0;
+    if (threadIdx.x == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t abase = tbase + buf * (uint32_t)kCmTile;
 #pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {  // 16-channel halves of K within this tap
-      uint32_t bf[2][4];
+      for (int cc = 0; cc < 2; ++cc) {  // K = 16 halves of this tap's 32 channels
+        const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
 #pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        const int n = np * 16 + b_n;
-        const int kchunk = tap * 4 + cc * 2 + b_kc;
-        ldsm4(bf[np], wbase + n * WROWB + kchunk * 16);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        const int pix = warp * TW + mt * 16 + a_px;
-        uint32_t af[4];
-        ldsm4(af, cur + pix_off(pix, cc * 2 + a_ch));
-#pragma unroll
-        for (int np = 0; np < 2; ++np) {
-          mma16816(acc[mt][np * 2 + 0], af, bf[np][0], bf[np][1]);
-          mma16816(acc[mt][np * 2 + 1], af, bf[np][2], bf[np][3]);
+        for (int h = 0; h < 2; ++h) {
+          const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
+          umma_bf16(tmem + h * C, ad, bd, (tap > 0 || cc > 0) ? 1u : 0u);
         }
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(bars + buf)) : "memory");
     }
-    __syncthreads();  // this buffer is refilled two taps later
+    if (tap + 2 <= 8) {
+      if (ok)
+        load_tap_cm(tiles + ((tap + 2) % kTapBufs) * kCmTile, in, b, y0, x0, tap_dy(tap + 2, dil),
+                    tap_dx(tap + 2, dil), H, W);
+      cp_commit();
+    }
   }
+  // the last commit (tap 8) covers every MMA of the tile
+  if (threadIdx.x == 0 && s_ok && !mbar_wait(smem_u32(bars + 8 % kTapBufs), (8 / kTapBufs) & 1))
+    s_ok = 0;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool ok = s_ok != 0;
 
-  // epilogue: thread holds rows g, g+8 (pixels) and columns 2q, 2q+1 (channels)
-  const int g = lane >> 2, q = lane & 3;
-  const int y = y0 + warp;
+  if (ok) {
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      uint32_t v[32];
+      tmem_ld32(v, tmem + h * C + ((uint32_t)(warp * 32) << 16));
+      const int pix = h * kUmmaM + warp * 32 + lane;
+      const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
+      const int64_t pb = (((int64_t)b * H + y) * W + x) * C;
+      __nv_bfloat162 zz[C / 2], aa[C / 2];
+      if (kMode == 0) {
 #pragma unroll
-  for (int mt = 0; mt < 4; ++mt) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int x = x0 + mt * 16 + g + half * 8;
-      const int64_t pbase_g = (((int64_t)b * H + y) * W + x) * C;
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int co = nt * 8 + 2 * q;
-        float v0 = acc[mt][nt][half * 2 + 0], v1 = acc[mt][nt][half * 2 + 1];
-        if (kMode == 0) {
-          v0 += bias[co];
-          v1 += bias[co + 1];
-          if (zout)
-            *reinterpret_cast<__nv_bfloat162*>(zout + pbase_g + co) = __floats2bfloat162_rn(v0, v1);
-          *reinterpret_cast<__nv_bfloat162*>(aout + pbase_g + co) =
-              __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
-        } else {
-          const __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162*>(zprev + pbase_g + co);
-          const float2 zf = __bfloat1622float2(zp);
-          *reinterpret_cast<__nv_bfloat162*>(aout + pbase_g + co) =
-              __floats2bfloat162_rn(v0 * gelu_grad_f(zf.x), v1 * gelu_grad_f(zf.y));
+        for (int o = 0; o < C; o += 2) {
+          const float v0 = __uint_as_float(v[o]) + __ldg(bias + o);
+          const float v1 = __uint_as_float(v[o + 1]) + __ldg(bias + o + 1);
+          zz[o / 2] = __floats2bfloat162_rn(v0, v1);
+          aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
         }
+        if (zout) {
+          uint4* zo = reinterpret_cast<uint4*>(zout + pb);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
+        }
+      } else {
+        float zf[C];
+        load_px32(zf, zprev + pb);
+#pragma unroll
+        for (int o = 0; o < C; o += 2)
+          aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
+                                            __uint_as_float(v[o + 1]) * gelu_grad_f(zf[o + 1]));
       }
+      uint4* ao = reinterpret_cast<uint4*>(aout + pb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) ao[k] = reinterpret_cast<const uint4*>(aa)[k];
     }
+  } else if (threadIdx.x == 0) {
+    atomicOr(fault, 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) {
+    // after a timeout, MMAs still in flight must end before the free: the last
+    // issued commit went to some buffer; wait (bounded) on all of them
+    if (!ok)
+      for (int k = 0; k < kTapBufs; ++k) {
+        mbar_wait(smem_u32(bars + k), 0);
+        mbar_wait(smem_u32(bars + k), 1);
+      }
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
   }
 }
 
@@ -353,20 +479,6 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
   }
 }
 
-__device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p) {
-  const uint4* q = reinterpret_cast<const uint4*>(p);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    uint4 u = q[k];
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float2 t = __bfloat1622float2(h[e]);
-      f[k * 8 + 2 * e] = t.x;
-      f[k * 8 + 2 * e + 1] = t.y;
-    }
-  }
-}
 
 // Last layer (32 -> 1) forward: y = b6 + sum_{tap,c} W6[c][tap] a[p + tap][c] (FP32 out).
 __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __restrict__ w6,
@@ -452,37 +564,98 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
 }
 
 // Weight gradient of a single-channel side (first and last layers):
-//   mode 0 (first): dW1[o][tap] = sum_p g32[p][o] * s1[p + tap],   db1[o] = sum_p g32[p][o]
-//   mode 1 (last):  dW6[c][tap] = sum_p s1[p] * g32[p + tap][c],   db6    = sum_p s1[p]
-// One CTA of 288 threads per group of pixels; thread (c, tap). Partials per CTA.
+//   mode 0 (first): dW1[o][tap] = sum_p g32[p][o] * s1[p + off(tap)],  db1[o] = sum_p g32[p][o]
+//   mode 1 (last):  dW6[c][tap] = sum_p s1[p] * g32[p + off(tap)][c],  db6    = sum_p s1[p]
+// Mode 1 is computed as sum_q g32[q][c] * s1[q - off(tap)]: both modes are
+// then "32-channel image times a shifted single-channel image", with the
+// shift sign flipped. A CTA of 256 threads owns a range of image rows; thread
+// t takes channels 8 (t & 3) .. +7 and pixel slot t >> 2 (64 slots striding
+// along each row), and keeps 72 independent accumulators. The wrapped
+// neighbour rows are found once per row. The CTA reduces its threads in a
+// fixed order (shuffles within a warp, then warps in index order) and writes
+// one partial per CTA, so the result is deterministic.
+constexpr int kWsThreads = 256;
 template <int kMode>
-__global__ void __launch_bounds__(288)
+__global__ void __launch_bounds__(kWsThreads)
 wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1,
-             float* __restrict__ part, int B, int H, int W, int px_per_cta, int dil) {
-  const int c = threadIdx.x / 9, tap = threadIdx.x % 9;
-  const int dy = tap_dy(tap, dil), dx = tap_dx(tap, dil);
-  const int64_t n = (int64_t)B * H * W;
-  const int64_t p0 = (int64_t)blockIdx.x * px_per_cta;
-  const int64_t p1 = std::min<int64_t>(n, p0 + px_per_cta);
-  float acc = 0.f, accb = 0.f;
-  for (int64_t p = p0; p < p1; ++p) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const int64_t img = p / ((int64_t)H * W);
-    const int64_t ps = (img * H + wrapn(yy + dy, H)) * W + wrapn(xx + dx, W);
-    if (kMode == 0) {
-      const float gv = __bfloat162float(g32[p * C + c]);
-      acc = fmaf(gv, s1[ps], acc);
-      if (tap == 0) accb += gv;
-    } else {
-      const float sv = s1[p];
-      acc = fmaf(sv, __bfloat162float(g32[ps * C + c]), acc);
-      if (threadIdx.x == 0) accb += sv;
+             float* __restrict__ part, int B, int H, int W, int rows_per_cta, int dil) {
+  __shared__ float red[kWsThreads / 32][4][C / 4 * 9 + C / 4];
+  const int cg = threadIdx.x & 3, slot = threadIdx.x >> 2;
+  const int sd = kMode == 0 ? dil : -dil;  // shift of s1 relative to g32
+  const int rows = B * H;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(rows, r0 + rows_per_cta);
+  float acc[8][9], accb[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    accb[k] = 0.f;
+#pragma unroll
+    for (int tp = 0; tp < 9; ++tp) acc[k][tp] = 0.f;
+  }
+  for (int row = r0; row < r1; ++row) {
+    const int img = row / H, y = row - img * H;
+    const int64_t ibase = (int64_t)img * H * W;
+    const float* srow[3];
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty) srow[ty] = s1 + ibase + (int64_t)wrapn(y + (ty - 1) * sd, H) * W;
+    const __nv_bfloat16* grow = g32 + ((int64_t)row * W) * C + cg * 8;
+    for (int x = slot; x < W; x += kWsThreads / 4) {
+      const int xs[3] = {wrapn(x - sd, W), x, wrapn(x + sd, W)};
+      float sv[9];
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) sv[ty * 3 + tx] = __ldg(srow[ty] + xs[tx]);
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(grow + (int64_t)x * C));
+      const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
+      float g[8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 f = __bfloat1622float2(hv[e]);
+        g[2 * e] = f.x;
+        g[2 * e + 1] = f.y;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+#pragma unroll
+        for (int tp = 0; tp < 9; ++tp) acc[k][tp] = fmaf(g[k], sv[tp], acc[k][tp]);
+        if (kMode == 0) accb[k] += g[k];
+      }
+      if (kMode == 1 && cg == 0) accb[0] += sv[4];
     }
   }
+  // lanes l, l ^ 4, l ^ 8, l ^ 16 share a channel group: reduce them
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int tp = 0; tp < 9; ++tp) {
+      float v = acc[k][tp];
+      v += __shfl_xor_sync(0xffffffffu, v, 4);
+      v += __shfl_xor_sync(0xffffffffu, v, 8);
+      v += __shfl_xor_sync(0xffffffffu, v, 16);
+      if (lane < 4) red[warp][cg][k * 9 + tp] = v;
+    }
+    float vb = accb[k];
+    vb += __shfl_xor_sync(0xffffffffu, vb, 4);
+    vb += __shfl_xor_sync(0xffffffffu, vb, 8);
+    vb += __shfl_xor_sync(0xffffffffu, vb, 16);
+    if (lane < 4) red[warp][cg][C / 4 * 9 + k] = vb;
+  }
+  __syncthreads();
   float* out = part + (size_t)blockIdx.x * (C * 9 + C);
-  out[c * 9 + tap] = acc;
-  if (kMode == 0 && tap == 0) out[C * 9 + c] = accb;
-  if (kMode == 1 && threadIdx.x == 0) out[C * 9] = accb;
+  for (int i = threadIdx.x; i < 4 * (C / 4 * 9 + C / 4); i += blockDim.x) {
+    const int g = i / (C / 4 * 9 + C / 4), j = i - g * (C / 4 * 9 + C / 4);
+    float v = 0.f;
+    for (int w = 0; w < kWsThreads / 32; ++w) v += red[w][g][j];
+    if (j < C / 4 * 9) {
+      const int k = j / 9, tp = j - k * 9;
+      out[(g * 8 + k) * 9 + tp] = v;  // channel g*8 + k, tap tp
+    } else if (kMode == 0) {
+      out[C * 9 + g * 8 + (j - C / 4 * 9)] = v;
+    } else if (g == 0 && j == C / 4 * 9) {
+      out[C * 9] = v;  // db6: only channel group 0 summed s1
+    }
+  }
 }
 
 // Sum partials over CTAs in index order (deterministic): dst[i] += sum_k part[k][i] * scale.
@@ -516,8 +689,8 @@ __global__ void pack_weights(const float* __restrict__ Wt, __nv_bfloat16* __rest
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C * C * 9; i += gridDim.x * blockDim.x) {
     const int o = i / (C * 9), c = (i / 9) % C, tap = i % 9;
     const __nv_bfloat16 w = __float2bfloat16_rn(Wt[i]);
-    fwd[o * K9 + tap * C + c] = w;
-    bwd[c * K9 + (8 - tap) * C + o] = w;
+    fwd[cm_index(o, tap * C + c)] = w;
+    bwd[cm_index(c, (8 - tap) * C + o)] = w;
   }
 }
 
@@ -716,11 +889,38 @@ px_status check_shape(px_cnn* n, int B, int H, int W) {
   return PX_OK;
 }
 
+// Device address of the conv fault word (looked up once, then cached).
+unsigned* conv_fault_ptr() {
+  static unsigned* p = nullptr;
+  if (!p) {
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&q, g_conv_fault) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    p = static_cast<unsigned*>(q);
+  }
+  return p;
+}
+
+// PX_ETIMEOUT (and the word cleared) if a conv CTA gave up on a bounded wait
+// since the last check; synchronises the stream.
+px_status check_conv_fault(px_cnn* n, cudaStream_t st) {
+  unsigned* p = conv_fault_ptr();
+  if (!p) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, p, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cnn_cuda(n, e, "conv fault readback");
+  if (h) {
+    cudaMemsetAsync(p, 0, sizeof h, st);
+    return px::ctx_fail(n->ctx, PX_ETIMEOUT, "a tensor-core conv CTA timed out waiting for its MMAs");
+  }
+  return PX_OK;
+}
+
 px_status set_conv_attrs() {
   static bool done = false;
   if (done) return PX_OK;
-  cudaError_t e = cudaFuncSetAttribute(conv32_mma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_mma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+  cudaError_t e = cudaFuncSetAttribute(conv32_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
@@ -736,10 +936,12 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
   conv_first<<<grid_1d(px, 256), 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
                                                train ? n->z[0] : nullptr, n->a[0], B, H, W,
                                                n->dil[0]);
+  unsigned* fault = conv_fault_ptr();
+  if (!fault) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
   for (int l = 1; l <= 4; ++l)
-    conv32_mma<0><<<tiles, kConvThreads, kConvSmem, st>>>(
+    conv32_umma<0><<<tiles, kConvThreads, kUmmaSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y, n->dil[l]);
+        n->a[l], H, W, tiles_x, tiles_y, n->dil[l], fault);
   conv_last<<<grid_1d(px, 256), 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
@@ -758,11 +960,14 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   mse_grad<<<lblocks, 256, 0, st>>>(n->y, t, n->dy, n->lpart, px);
   *nloss = lblocks;
   // last layer
-  const int spc = 4096;  // pixels per CTA of the single-channel weight gradients
-  const int nsc = (int)((px + spc - 1) / spc);
-  const int nsc_cap = (int)std::min<int64_t>(nsc, n->part_floats / (C * 9 + C));
-  const int spc_eff = (int)((px + nsc_cap - 1) / nsc_cap);
-  wgrad_single<1><<<nsc_cap, 288, 0, st>>>(n->a[4], n->dy, n->part, B, H, W, spc_eff, n->dil[5]);
+  // single-channel weight gradients: whole image rows per CTA, about four CTAs per SM
+  const int rows = B * H;
+  const int64_t want = std::min<int64_t>((int64_t)px::device_sm_count() * 4,
+                                         (int64_t)(n->part_floats / (C * 9 + C)));
+  const int rpc = (int)((rows + want - 1) / want);
+  const int nsc_cap = (rows + rpc - 1) / rpc;
+  wgrad_single<1><<<nsc_cap, kWsThreads, 0, st>>>(n->a[4], n->dy,
+                                                  n->part, B, H, W, rpc, n->dil[5]);
   reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
   back_last<<<grid_1d(px, 256), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W,
                                               n->dil[5]);
@@ -774,18 +979,20 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
         n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles, n->dil[l]);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
-    conv32_mma<1><<<tiles, kConvThreads, kConvSmem, st>>>(gcur, n->wb[l], nullptr, n->z[l - 1],
-                                                          nullptr, gnext, H, W, tiles_x, tiles_y,
-                                                          n->dil[l]);
+    conv32_umma<1><<<tiles, kConvThreads, kUmmaSmem, st>>>(gcur, n->wb[l], nullptr, n->z[l - 1],
+                                                           nullptr, gnext, H, W, tiles_x, tiles_y,
+                                                           n->dil[l], conv_fault_ptr());
     std::swap(gcur, gnext);
   }
-  wgrad_single<0><<<nsc_cap, 288, 0, st>>>(gcur, x, n->part, B, H, W, spc_eff, n->dil[0]);
+  wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
   reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network backward");
 }
 
 px_status read_loss(px_cnn* n, int nloss, int64_t px, double* loss, cudaStream_t st) {
+  const px_status fs = check_conv_fault(n, st);
+  if (fs != PX_OK) return fs;
   std::vector<double> h(nloss);
   cudaError_t e = cudaMemcpyAsync(h.data(), n->lpart, nloss * sizeof(double),
                                   cudaMemcpyDeviceToHost, st);
