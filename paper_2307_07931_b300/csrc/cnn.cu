@@ -127,29 +127,19 @@ __device__ __forceinline__ int tap_dx(int tap, int d) { return (tap % 3 - 1) * d
 // ---------------------------------------------------------------------------
 // 32 -> 32 periodic convolution (dilation d) on the 5th-generation tensor
 // cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in tensor
-// memory). The 4 x 64 output tile is two M = 128 pixel halves, each with a
-// 128-lane x 32-column FP32 accumulator in TMEM (64 columns per CTA). Per tap
-// the shifted input tile [256 px][32 ch] is staged by cp.async into shared
-// memory in the no-swizzle K-major core-matrix layout (8 pixels x 16 bytes per
-// core matrix; chunk c of 8 channels at c * 4096 B, pixel p at p * 16 B), and
-// one thread issues 4 MMAs (2 halves x 2 x K = 16) and commits them to the
-// tap buffer's mbarrier. Three tap buffers rotate, filled two taps ahead: the
-// buffer of tap t + 2 last fed tap t - 1, so before the CTA barrier of tap t
-// the issuing thread (alone) checks that the MMAs of tap t - 1 are done, and
-// the other threads never spin. Weights come pre-packed in the same layout
-// ([k / 8][n][k % 8], 18 KB). The epilogue reads each pixel's 32 channels from
-// TMEM (tcgen05.ld 32x32b.x32: warp w owns lanes 32w..32w+31) and applies
-// bias + GELU (forward) or the product with GELU'(z) (input gradient).
-// Every wait is bounded; on timeout the CTA raises *fault, waits once more
-// (bounded) for its MMAs, frees its tensor memory and returns.
+// memory). A 4 x 64 output tile is two M = 128 pixel halves, each with a
+// 128-lane x 32-column FP32 accumulator in TMEM. Operands live in shared
+// memory in the no-swizzle K-major core-matrix layout (a core matrix is 8 rows
+// x 16 bytes, contiguous): a tap's shifted input tile [256 px][32 ch] has
+// chunk c of 8 channels at c * 4096 B and pixel p at p * 16 B; the weights
+// [32 n][288 k] are pre-packed as [k / 8][n][k % 8] (18 KB). Per tap and
+// K = 16 half the MMA reads A at (tile + 2 cc * 4096 + half * 2048, LBO 4096,
+// SBO 128) and B at (weights + (4 tap + 2 cc) * 512, LBO 512, SBO 128).
 constexpr int kUmmaM = 128;                               // pixels per MMA = TMEM lanes
-constexpr uint32_t kTmemCols = 64;                        // two 128 x 32 FP32 accumulators
 constexpr uint32_t kCmChunk = TR * TW * 16;               // 4096 B: next 8-channel chunk of a tile
 constexpr size_t kCmTile = (size_t)4 * kCmChunk;          // 16 KB: one tap tile
 constexpr uint32_t kCmWChunk = C * 16;                    // 512 B: next 8-k chunk of the weights
 constexpr size_t kWBytes = (size_t)(K9 / 8) * kCmWChunk;  // 18 KB
-constexpr int kTapBufs = 3;                              // tap tiles in flight or in use
-constexpr size_t kUmmaSmem = kTapBufs * kCmTile + kWBytes + 64;  // tap ring, weights, barriers
 constexpr uint32_t kSpinLimit = 1u << 26;
 __device__ unsigned g_conv_fault;  // set by a conv CTA whose bounded wait ran out
 // instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 32, M = 128
@@ -168,13 +158,6 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t b
                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
                ::"r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it)
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-  return done != 0;
-}
 __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
                "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -189,13 +172,63 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Stage one tap's input tile in the core-matrix layout (same thread mapping as
-// load_tap_tile: a warp copies 8 whole pixels, 512 contiguous global bytes,
-// into four 128-byte shared rows).
-__device__ __forceinline__ void load_tap_cm(unsigned char* dst, const __nv_bfloat16* act, int b,
-                                            int y0, int x0, int oy, int ox, int H, int W) {
+// ---------------------------------------------------------------------------
+// Warp-specialised persistent form of the same convolution (the one launched).
+// A CTA of 9 warps loops over 4 x 64 tiles:
+//   warps 4..7  producers: stage each tap's tile (cp.async, core-matrix
+//               layout) into a 4-stage ring; a thread waits for its own
+//               copies one step later, fences them to the async proxy and
+//               arrives on the stage's `full` barrier (128 arrivals);
+//   warp 8      lane 0 issues the 4 MMAs of a tap once `full` flips and
+//               commits them to the stage's `empty` barrier; after the 9th
+//               tap it commits the tile to `tfull` of its accumulator set;
+//               the warp also owns the tensor memory (2 sets x 64 columns);
+//   warps 0..3  epilogue: wait `tfull`, read their 32 TMEM lanes per half,
+//               apply bias + GELU or the GELU' product, store, and release the
+//               set on `tempty` (128 arrivals).
+// The epilogue of tile i overlaps the staging and MMAs of tile i + 1.
+// Barrier uses are counted per object and waited on with the use's parity;
+// every waiter of use u waits before use u + 1 can complete, so a parity
+// never refers to a stale phase. Every wait is bounded and gives up when the
+// shared abort flag is set; on an abort the CTA raises *fault, lets its MMAs
+// drain (bounded) and frees its tensor memory.
+constexpr int kWsStages = 4;
+// A producer declares step g complete kWsAhead steps later (kWsAhead <
+// kWsStages, or it would wait on its own undeclared step). One step measured
+// fastest: with more copies in flight the tap tiles contend in L2 (whole
+// forward at 16 x 256^2: 0.93 ms at one step ahead, 1.03 ms at three).
+constexpr int kWsAhead = 1;
+constexpr int kWsEpiWarps = 4, kWsProdWarps = 4;
+constexpr int kWsConvThreads = (kWsEpiWarps + kWsProdWarps + 1) * 32;  // 288
+constexpr uint32_t kWsTmemCols = 128;                                 // 2 sets x (2 x 32)
+constexpr int kWsBars = 2 * kWsStages + 4 + 1;  // full, empty, tfull[2], tempty[2], weights
+constexpr size_t kWsSmem = kWsStages * kCmTile + kWBytes + kWsBars * 8 + 16;
+
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+    if ((it & 63) == 63 && *abort_) return false;
+  }
+  *abort_ = 1;
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(bar) : "memory");
+}
+
+// load_tap_cm for a subset of the CTA: thread pid of np
+__device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfloat16* act, int b,
+                                              int y0, int x0, int oy, int ox, int H, int W,
+                                              int pid, int np) {
   const bool near = oy > -H && oy < H && ox > -W && ox < W;
-  for (int q = threadIdx.x; q < TR * TW * 4; q += blockDim.x) {
+  for (int q = pid; q < TR * TW * 4; q += np) {
     const int chunk = q & 3, pix = q >> 2;
     const int r = pix >> 6, c = pix & (TW - 1);
     const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
@@ -205,139 +238,186 @@ __device__ __forceinline__ void load_tap_cm(unsigned char* dst, const __nv_bfloa
 }
 
 template <int kMode>
-__global__ void __launch_bounds__(kConvThreads)
-conv32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
-            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
-            __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
-            int tiles_x, int tiles_y, int dil, unsigned* __restrict__ fault) {
-  extern __shared__ __align__(128) unsigned char usm[];
-  unsigned char* tiles = usm;                                 // kTapBufs x kCmTile
-  unsigned char* wsm = usm + kTapBufs * kCmTile;              // kWBytes
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + kWBytes);  // one mbarrier per tap buffer
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kTapBufs);
-  // The kernel declares no static shared variables: the core matrices must
-  // start on 128-byte boundaries, and a static variable would move the
-  // dynamic block off that alignment (MMAs would then read shifted operands).
-  volatile int& s_ok = *reinterpret_cast<int*>(tslot + 1);  // 0 once a wait ran out
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int t = blockIdx.x;
-  const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
-  const int x0 = tx * TW, y0 = ty * TR;
-
-  for (int q = threadIdx.x; q < (int)(kWBytes / 16); q += blockDim.x) cp16(wsm + q * 16, wk + q * 8);
-  load_tap_cm(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
-  cp_commit();
-  load_tap_cm(tiles + kCmTile, in, b, y0, x0, tap_dy(1, dil), tap_dx(1, dil), H, W);
-  cp_commit();
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+__device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int pix, int b, int y0,
+                                                   int x0, int H, int W,
+                                                   const float* __restrict__ bias,
+                                                   const __nv_bfloat16* __restrict__ zprev,
+                                                   __nv_bfloat16* __restrict__ zout,
+                                                   __nv_bfloat16* __restrict__ aout) {
+  const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
+  const int64_t pb = (((int64_t)b * H + y) * W + x) * C;
+  __nv_bfloat162 zz[C / 2], aa[C / 2];
+  if (kMode == 0) {
+#pragma unroll
+    for (int o = 0; o < C; o += 2) {
+      const float v0 = __uint_as_float(v[o]) + __ldg(bias + o);
+      const float v1 = __uint_as_float(v[o + 1]) + __ldg(bias + o + 1);
+      zz[o / 2] = __floats2bfloat162_rn(v0, v1);
+      aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+    }
+    if (zout) {
+      uint4* zo = reinterpret_cast<uint4*>(zout + pb);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
+    }
+  } else {
+    float zf[C];
+    load_px32(zf, zprev + pb);
+#pragma unroll
+    for (int o = 0; o < C; o += 2)
+      aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
+                                        __uint_as_float(v[o + 1]) * gelu_grad_f(zf[o + 1]));
   }
+  uint4* ao = reinterpret_cast<uint4*>(aout + pb);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) ao[k] = reinterpret_cast<const uint4*>(aa)[k];
+}
+
+template <int kMode>
+__global__ void __launch_bounds__(kWsConvThreads, 2)
+conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
+          const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
+          __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
+          int tiles_x, int tiles_y, int ntiles, int dil, unsigned* __restrict__ fault) {
+  // no static shared variables: the core matrices must start on 128-byte boundaries
+  extern __shared__ __align__(128) unsigned char wsu[];
+  unsigned char* ring = wsu;
+  unsigned char* wsm = wsu + kWsStages * kCmTile;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + kWBytes);
+  const uint32_t full0 = smem_u32(bar), empty0 = smem_u32(bar + kWsStages);
+  const uint32_t tfull0 = smem_u32(bar + 2 * kWsStages), tempty0 = smem_u32(bar + 2 * kWsStages + 2);
+  const uint32_t wfull = smem_u32(bar + 2 * kWsStages + 4);
+  volatile int* abort_ = reinterpret_cast<volatile int*>(bar + kWsBars);
+  volatile uint32_t* tslot = reinterpret_cast<volatile uint32_t*>(abort_ + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
   if (threadIdx.x == 0) {
-    for (int k = 0; k < kTapBufs; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)) : "memory");
+    for (int k = 0; k < kWsStages; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(full0 + 8 * k), "r"(kWsProdWarps * 32) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * k) : "memory");
+    }
+    for (int a = 0; a < 2; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull0 + 8 * a) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tempty0 + 8 * a), "r"(kWsEpiWarps * 32) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(wfull), "r"(kWsProdWarps * 32) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_ok = (smem_u32(usm) & 127u) == 0;  // misaligned operands: no MMA, raise the fault
+    *abort_ = (smem_u32(wsu) & 127u) != 0;  // misaligned operands: no MMA, raise the fault
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32((const void*)tslot)), "r"(kWsTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  const uint32_t tbase = smem_u32(tiles), wbase = smem_u32(wsm);
+  uint32_t last_bar = 0, last_par = 0;  // MMA thread: its last commit
 
-#pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int buf = tap % kTapBufs;
-    if (tap < 8) cp_wait_group<1>();
-    else cp_wait_group<0>();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // cp.async data -> tensor core
-    if (threadIdx.x == 0 && tap >= 1 && tap + 2 <= 8) {
-      // the buffer about to take tap + 2 fed tap - 1: its MMAs must be done
-      const int pt = tap - 1;
-      if (!mbar_wait(smem_u32(bars + pt % kTapBufs), (pt / kTapBufs) & 1)) s_ok = 0;
+  if (warp >= kWsEpiWarps && warp < kWsEpiWarps + kWsProdWarps) {
+    // ---- producers
+    const int pid = threadIdx.x - kWsEpiWarps * 32, np = kWsProdWarps * 32;
+    for (int q = pid; q < (int)(kWBytes / 16); q += np) cp16(wsm + q * 16, wk + q * 8);
+    cp_commit();
+    cp_wait_group<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_arrive(wfull);
+    bool go = *abort_ == 0;
+    int g = 0;
+    for (int i = 0; i < my_tiles && go; ++i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
+      for (int tap = 0; tap < 9; ++tap, ++g) {
+        const int st = g % kWsStages, u = g / kWsStages;
+        if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_)) { go = false; break; }
+        load_tap_cm_p(ring + st * kCmTile, in, b, ty * TR, tx * TW, tap_dy(tap, dil),
+                      tap_dx(tap, dil), H, W, pid, np);
+        cp_commit();
+        if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
+          cp_wait_group<kWsAhead>();
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(full0 + 8 * ((g - kWsAhead) % kWsStages));
+        }
+      }
     }
-    __syncthreads();
-    const bool ok = s_ok != 0;
-    if (threadIdx.x == 0 && ok) {
+    cp_wait_group<0>();
+    if (go) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int k = g > kWsAhead ? g - kWsAhead : 0; k < g; ++k) mbar_arrive(full0 + 8 * (k % kWsStages));
+    }
+  } else if (warp == kWsEpiWarps + kWsProdWarps) {
+    // ---- MMA issue
+    if (lane == 0) {
+      bool go = mbar_wait_ab(wfull, 0, abort_);
+      const uint32_t tbase = smem_u32(ring), wbase = smem_u32(wsm);
+      int g = 0;
+      for (int i = 0; i < my_tiles && go; ++i) {
+        const int a = i & 1;
+        if (i >= 2 && !mbar_wait_ab(tempty0 + 8 * a, ((i >> 1) - 1) & 1, abort_)) { go = false; break; }
+        for (int tap = 0; tap < 9; ++tap, ++g) {
+          const int st = g % kWsStages;
+          if (!mbar_wait_ab(full0 + 8 * st, (g / kWsStages) & 1, abort_)) { go = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t abase = tbase + st * (uint32_t)kCmTile;
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
+              umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (tap > 0 || cc > 0) ? 1u : 0u);
+            }
+          }
+          umma_commit(empty0 + 8 * st);
+          last_bar = empty0 + 8 * st;
+          last_par = (g / kWsStages) & 1;
+        }
+        if (!go) break;
+        umma_commit(tfull0 + 8 * a);
+      }
+      if (!go) *abort_ = 1;
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue
+    for (int i = 0; i < my_tiles; ++i) {
+      const int a = i & 1;
+      if (!mbar_wait_ab(tfull0 + 8 * a, (i >> 1) & 1, abort_)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t abase = tbase + buf * (uint32_t)kCmTile;
-#pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {  // K = 16 halves of this tap's 32 channels
-        const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
-          umma_bf16(tmem + h * C, ad, bd, (tap > 0 || cc > 0) ? 1u : 0u);
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   ::"r"(smem_u32(bars + buf)) : "memory");
-    }
-    if (tap + 2 <= 8) {
-      if (ok)
-        load_tap_cm(tiles + ((tap + 2) % kTapBufs) * kCmTile, in, b, y0, x0, tap_dy(tap + 2, dil),
-                    tap_dx(tap + 2, dil), H, W);
-      cp_commit();
-    }
-  }
-  // the last commit (tap 8) covers every MMA of the tile
-  if (threadIdx.x == 0 && s_ok && !mbar_wait(smem_u32(bars + 8 % kTapBufs), (8 / kTapBufs) & 1))
-    s_ok = 0;
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const bool ok = s_ok != 0;
-
-  if (ok) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      uint32_t v[32];
-      tmem_ld32(v, tmem + h * C + ((uint32_t)(warp * 32) << 16));
-      const int pix = h * kUmmaM + warp * 32 + lane;
-      const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
-      const int64_t pb = (((int64_t)b * H + y) * W + x) * C;
-      __nv_bfloat162 zz[C / 2], aa[C / 2];
-      if (kMode == 0) {
-#pragma unroll
-        for (int o = 0; o < C; o += 2) {
-          const float v0 = __uint_as_float(v[o]) + __ldg(bias + o);
-          const float v1 = __uint_as_float(v[o + 1]) + __ldg(bias + o + 1);
-          zz[o / 2] = __floats2bfloat162_rn(v0, v1);
-          aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
-        }
-        if (zout) {
-          uint4* zo = reinterpret_cast<uint4*>(zout + pb);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
-        }
-      } else {
-        float zf[C];
-        load_px32(zf, zprev + pb);
-#pragma unroll
-        for (int o = 0; o < C; o += 2)
-          aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
-                                            __uint_as_float(v[o + 1]) * gelu_grad_f(zf[o + 1]));
+      for (int h = 0; h < 2; ++h) {
+        uint32_t v[32];
+        tmem_ld32(v, tmem + a * 2 * C + h * C + ((uint32_t)(warp * 32) << 16));
+        conv_epilogue_half<kMode>(v, h * kUmmaM + warp * 32 + lane, b, ty * TR, tx * TW, H, W,
+                                  bias, zprev, zout, aout);
       }
-      uint4* ao = reinterpret_cast<uint4*>(aout + pb);
-#pragma unroll
-      for (int k = 0; k < 4; ++k) ao[k] = reinterpret_cast<const uint4*>(aa)[k];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(tempty0 + 8 * a);
     }
-  } else if (threadIdx.x == 0) {
-    atomicOr(fault, 1u);
   }
+
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) {
-    // after a timeout, MMAs still in flight must end before the free: the last
-    // issued commit went to some buffer; wait (bounded) on all of them
-    if (!ok)
-      for (int k = 0; k < kTapBufs; ++k) {
-        mbar_wait(smem_u32(bars + k), 0);
-        mbar_wait(smem_u32(bars + k), 1);
+  if (warp == kWsEpiWarps + kWsProdWarps) {
+    if (*abort_) {
+      if (lane == 0) {
+        atomicOr(fault, 1u);
+        // MMAs already issued finish on their own: wait (bounded) for the last commit
+        if (last_bar) {
+          uint32_t done = 0;
+          for (uint32_t it = 0; it < kSpinLimit && !done; ++it)
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(last_bar), "r"(last_par) : "memory");
+        }
       }
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+      __syncwarp();
+    }
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWsTmemCols)
                  : "memory");
   }
 }
@@ -919,8 +999,8 @@ px_status check_conv_fault(px_cnn* n, cudaStream_t st) {
 px_status set_conv_attrs() {
   static bool done = false;
   if (done) return PX_OK;
-  cudaError_t e = cudaFuncSetAttribute(conv32_umma<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_umma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
+  cudaError_t e = cudaFuncSetAttribute(conv32_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
@@ -938,10 +1018,11 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
                                                n->dil[0]);
   unsigned* fault = conv_fault_ptr();
   if (!fault) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
+  const int cgrid = std::min(tiles, 2 * px::device_sm_count());  // persistent: 2 CTAs per SM
   for (int l = 1; l <= 4; ++l)
-    conv32_umma<0><<<tiles, kConvThreads, kUmmaSmem, st>>>(
+    conv32_ws<0><<<cgrid, kWsConvThreads, kWsSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y, n->dil[l], fault);
+        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault);
   conv_last<<<grid_1d(px, 256), 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
@@ -979,9 +1060,9 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
         n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles, n->dil[l]);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
-    conv32_umma<1><<<tiles, kConvThreads, kUmmaSmem, st>>>(gcur, n->wb[l], nullptr, n->z[l - 1],
-                                                           nullptr, gnext, H, W, tiles_x, tiles_y,
-                                                           n->dil[l], conv_fault_ptr());
+    conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
+        gcur, n->wb[l], nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
+        n->dil[l], conv_fault_ptr());
     std::swap(gcur, gnext);
   }
   wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
