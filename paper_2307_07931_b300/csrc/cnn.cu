@@ -7,19 +7,19 @@
 // are periodic cross-correlations: z[p][o] = b[o] + sum_{dy,dx,c} W[o][c][dy][dx]
 // x[p + (dy - 1, dx - 1)][c].
 //
-// The 32 -> 32 layers are implicit GEMMs on the tensor cores (mma.sync
-// m16n8k16, BF16 in, FP32 accumulate): M = pixels, N = 32 output channels,
-// K = 9 taps x 32 channels. A CTA of 4 warps owns a 4 x 64 output tile; its
-// input patch (6 x 66 pixels, periodic wrap in the loads) and the weight
-// matrix are staged in shared memory by cp.async with a 16-byte-chunk XOR
-// swizzle so that every ldmatrix is conflict-free. Epilogues are fused:
+// The 32 -> 32 layers are implicit GEMMs on the 5th-generation tensor cores
+// (tcgen05.mma, BF16 in, FP32 accumulate in tensor memory): M = pixels, N = 32
+// output channels, K = 9 taps x 32 channels, one 4 x 64 output tile per step
+// of a persistent, warp-specialised kernel (producer warps stage each tap's
+// shifted tile with cp.async, periodic wrap in the loads; one thread issues
+// the MMAs; epilogue warps drain the accumulators). Epilogues are fused:
 // bias + GELU (forward, storing the pre-activation for the backward pass) or
 // the product with GELU'(z) of the previous layer (input gradient, which is
 // the same convolution with the weights flipped in both taps and transposed).
-// The weight gradient is a GEMM over pixels (M = 32, N = 288, K = pixels) on
-// the tensor cores as well, accumulated per CTA and reduced in a fixed order.
-// The 1 -> 32 and 32 -> 1 layers have 288 multiply-adds per pixel and run on
-// the CUDA cores.
+// The weight gradient is a GEMM over pixels on tcgen05 as well (M = 4 taps x
+// 32 channels, N = 32, K = pixels), accumulated in tensor memory per CTA and
+// reduced in a fixed order. The 1 -> 32 and 32 -> 1 layers have 288
+// multiply-adds per pixel and run on the CUDA cores.
 #include "px_internal.cuh"
 
 #include <cuda_bf16.h>
@@ -36,10 +36,8 @@ namespace cnn {
 constexpr int C = 32;            // channels of the hidden layers
 constexpr int K9 = 9 * C;        // GEMM K of a 32 -> 32 layer
 constexpr int TR = 4, TW = 64;   // output tile: rows x columns (one row per warp)
-static_assert(TW == 64, "load_tap_tile splits pixel indices with shifts");
+static_assert(TW == 64, "load_tap_cm_p splits pixel indices with shifts");
 constexpr int kConvThreads = 128;
-constexpr size_t kTileBytes = (size_t)TR * TW * 64;             // one [TR*TW px][32 ch] tile
-constexpr size_t kWgradSmem = 3 * kTileBytes;                     // dz tile + tap double buffer
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -47,35 +45,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ void cp16(void* s, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
 }
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait_group() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-__device__ __forceinline__ void ldsm4(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
-}
-__device__ __forceinline__ void ldsm4t(uint32_t (&r)[4], uint32_t addr) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(addr));
-}
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
-// Byte offset of (pixel, 16-byte channel chunk) in a swizzled [pixel][32 ch] tile:
-// chunk ^ ((pixel >> 1) & 3) keeps 8 consecutive pixels on 8 distinct bank groups.
-__device__ __forceinline__ int pix_off(int pix, int chunk) {
-  return pix * 64 + ((chunk ^ ((pix >> 1) & 3)) << 4);
-}
 
 __device__ __forceinline__ float gelu_f(float z) {
   return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
@@ -85,22 +61,6 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
          z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-// Stage the input tile seen by one tap: pixels (y0 + r + oy, x0 + c + ox) of
-// image b for r < TR, c < TW, periodic, all 32 channels. Consecutive threads
-// copy consecutive 16-byte chunks (a warp covers 8 whole pixels, 512 bytes).
-// The wrap is a conditional add or subtract when the tap offset is smaller
-// than the image (decided once per tap), a full modulo otherwise.
-__device__ __forceinline__ void load_tap_tile(unsigned char* dst, const __nv_bfloat16* act, int b,
-                                              int y0, int x0, int oy, int ox, int H, int W) {
-  const bool near = oy > -H && oy < H && ox > -W && ox < W;
-  for (int q = threadIdx.x; q < TR * TW * 4; q += blockDim.x) {
-    const int chunk = q & 3, pix = q >> 2;
-    const int r = pix >> 6, c = pix & (TW - 1);  // TW == 64
-    const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
-    const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
-    cp16(dst + pix_off(pix, chunk), act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
-  }
-}
 
 __device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p) {
   const uint4* q = reinterpret_cast<const uint4*>(p);
@@ -223,17 +183,22 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                ::"r"(bar) : "memory");
 }
 
-// load_tap_cm for a subset of the CTA: thread pid of np
+// Stage one tap's [R * 64 px][32 ch] input tile in the core-matrix layout
+// (chunk c of 8 channels at c * R * 1024 B, pixel p at p * 16 B), threads pid
+// of np. A warp copies 8 whole pixels: 512 contiguous global bytes into four
+// 128-byte shared rows. The periodic wrap is a conditional add or subtract
+// when the tap offset is smaller than the image, a full modulo otherwise.
+template <int R>
 __device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfloat16* act, int b,
                                               int y0, int x0, int oy, int ox, int H, int W,
                                               int pid, int np) {
   const bool near = oy > -H && oy < H && ox > -W && ox < W;
-  for (int q = pid; q < TR * TW * 4; q += np) {
+  for (int q = pid; q < R * TW * 4; q += np) {
     const int chunk = q & 3, pix = q >> 2;
     const int r = pix >> 6, c = pix & (TW - 1);
     const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
     const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
-    cp16(dst + chunk * kCmChunk + pix * 16, act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
+    cp16(dst + chunk * (R * TW * 16) + pix * 16, act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
   }
 }
 
@@ -332,7 +297,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       for (int tap = 0; tap < 9; ++tap, ++g) {
         const int st = g % kWsStages, u = g / kWsStages;
         if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_)) { go = false; break; }
-        load_tap_cm_p(ring + st * kCmTile, in, b, ty * TR, tx * TW, tap_dy(tap, dil),
+        load_tap_cm_p<TR>(ring + st * kCmTile, in, b, ty * TR, tx * TW, tap_dy(tap, dil),
                       tap_dx(tap, dil), H, W, pid, np);
         cp_commit();
         if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
@@ -422,101 +387,129 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   }
 }
 
-// Weight gradient of a 32 -> 32 layer (dilation d) on the tensor cores:
-//   dW[o][tap*32 + c] = sum_p dz[p][o] * in[p + off(tap)][c],  db[o] = sum_p dz[p][o].
-// GEMM with M = 32 output channels (A = dz^T), N = 288 (B = shifted input),
-// K = pixels. Persistent CTAs loop over 4 x 64 tiles; for each tile the taps
-// stream through a shared double buffer and warp w accumulates the 8 input
-// channels 8w..8w+7 of every tap in registers. Each CTA writes its partial
-// (32 x 288 + 32 floats) to `part`.
-__global__ void __launch_bounds__(kConvThreads)
-wgrad32_mma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
-            float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
-            int dil) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  unsigned char* dzs = sm;                  // [TR*TW px][32 ch]
-  unsigned char* tiles = sm + kTileBytes;   // 2 x [TR*TW px][32 ch]
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float acc[9][2][4];
-#pragma unroll
-  for (int i = 0; i < 9; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  float dbs = 0.f;  // thread t < 32 sums channel t
-  const uint32_t dbase = smem_u32(dzs), tbase = smem_u32(tiles);
-  // A = dz^T (m = channel, k = pixel) via ldmatrix.trans of [px][ch]:
-  //   matrices (px 0-7, ch 0-7) (px 0-7, ch 8-15) (px 8-15, ch 0-7) (px 8-15, ch 8-15)
-  const int ta_px = (lane & 7) + (lane >> 4) * 8;
-  const int ta_ch = (lane >> 3) & 1;
-  // B = shifted input (k = pixel, n = channel) via ldmatrix.trans, two k-steps:
-  //   matrices (px 0-7) (px 8-15) (px 16-23) (px 24-31), channel chunk = warp
-  const int tb_px = lane;
+// ---------------------------------------------------------------------------
+// Weight gradient of a 32 -> 32 layer on tcgen05 (the one launched):
+//   D[(tap, c)][o] = sum_p in[p + off(tap)][c] * dz[p][o],  db[o] = sum_p dz[p][o].
+// The contraction runs over pixels. The staged tiles ([chunk][pixel][8 ch])
+// are then MN-major operands: a core matrix is 8 pixels (K) x 8 channels
+// (16 B), K-neighbours 128 B apart (leading byte offset) and channel groups
+// 2048 B apart (stride byte offset). A CTA keeps 12 tiles of 16 KB in shared
+// memory, in this order: the 9 tap tiles of `in`, a tile of ones, the dz tile
+// and one spare (2 x 64-pixel tiles of 8 KB: 96 KB, two CTAs per SM, so one
+// CTA's MMAs overlap the other's staging). Three M = 128 blocks cover
+// (taps 0-3), (taps 4-7) and (tap 8, ones, two unused row groups): the ones
+// rows give db. N = 32 output channels; 8 MMAs of K = 16 pixels per block
+// and tile. The CTA loops over
+// its tiles accumulating in TMEM (3 x 32 columns), waits for each tile's MMAs
+// before restaging, and finally writes its partial
+// (part[o * 288 + tap * 32 + c], part[9216 + o]) for the fixed-order reduction.
+constexpr int kWgTiles = 12;
+constexpr int kWgRows = 2;                              // tile: 2 x 64 pixels (K = 128)
+constexpr uint32_t kWgChunk = kWgRows * TW * 16;        // 2048 B: next 8-channel group
+constexpr size_t kWgTile = (size_t)4 * kWgChunk;        // 8 KB
+constexpr size_t kWgUmmaSmem = kWgTiles * kWgTile + 64; // 96 KB: two CTAs per SM
+constexpr uint32_t kWgTmemCols = 128;
+constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);  // A and B MN-major
 
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int tx = t % tiles_x, ty = (t / tiles_x) % tiles_y, b = t / (tiles_x * tiles_y);
-    const int x0 = tx * TW, y0 = ty * TR;
-    __syncthreads();  // previous tile's shared reads are done
-    for (int qq = threadIdx.x; qq < TR * TW * 4; qq += blockDim.x) {
-      const int chunk = qq & 3, pix = qq >> 2;
-      const int r = pix >> 6, c = pix & (TW - 1);
-      cp16(dzs + pix_off(pix, chunk), dz + (((int64_t)b * H + y0 + r) * W + x0 + c) * C + chunk * 8);
-    }
-    load_tap_tile(tiles, in, b, y0, x0, tap_dy(0, dil), tap_dx(0, dil), H, W);
-    cp_commit();
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      if (tap < 8) {
-        load_tap_tile(tiles + ((tap + 1) & 1) * kTileBytes, in, b, y0, x0, tap_dy(tap + 1, dil),
-                      tap_dx(tap + 1, dil), H, W);
-        cp_commit();
-        cp_wait_group<1>();
-      } else {
-        cp_wait_group<0>();
-      }
-      __syncthreads();
-      if (tap == 0 && threadIdx.x < 32) {
-        for (int pix = 0; pix < TR * TW; ++pix) {
-          const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(
-              dzs + pix_off(pix, threadIdx.x >> 3)) + (threadIdx.x & 7);
-          dbs += __bfloat162float(*p);
-        }
-      }
-      const uint32_t cur = tbase + (tap & 1) * (uint32_t)kTileBytes;
+__global__ void __launch_bounds__(kConvThreads, 2)
+wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
+             float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
+             int dil, unsigned* __restrict__ fault) {
+  // no static shared variables: the core matrices must start on 128-byte boundaries
+  extern __shared__ __align__(128) unsigned char wgu[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wgu + kWgTiles * kWgTile);
+  volatile int* s_ok = reinterpret_cast<volatile int*>(bar + 1);
+  volatile uint32_t* tslot = reinterpret_cast<volatile uint32_t*>(bar + 2);
+  volatile int* abort_ = reinterpret_cast<volatile int*>(bar + 3);  // stays 0: one waiter only
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  {
+    uint4* ones = reinterpret_cast<uint4*>(wgu + 9 * kWgTile);  // BF16 1.0 = 0x3f80
+    for (int q = threadIdx.x; q < (int)(kWgTile / 16); q += blockDim.x)
+      ones[q] = make_uint4(0x3f803f80u, 0x3f803f80u, 0x3f803f80u, 0x3f803f80u);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32((const void*)tslot)), "r"(kWgTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_ok = (smem_u32(wgu) & 127u) == 0;
+    *abort_ = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t base = smem_u32(wgu);
+
 #pragma unroll 1
-      for (int k2 = 0; k2 < TR * TW / 32; ++k2) {  // 32 pixels = two k-steps
-        uint32_t bf[4];
-        ldsm4t(bf, cur + pix_off(k2 * 32 + tb_px, warp));
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int pix = k2 * 32 + h2 * 16 + ta_px;
-#pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            uint32_t af[4];
-            ldsm4t(af, dbase + pix_off(pix, mt * 2 + ta_ch));
-            mma16816(acc[tap][mt], af, bf[h2 * 2], bf[h2 * 2 + 1]);
-          }
+  for (int i = 0; i < my_tiles; ++i) {
+    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+    const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
+    if (*s_ok) {
+      for (int tap = 0; tap < 9; ++tap)
+        load_tap_cm_p<kWgRows>(wgu + tap * kWgTile, in, b, ty * kWgRows, tx * TW, tap_dy(tap, dil),
+                               tap_dx(tap, dil), H, W, threadIdx.x, blockDim.x);
+      load_tap_cm_p<kWgRows>(wgu + 10 * kWgTile, dz, b, ty * kWgRows, tx * TW, 0, 0, H, W,
+                             threadIdx.x, blockDim.x);
+    }
+    cp_commit();
+    cp_wait_group<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // tiles -> tensor core
+    __syncthreads();
+    if (threadIdx.x == 0 && *s_ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int blk = 0; blk < 3; ++blk) {
+#pragma unroll 4
+        for (int ks = 0; ks < (kWgRows * TW) / 16; ++ks) {
+          const uint64_t ad = umma_desc(base + blk * 4 * (uint32_t)kWgTile + ks * 256, 128, kWgChunk);
+          const uint64_t bd = umma_desc(base + 10 * (uint32_t)kWgTile + ks * 256, 128, kWgChunk);
+          asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                       ::"r"(tmem + blk * C), "l"(ad), "l"(bd), "r"(kIdescMN),
+                         "r"((i > 0 || ks > 0) ? 1u : 0u) : "memory");
         }
       }
-      __syncthreads();  // this buffer is refilled two taps later
+      umma_commit(smem_u32(bar));
+      // the tiles are restaged only after these MMAs have read them
+      if (!mbar_wait_ab(smem_u32(bar), i & 1, abort_)) *s_ok = 0;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+
+  float* out = part + (size_t)blockIdx.x * (C * K9 + C);
+  const bool ok = *s_ok != 0;
+#pragma unroll 1
+  for (int blk = 0; blk < 3; ++blk) {
+    const int tap = 4 * blk + warp;  // row group of this warp: tap 0..8, 9 = the ones rows
+    uint32_t v[32];
+    if (ok && my_tiles > 0) tmem_ld32(v, tmem + blk * C + ((uint32_t)(warp * 32) << 16));
+    else
+#pragma unroll
+      for (int o = 0; o < C; ++o) v[o] = 0u;
+    if (tap < 9) {
+#pragma unroll
+      for (int o = 0; o < C; ++o) out[o * K9 + tap * C + lane] = __uint_as_float(v[o]);
+    } else if (tap == 9 && lane == 0) {
+#pragma unroll
+      for (int o = 0; o < C; ++o) out[C * K9 + o] = __uint_as_float(v[o]);
     }
   }
-  // write the CTA partial: rows o (m), columns n = tap*32 + 8 warp + 2q
-  float* out = part + (size_t)blockIdx.x * (C * K9 + C);
-  const int g = lane >> 2, q = lane & 3;
-#pragma unroll
-  for (int tap = 0; tap < 9; ++tap)
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int col = tap * C + warp * 8 + 2 * q;
-      out[(mt * 16 + g) * K9 + col] = acc[tap][mt][0];
-      out[(mt * 16 + g) * K9 + col + 1] = acc[tap][mt][1];
-      out[(mt * 16 + g + 8) * K9 + col] = acc[tap][mt][2];
-      out[(mt * 16 + g + 8) * K9 + col + 1] = acc[tap][mt][3];
-    }
-  if (threadIdx.x < 32) out[C * K9 + threadIdx.x] = dbs;
+  if (!ok && threadIdx.x == 0) atomicOr(fault, 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols)
+                 : "memory");
 }
+
 
 // First layer (1 -> 32) forward: z = b + sum_tap W1[o][tap] x[p + tap]; a = gelu(z).
 __global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
@@ -1001,7 +994,7 @@ px_status set_conv_attrs() {
   if (done) return PX_OK;
   cudaError_t e = cudaFuncSetAttribute(conv32_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgradSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgUmmaSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
   return PX_OK;
@@ -1054,10 +1047,13 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
                                               n->dil[5]);
   __nv_bfloat16* gcur = n->g0;
   __nv_bfloat16* gnext = n->g1;
-  const int wg_ctas = std::min(tiles, px::device_sm_count() * 4);
+  // weight gradients: 2 x 64-pixel tiles, two CTAs per SM
+  const int wg_tiles = B * tiles_x * (H / kWgRows);
+  const int wg_ctas = std::min(wg_tiles, 2 * px::device_sm_count());
   for (int l = 4; l >= 1; --l) {
-    wgrad32_mma<<<wg_ctas, kConvThreads, kWgradSmem, st>>>(
-        n->a[l - 1], gcur, n->part, H, W, tiles_x, tiles_y, tiles, n->dil[l]);
+    wgrad32_umma<<<wg_ctas, kConvThreads, kWgUmmaSmem, st>>>(
+        n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, n->dil[l],
+        conv_fault_ptr());
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
