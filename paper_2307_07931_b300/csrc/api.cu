@@ -112,10 +112,15 @@ px_status ensure_scratch(px_ctx* c, size_t bytes) {
 
 int auto_tblock(const px::FieldDesc& f) {
   // FP64 is bound by the FP64 pipe at depth 1, so deeper blocking only adds
-  // redundant halo work; FP32 is bound by HBM at depth 1.
+  // redundant halo work. FP32 is bound by HBM at depth 1; measured on B300
+  // (GLUP/s, 200-800 sweeps): depth 4 on the register wavefront wins from
+  // about 6144^2 up (1687 vs 1567 at depth 8; 1830 vs 1430 at 16384^2), depth 8
+  // below (1223 vs 1016 at 2048^2, 63 vs 42 at 256^2, 16 vs 5 at depth 1 on
+  // 128^2).
   if (f.dtype == PX_F64) return 1;
   const int64_t cells = (int64_t)f.nx * f.ny;
-  return cells >= (1 << 16) ? 4 : 1;
+  if (cells >= ((int64_t)1 << 25)) return 4;
+  return cells >= (1 << 10) ? 8 : 1;
 }
 
 

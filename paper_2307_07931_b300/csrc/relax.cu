@@ -743,8 +743,9 @@ cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, con
 // FP32 kernel family for depth >= 2, from PX_FP32_WAVE: "w1" the one-row
 // wavefront, "w2" the two-row wavefront, anything else (the default) the
 // fastest measured per depth (16384^2, a report every sweep): the register
-// wavefront for depths 3 and 4, the one-row wavefront for 6 and 7, the
-// two-row wavefront for 2, 5 and 8.
+// wavefront for depths 3 and 4 (on fields of 2^24 cells or more; below, the
+// two-row one), the one-row wavefront for 6 and 7, the two-row wavefront for
+// 2, 5 and 8.
 int wave_kernel() {
   static int v = -1;
   if (v < 0) {
@@ -1165,7 +1166,8 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
   }
   if constexpr (sizeof(T) == 4) {
     const int fam = wave_kernel();
-    if (fam == 0 && (tb == 3 || tb == 4))
+    // the register wavefront needs many warps' worth of rows: from 2^24 cells
+    if (fam == 0 && (tb == 3 || tb == 4) && (int64_t)f.nx * f.ny >= ((int64_t)1 << 24))
       return tb == 3 ? launch_reg2_t<3>(f, src, dst, rho, k, rep, sched, sched_cap, st)
                      : launch_reg2_t<4>(f, src, dst, rho, k, rep, sched, sched_cap, st);
     if (fam == 2 || (fam == 0 && tb != 6 && tb != 7)) {
