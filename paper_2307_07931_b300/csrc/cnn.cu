@@ -512,69 +512,100 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
 
 
 // First layer (1 -> 32) forward: z = b + sum_tap W1[o][tap] x[p + tap]; a = gelu(z).
+// Row-structured loops shared by the three single-channel layers: a CTA takes
+// whole image rows (one division per row), its 4 W threads slots cover
+// (pixel x = slot / 4, channel group slot % 4), the three wrapped tap rows
+// are found once per row and the columns wrap with a conditional add when
+// the dilation is below the width.
+__device__ __forceinline__ int wrap_col(int x, int W, bool near) { return near ? wrap1(x, W) : wrapn(x, W); }
+
 __global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
                            const float* __restrict__ b1, __nv_bfloat16* __restrict__ zout,
                            __nv_bfloat16* __restrict__ aout, int B, int H, int W, int dil) {
-  __shared__ float ws[C * 9 + C];
-  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w1[i];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) ws[C * 9 + i] = b1[i];
-  __syncthreads();
-  const int64_t n = (int64_t)B * H * W;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const int64_t img = p / ((int64_t)H * W);
-    float v[9];
+  const int cg = threadIdx.x & 3;  // blockDim is a multiple of 4: fixed per thread
+  float wr[8][9], br[8];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrapn(yy + tap_dy(tap, dil), H), gx = wrapn(xx + tap_dx(tap, dil), W);
-      v[tap] = x[(img * H + gy) * W + gx];
-    }
-    __nv_bfloat162 zz[C / 2], aa[C / 2];
+  for (int j = 0; j < 8; ++j) {
+    br[j] = __ldg(b1 + cg * 8 + j);
 #pragma unroll
-    for (int o = 0; o < C; o += 2) {
-      float s0 = ws[C * 9 + o], s1 = ws[C * 9 + o + 1];
+    for (int tap = 0; tap < 9; ++tap) wr[j][tap] = __ldg(w1 + (cg * 8 + j) * 9 + tap);
+  }
+  const bool near = dil < W;
+  for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
+    const int img = row / H, yy = row - img * H;
+    const float* xr[3];
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        s0 = fmaf(ws[o * 9 + tap], v[tap], s0);
-        s1 = fmaf(ws[(o + 1) * 9 + tap], v[tap], s1);
+    for (int ty = 0; ty < 3; ++ty) xr[ty] = x + ((int64_t)img * H + wrapn(yy + (ty - 1) * dil, H)) * W;
+    for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
+      const int xx = t >> 2;
+      const int xs[3] = {wrap_col(xx - dil, W, near), xx, wrap_col(xx + dil, W, near)};
+      float v[9];
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) v[ty * 3 + tx] = __ldg(xr[ty] + xs[tx]);
+      __nv_bfloat162 zz[4], aa[4];
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        float s0 = br[j], s1 = br[j + 1];
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          s0 = fmaf(wr[j][tap], v[tap], s0);
+          s1 = fmaf(wr[j + 1][tap], v[tap], s1);
+        }
+        zz[j / 2] = __floats2bfloat162_rn(s0, s1);
+        aa[j / 2] = __floats2bfloat162_rn(gelu_f(s0), gelu_f(s1));
       }
-      zz[o / 2] = __floats2bfloat162_rn(s0, s1);
-      aa[o / 2] = __floats2bfloat162_rn(gelu_f(s0), gelu_f(s1));
-    }
-    uint4* zo = reinterpret_cast<uint4*>(zout + p * C);
-    uint4* ao = reinterpret_cast<uint4*>(aout + p * C);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (zout) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
-      ao[k] = reinterpret_cast<const uint4*>(aa)[k];
+      const int64_t po = ((int64_t)row * W + xx) * C + cg * 8;
+      if (zout) *reinterpret_cast<uint4*>(zout + po) = *reinterpret_cast<const uint4*>(zz);
+      *reinterpret_cast<uint4*>(aout + po) = *reinterpret_cast<const uint4*>(aa);
     }
   }
 }
 
 
 // Last layer (32 -> 1) forward: y = b6 + sum_{tap,c} W6[c][tap] a[p + tap][c] (FP32 out).
+// Four threads per pixel sum 8 channels each (coalesced 16-byte loads: a warp
+// reads 8 whole pixels per tap), then combine their partial sums in a fixed
+// order with two shuffles (W is a multiple of 8, so whole warps iterate).
 __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __restrict__ w6,
                           const float* __restrict__ b6, float* __restrict__ y, int B, int H, int W,
                           int dil) {
-  __shared__ float ws[C * 9];
-  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
-  __syncthreads();
-  const int64_t n = (int64_t)B * H * W;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const int64_t img = p / ((int64_t)H * W);
-    float s = b6[0];
-#pragma unroll 1
-    for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrapn(yy + tap_dy(tap, dil), H), gx = wrapn(xx + tap_dx(tap, dil), W);
-      float f[C];
-      load_px32(f, a + ((img * H + gy) * W + gx) * C);
+  const int cg = threadIdx.x & 3;
+  float wr[8][9];
 #pragma unroll
-      for (int c = 0; c < C; ++c) s = fmaf(ws[c * 9 + tap], f[c], s);
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) wr[j][tap] = __ldg(w6 + (cg * 8 + j) * 9 + tap);
+  const float bias = __ldg(b6);
+  const bool near = dil < W;
+  for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
+    const int img = row / H, yy = row - img * H;
+    const __nv_bfloat16* ar[3];
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty)
+      ar[ty] = a + ((int64_t)img * H + wrapn(yy + (ty - 1) * dil, H)) * W * C + cg * 8;
+    for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
+      const int xx = t >> 2;
+      const int xs[3] = {wrap_col(xx - dil, W, near), xx, wrap_col(xx + dil, W, near)};
+      float s = 0.f;
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) {
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(ar[ty] + (int64_t)xs[tx] * C));
+          const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 f = __bfloat1622float2(hv[e]);
+            s = fmaf(wr[2 * e][ty * 3 + tx], f.x, s);
+            s = fmaf(wr[2 * e + 1][ty * 3 + tx], f.y, s);
+          }
+        }
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (cg == 0) y[(int64_t)row * W + xx] = bias + s;
     }
-    y[p] = s;
   }
 }
 
@@ -603,36 +634,44 @@ __global__ void mse_grad(const float* __restrict__ y, const float* __restrict__ 
 __global__ void back_last(const float* __restrict__ dy, const float* __restrict__ w6,
                           const __nv_bfloat16* __restrict__ z5, __nv_bfloat16* __restrict__ dz5,
                           int B, int H, int W, int dil) {
-  __shared__ float ws[C * 9];
-  for (int i = threadIdx.x; i < C * 9; i += blockDim.x) ws[i] = w6[i];
-  __syncthreads();
-  const int64_t n = (int64_t)B * H * W;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(p % W), yy = (int)((p / W) % H);
-    const int64_t img = p / ((int64_t)H * W);
-    float g[9];
+  // four threads per pixel, 8 channels each (coalesced 16-byte z5 loads and dz5 stores)
+  const int cg = threadIdx.x & 3;
+  float wr[8][9];
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int gy = wrapn(yy - tap_dy(tap, dil), H), gx = wrapn(xx - tap_dx(tap, dil), W);
-      g[tap] = dy[(img * H + gy) * W + gx];
-    }
-    float z[C];
-    load_px32(z, z5 + p * C);
-    __nv_bfloat162 o[C / 2];
+  for (int j = 0; j < 8; ++j)
 #pragma unroll
-    for (int c = 0; c < C; c += 2) {
-      float s0 = 0.f, s1 = 0.f;
+    for (int tap = 0; tap < 9; ++tap) wr[j][tap] = __ldg(w6 + (cg * 8 + j) * 9 + tap);
+  const bool near = dil < W;
+  for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
+    const int img = row / H, yy = row - img * H;
+    const float* gr[3];  // dy at (q - off(tap)): tap row ty reads row y - (ty - 1) d
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        s0 = fmaf(ws[c * 9 + tap], g[tap], s0);
-        s1 = fmaf(ws[(c + 1) * 9 + tap], g[tap], s1);
+    for (int ty = 0; ty < 3; ++ty) gr[ty] = dy + ((int64_t)img * H + wrapn(yy - (ty - 1) * dil, H)) * W;
+    for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
+      const int xx = t >> 2;
+      const int xs[3] = {wrap_col(xx + dil, W, near), xx, wrap_col(xx - dil, W, near)};
+      float g[9];
+#pragma unroll
+      for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+        for (int tx = 0; tx < 3; ++tx) g[ty * 3 + tx] = __ldg(gr[ty] + xs[tx]);
+      const int64_t po = ((int64_t)row * W + xx) * C + cg * 8;
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(z5 + po));
+      const __nv_bfloat162* hz = reinterpret_cast<const __nv_bfloat162*>(&u);
+      __nv_bfloat162 o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 z = __bfloat1622float2(hz[e]);
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          s0 = fmaf(wr[2 * e][tap], g[tap], s0);
+          s1 = fmaf(wr[2 * e + 1][tap], g[tap], s1);
+        }
+        o[e] = __floats2bfloat162_rn(s0 * gelu_grad_f(z.x), s1 * gelu_grad_f(z.y));
       }
-      o[c / 2] = __floats2bfloat162_rn(s0 * gelu_grad_f(z[c]), s1 * gelu_grad_f(z[c + 1]));
+      *reinterpret_cast<uint4*>(dz5 + po) = *reinterpret_cast<const uint4*>(o);
     }
-    uint4* out = reinterpret_cast<uint4*>(dz5 + p * C);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) out[k] = reinterpret_cast<const uint4*>(o)[k];
   }
 }
 
@@ -731,14 +770,31 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
   }
 }
 
-// Sum partials over CTAs in index order (deterministic): dst[i] += sum_k part[k][i] * scale.
-__global__ void reduce_partials(const float* __restrict__ part, int nparts, int stride, int count,
-                                float* __restrict__ dst) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nparts; ++k) s += part[(size_t)k * stride + i];
-    dst[i] = s;
-  }
+// Sum partials over CTAs (deterministic): dst[i] = sum_k part[k][i]. A block
+// covers 32 outputs with 8 warps; warp w sums partials k = w, w + 8, ... in
+// order (coalesced: 32 consecutive outputs per load), then the 8 slices are
+// added in warp order.
+constexpr int kRedSlices = 8;
+__device__ __forceinline__ float reduce_slices(const float* __restrict__ part, int nparts,
+                                               int stride, int i, bool in) {
+  __shared__ float sl[kRedSlices][32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  float v = 0.f;
+  if (in)
+    for (int k = w; k < nparts; k += kRedSlices) v += part[(size_t)k * stride + i];
+  sl[w][l] = v;
+  __syncthreads();
+  float t = 0.f;
+  if (w == 0)
+    for (int q = 0; q < kRedSlices; ++q) t += sl[q][l];
+  return t;
+}
+__global__ void __launch_bounds__(32 * kRedSlices)
+reduce_partials(const float* __restrict__ part, int nparts, int stride, int count,
+                float* __restrict__ dst) {
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float t = reduce_slices(part, nparts, stride, i, i < count);
+  if (threadIdx.x < 32 && i < count) dst[i] = t;
 }
 
 // Adam on the flat FP32 parameter vector, then refresh the kernel-layout copies.
@@ -827,17 +883,18 @@ namespace px {
 namespace cnn {
 // [o][tap*32 + c] partials (plus 32 bias sums) summed over CTAs in index order,
 // written as W[o][c][tap] and b[o].
-__global__ void reduce_w32(const float* __restrict__ part, int nparts, float* __restrict__ dw,
-                           float* __restrict__ db) {
+__global__ void __launch_bounds__(32 * kRedSlices)
+reduce_w32(const float* __restrict__ part, int nparts, float* __restrict__ dw,
+           float* __restrict__ db) {
   const int stride = C * K9 + C;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < stride; i += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nparts; ++k) s += part[(size_t)k * stride + i];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const float t = reduce_slices(part, nparts, stride, i, i < stride);
+  if (threadIdx.x < 32 && i < stride) {
     if (i < C * K9) {
       const int o = i / K9, rem = i - o * K9, tap = rem / C, c = rem - tap * C;
-      dw[o * K9 + c * 9 + tap] = s;
+      dw[o * K9 + c * 9 + tap] = t;
     } else {
-      db[i - C * K9] = s;
+      db[i - C * K9] = t;
     }
   }
 }
@@ -1003,12 +1060,11 @@ px_status set_conv_attrs() {
 // Forward pass into n->a / n->z (z only when training) and output y.
 px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool train,
                   cudaStream_t st) {
-  const int64_t px = (int64_t)B * H * W;
   const int tiles_x = W / TW, tiles_y = H / TR;
   const int tiles = B * tiles_x * tiles_y;
-  conv_first<<<grid_1d(px, 256), 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
-                                               train ? n->z[0] : nullptr, n->a[0], B, H, W,
-                                               n->dil[0]);
+  const int rows_grid = std::min(B * H, 8 * px::device_sm_count());  // whole rows per CTA
+  conv_first<<<rows_grid, 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
+                                        train ? n->z[0] : nullptr, n->a[0], B, H, W, n->dil[0]);
   unsigned* fault = conv_fault_ptr();
   if (!fault) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
   const int cgrid = std::min(tiles, 2 * px::device_sm_count());  // persistent: 2 CTAs per SM
@@ -1016,7 +1072,7 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
     conv32_ws<0><<<cgrid, kWsConvThreads, kWsSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
         n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault);
-  conv_last<<<grid_1d(px, 256), 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
+  conv_last<<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network forward");
@@ -1042,8 +1098,8 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   const int nsc_cap = (rows + rpc - 1) / rpc;
   wgrad_single<1><<<nsc_cap, kWsThreads, 0, st>>>(n->a[4], n->dy,
                                                   n->part, B, H, W, rpc, n->dil[5]);
-  reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
-  back_last<<<grid_1d(px, 256), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W,
+  reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
+  back_last<<<std::min(B * H, 8 * px::device_sm_count()), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W,
                                               n->dil[5]);
   __nv_bfloat16* gcur = n->g0;
   __nv_bfloat16* gnext = n->g1;
@@ -1055,14 +1111,14 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
         n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, n->dil[l],
         conv_fault_ptr());
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
-    reduce_w32<<<36, 256, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
+    reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
         gcur, n->wb[l], nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
         n->dil[l], conv_fault_ptr());
     std::swap(gcur, gnext);
   }
   wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
-  reduce_partials<<<2, 256, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
+  reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network backward");
 }
