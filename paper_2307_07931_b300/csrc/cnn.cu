@@ -81,6 +81,9 @@ __device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p)
 // tensor cores' no-swizzle core-matrix order: [k / 8][n][k % 8].
 __host__ __device__ __forceinline__ int cm_index(int n, int k) { return (k / 8) * (C * 8) + n * 8 + (k % 8); }
 
+// Periodic column index for |x - wrapped| < W (a conditional add or subtract)
+// or any x (a full modulo), chosen once per launch from the dilation.
+__device__ __forceinline__ int wrap_col(int x, int W, bool near) { return near ? wrap1(x, W) : wrapn(x, W); }
 __device__ __forceinline__ int tap_dy(int tap, int d) { return (tap / 3 - 1) * d; }
 __device__ __forceinline__ int tap_dx(int tap, int d) { return (tap % 3 - 1) * d; }
 
@@ -517,7 +520,6 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
 // (pixel x = slot / 4, channel group slot % 4), the three wrapped tap rows
 // are found once per row and the columns wrap with a conditional add when
 // the dilation is below the width.
-__device__ __forceinline__ int wrap_col(int x, int W, bool near) { return near ? wrap1(x, W) : wrapn(x, W); }
 
 __global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
                            const float* __restrict__ b1, __nv_bfloat16* __restrict__ zout,
@@ -694,6 +696,7 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
   __shared__ float red[kWsThreads / 32][4][C / 4 * 9 + C / 4];
   const int cg = threadIdx.x & 3, slot = threadIdx.x >> 2;
   const int sd = kMode == 0 ? dil : -dil;  // shift of s1 relative to g32
+  const bool near = dil < W;
   const int rows = B * H;
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(rows, r0 + rows_per_cta);
   float acc[8][9], accb[8];
@@ -711,7 +714,7 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
     for (int ty = 0; ty < 3; ++ty) srow[ty] = s1 + ibase + (int64_t)wrapn(y + (ty - 1) * sd, H) * W;
     const __nv_bfloat16* grow = g32 + ((int64_t)row * W) * C + cg * 8;
     for (int x = slot; x < W; x += kWsThreads / 4) {
-      const int xs[3] = {wrapn(x - sd, W), x, wrapn(x + sd, W)};
+      const int xs[3] = {wrap_col(x - sd, W, near), x, wrap_col(x + sd, W, near)};
       float sv[9];
 #pragma unroll
       for (int ty = 0; ty < 3; ++ty)
