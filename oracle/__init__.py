@@ -52,6 +52,8 @@ def bind(lib):
         lib.oracle_sweep.argtypes = [i, i, i64, d, d, _dp, _dp, _dp]
         lib.oracle_sweep.restype = d
         lib.oracle_relax_n.argtypes = [i, i, d, d, _dp, _dp, i, i, _dp, _dp]
+        lib.oracle_rbsor_n.argtypes = [i, i, d, d, _dp, _dp, i, i, _dp, _dp]
+        lib.oracle_rbsor_n.restype = i
         lib.oracle_relax_n.restype = i
         lib.oracle_relax_unfused.argtypes = [i, i, d, d, _dp, _dp, i, _dp]
         lib.oracle_relax_unfused.restype = i
@@ -130,6 +132,25 @@ def relax_n(phi0, rho, h: float, omega: float, nsweeps: int, every: int = 0
                                 every, _ptr(out), _ptr(rep))
     if rc != 0:
         raise MemoryError("oracle_relax_n: allocation failed")
+    return out, rep[:report_count(nsweeps, every)]
+
+
+def rbsor_n(phi0, rho, h: float, omega: float, nsweeps: int, every: int = 0
+            ) -> tuple[np.ndarray, np.ndarray]:
+    """nsweeps red-black SOR sweeps from phi0 (red = (i + j) even first, then
+    black, each in place with the Jacobi per-point update); returns (phi^n,
+    reports) with reports[k] = ||rho - L phi^(k*every)||_inf of the input
+    state of that sweep. nx and ny must be even."""
+    phi0, rho = _f64(phi0), _f64(rho)
+    nx, ny = _shape(phi0)
+    if nx % 2 or ny % 2:
+        raise ValueError("red-black SOR needs even nx and ny")
+    out = np.empty_like(phi0)
+    rep = np.zeros(max(1, report_count(nsweeps, every)), dtype=np.float64)
+    rc = _load().oracle_rbsor_n(nx, ny, h, omega, _ptr(phi0), _ptr(rho), nsweeps, every,
+                                _ptr(out), _ptr(rep))
+    if rc != 0:
+        raise MemoryError("oracle_rbsor_n: allocation failed")
     return out, rep[:report_count(nsweeps, every)]
 
 

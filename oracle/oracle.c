@@ -249,3 +249,47 @@ int oracle_relax_n_omp(int nx, int ny, double h, double omega, double* a,
   (void)nthreads;
   return used;
 }
+
+/* Red-black SOR: the relaxation the paper names as the smoother of Proto's
+ * multigrid (Sec. VI, future work), in its standard definition. One sweep
+ * updates IN PLACE first every red cell ((i + j) even), then every black cell
+ * ((i + j) odd), each with the Jacobi per-point update of oracle_sweep,
+ *     phi[i,j] <- (phi + w*s) - lam*rho,  w = omega/4, lam = omega*h^2/4,
+ * where s is the tap sum of the CURRENT array: during the red half all
+ * neighbours (black) are still old, during the black half all neighbours
+ * (red) are already new. omega = 1 is red-black Gauss-Seidel. nx and ny must
+ * be even, so that the colouring agrees across the periodic wrap. The
+ * residual reported for a sweep is that of its INPUT state, over all cells,
+ * in the expressions of oracle_sweep.
+ * Returns 0, -1 on allocation failure, -2 for an odd extent. */
+int oracle_rbsor_n(int nx, int ny, double h, double omega, const double* phi0,
+                   const double* rho, int nsweeps, int every, double* phi_out,
+                   double* resid) {
+  if (nx % 2 != 0 || ny % 2 != 0) return -2;
+  size_t n = (size_t)nx * (size_t)ny;
+  double* a = (double*)malloc(n * sizeof(double));
+  if (!a) return -1;
+  memcpy(a, phi0, n * sizeof(double));
+  double ih2 = 1.0 / (h * h);
+  double w = omega / 4.0, lam = omega * h * h / 4.0;
+  for (int s = 0; s < nsweeps; ++s) {
+    if (resid && every > 0 && s % every == 0) {
+      double R = 0.0;
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+          R = maxnan(R, fabs(ih2 * taps(nx, ny, nx, a, i, j) - rho[(int64_t)j * nx + i]));
+      resid[s / every] = R;
+    }
+    for (int colour = 0; colour < 2; ++colour)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          if (((i + j) & 1) != colour) continue;
+          int64_t c = (int64_t)j * nx + i;
+          double sv = taps(nx, ny, nx, a, i, j);
+          a[c] = (a[c] + w * sv) - lam * rho[c];
+        }
+  }
+  memcpy(phi_out, a, n * sizeof(double));
+  free(a);
+  return 0;
+}
