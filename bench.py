@@ -40,6 +40,13 @@ ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cel
 MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (2226466688 + 1045071360) / 16384**2}
 
 
+# red-black SOR: FP32 runs three sweeps (six colour stages) per launch of the
+# register wavefront; FP64 runs a red pass (all cells read, residual, red
+# updated) and a black pass (black updated in place) per sweep
+RBSOR_KERNEL = {"f32": "relaxR2_f32<6,true>", "f64": "rb_pass<double,2>"}
+RBSOR_LAUNCHES_PER_SWEEP = {"f32": 1.0 / 3.0, "f64": 2.0}
+
+
 def kernel_name(dt: str, tb: int) -> str:
     if tb == 1:
         return "relax1_stream<float,4>" if dt == "f32" else "relax1_stream<double,2>"
@@ -224,6 +231,37 @@ def time_variant(px, torch, phi0, out, rho, resid, h, tblock, steps, warmup, eve
         b.record(st)
     torch.cuda.synchronize()
     return [a.elapsed_time(b) / 1000.0 for a, b in evs]
+
+
+def bench_rbsor(px, torch, phi0, out, rho, resid, h, cells, hbm_peak, steps, warmup):
+    """Red-black Gauss-Seidel (omega = 1) on the same field: SWEEPS sweeps per
+    step with a report every sweep, FP32 and FP64 storage. Algorithmic bytes
+    per sweep are those of one Jacobi sweep (read phi and rho, write phi')."""
+    res = {}
+    st = torch.cuda.current_stream()
+    for dt in ("f32", "f64"):
+        def step():
+            px.rbsor_n(phi0[dt], out[dt], rho[dt], h, 1.0, SWEEPS, resid, 1)
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            a.record(st)
+            step()
+            b.record(st)
+        torch.cuda.synchronize()
+        t = statistics.median(a.elapsed_time(b) / 1000.0 for a, b in evs)
+        lps = int(np.ceil(RBSOR_LAUNCHES_PER_SWEEP[dt] * SWEEPS))
+        # algorithmic bytes per launch: phi and rho read, phi' written once
+        per_launch = ALGO_BYTES[dt] * cells / (t / lps) / 1e9
+        res[dt] = {"kernel": RBSOR_KERNEL[dt], "omega": 1.0, "ms_per_step": 1000 * t,
+                   "GLUP_s": cells * SWEEPS / t / 1e9,
+                   "effective_GB_s": ALGO_BYTES[dt] * cells * SWEEPS / t / 1e9,
+                   "launches_per_step": lps, "algo_GB_s_per_launch": per_launch,
+                   "hbm_frac": per_launch / hbm_peak}
+    return res
 
 
 def bench_batched(px, torch, steps: int, warmup: int):
@@ -462,6 +500,8 @@ def run_gpu(args, world, rank, local):
     h2d = 2 * cells * 4
     d2h = cells * 4 + SWEEPS * 8
 
+    rbsor = bench_rbsor(px, torch, phi0, out, rho, resid, h, cells, hbm_peak,
+                        min(K, 3), min(W, 3))
     batched = bench_batched(px, torch, K, W) if not args.quick else None
     ttt = bench_time_to_tol(px, torch) if not args.quick else None
 
@@ -495,6 +535,7 @@ def run_gpu(args, world, rank, local):
                         f"launch times the cell count",
             },
             "variants": variants,
+            "rbsor": rbsor,
             "fp64_note": "FP64 sweep is bound by the FP64 pipe (0.555 T DFMA/s measured), "
                          "6 FP64 ops per cell",
             "e2e": {"value": cells * SWEEPS / e2e_t / 1e9 * world, "unit": UNIT,

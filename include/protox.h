@@ -159,6 +159,28 @@ px_status px_relax_n_static(const px_grid* g, const void* phi_in, void* phi_out,
                             const void* rho, double omega, int nsweeps, int tblock,
                             double* resid_dev, int report_every, void* stream);
 
+/* nsweeps red-black SOR sweeps from phi_in into phi_out: the relaxation the
+ * paper names as the smoother of Proto's multigrid (Sec. VI, future work), in
+ * its standard definition. One sweep updates, in place, first every red cell
+ * ((x + y) even) and then every black cell, each with the per-point update of
+ * px_relax_n, phi <- phi + (omega h^2 / 4)(L phi - rho), L phi taken from the
+ * current state (black neighbours old during the red half, red neighbours new
+ * during the black half). omega = 1 is red-black Gauss-Seidel; 0 < omega < 2
+ * converges on the mean-zero problem.
+ *
+ *  g                unghosted layout (PX_EUNSUPPORTED otherwise), nx and ny
+ *                   even (the colouring must agree across the periodic wrap;
+ *                   PX_EINVAL otherwise), FP64 or FP32.
+ *  phi_in, phi_out, rho, omega, nsweeps, resid_dev, report_every, stream
+ *                   as in px_relax_n; resid_dev[k] is the residual of the
+ *                   INPUT state of sweep k * report_every, over all cells.
+ * Each sweep is two launches (red pass out of place with the residual, black
+ * pass in place); the context's scratch field is used when in place or for
+ * two sweeps or more. Asynchronous. */
+px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* phi_out,
+                     const void* rho, double omega, int nsweeps, double* resid_dev,
+                     int report_every, void* stream);
+
 /* The launch plan px_relax_n would use for these arguments, without running
  * it: *tblock_used = sweeps fused per launch (after auto choice and layout
  * fallback), *launches = relax kernel launches (excluding the zero-fill of

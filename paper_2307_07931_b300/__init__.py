@@ -78,6 +78,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_status_string.restype = ctypes.c_char_p
     lib.px_apply_stencil.argtypes = [_vp, gp, _vp, _vp, _vp]
     lib.px_relax_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
+    lib.px_rbsor_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, _vp, i, _vp]
     lib.px_residual_norm.argtypes = [_vp, gp, _vp, _vp, dp, dp, _vp]
     lib.px_residual_norm_async.argtypes = [_vp, gp, _vp, _vp, _vp, _vp]
     ip = ctypes.POINTER(ctypes.c_int)
@@ -110,7 +111,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         getattr(lib, name).restype = i
     lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
                              ctypes.POINTER(SolveInfo), _vp]
-    for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n",
+    for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n", "px_rbsor_n",
                  "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
                  "px_relax_n_static", "px_solve", "px_batch_plan", "px_batch_run",
                  "px_batch_destroy"):
@@ -231,6 +232,28 @@ def relax_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, tblock: 
                                         _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
                                         int(tblock), _ptr(resid), int(report_every),
                                         _stream(stream)))
+    return phi_out
+
+
+def rbsor_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, resid=None,
+            report_every: int = 0, ctx: Context | None = None, stream=None):
+    """nsweeps red-black SOR sweeps phi_in -> phi_out (px_rbsor_n): red cells
+    ((x + y) even) then black cells, in place within a sweep; nx, ny even.
+    `resid`, if given, is a float64 CUDA tensor of ceil(nsweeps /
+    report_every) entries (residual of each reported sweep's input state)."""
+    _same_layout(phi_in, phi_out)
+    _same_layout(phi_in, rho)
+    ctx = ctx or context(phi_in.device.index)
+    g = grid_of(phi_in, h, 0)
+    if resid is not None:
+        import torch
+        need = (nsweeps + report_every - 1) // report_every if report_every > 0 else 0
+        if resid.dtype != torch.float64 or not resid.is_cuda or resid.numel() < need \
+                or not resid.is_contiguous():
+            raise ValueError(f"resid must be a contiguous CUDA float64 tensor of >= {need}")
+    ctx.check(load_library().px_rbsor_n(ctx.handle, ctypes.byref(g), _ptr(phi_in),
+                                        _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
+                                        _ptr(resid), int(report_every), _stream(stream)))
     return phi_out
 
 

@@ -96,6 +96,20 @@ cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst,
                          double* resid, int s0, int every, unsigned long long* sched,
                          int sched_cap, cudaStream_t st);
 
+// One pass of a red-black SOR sweep (rbsor.cu): red_pass = src -> dst with the
+// input-state residual folded into *slot (if not NULL); else black cells of
+// dst updated in place.
+// `sweeps` (1..4) red-black SOR sweeps in one launch of the FP32 register
+// wavefront (two stages per sweep: red, then black); src != dst, vector
+// layout (vector_ok), nx and ny even. Reports as launch_relax (sweep s0 first).
+cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, const float* rho,
+                             double omega, int sweeps, double* resid, int s0, int every,
+                             unsigned long long* sched, int sched_cap, cudaStream_t st);
+
+cudaError_t launch_rbsor_pass(const FieldDesc& f, const void* src, void* dst, const void* rho,
+                              double omega, bool red_pass, bool vec, double* slot,
+                              cudaStream_t st);
+
 cudaError_t launch_apply_stencil(const FieldDesc& f, const void* phi, void* out,
                                  cudaStream_t st);
 // out2[0] = max|rho - L phi| (FP64), out2[1] = max|rho|; out2 zero-filled here.

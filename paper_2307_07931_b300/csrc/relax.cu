@@ -756,8 +756,10 @@ int wave_kernel() {
 }
 
 // ---------------------------------------------------------------------------
-// relaxR2_f32: register wavefront, TB = 3 or 4 sweeps per launch, no shared
-// tiles and no CTA barriers.
+// relaxR2_f32: register wavefront, TB stages per launch, no shared tiles and
+// no CTA barriers. A stage is a Jacobi sweep (TB = 3 or 4) or, with kRB, half
+// a red-black sweep (TB = 2, 4, 6, 8: red, black, red, ...; a stage updates
+// the cells of its colour and copies the others).
 //
 // One warp owns a strip of 128 cells (4 per lane, periodic columns x0 - 4 ..
 // x0 + 123) and a range of output rows, and runs every stage itself. Step s
@@ -770,7 +772,8 @@ int wave_kernel() {
 // cp.async, waits, addresses, predicates) is shared by two rows. x neighbours
 // come from shuffles. Rows and columns outside the valid cone (one cell and
 // one row smaller per stage) are computed and discarded: the strip owns its
-// central 120 columns (lanes 1..30) and the range's own rows.
+// central 128 - 8 HL columns (HL = ceil(TB / 4) halo lanes per side: lanes
+// 1..30 up to 4 stages, 2..29 up to 8) and the range's own rows.
 //
 // phi and rho rows stream through per-warp shared-memory rings filled by
 // cp.async kR2Ahead row pairs ahead; each lane copies and reads back only its
@@ -781,7 +784,7 @@ int wave_kernel() {
 // the bottom always (stage t reads no row beyond the newest loaded one).
 // Exact values of rows and wrapped columns outside the owned ones are
 // residuals of real cells, so including them leaves the max unchanged; only
-// the two edge lanes, whose x neighbours are garbage from the first stage on,
+// the HL edge lanes per side, whose columns lose exactness stage by stage,
 // are dropped, once, before the warp reduction.
 //
 // Load balance. SMs run this kernel at different speeds (how many warps share
@@ -795,8 +798,11 @@ int wave_kernel() {
 // The owner sees the lower end at its next claim. Nothing waits on another
 // warp: every loop is bounded, and a failed steal ends the warp. Without
 // `sched` the static ranges are used as they are.
-constexpr int kRHalo = 4;                       // halo columns per side (one lane)
-constexpr int kRStrip = 128, kROwned = kRStrip - 2 * kRHalo;
+constexpr int kRStrip = 128;
+// Halo lanes per side: each stage's valid region is one column narrower per
+// side, so TB stages need TB halo columns (4 per lane).
+template <int TB> __host__ __device__ constexpr int r_halo_lanes() { return (TB + 3) / 4; }
+template <int TB> __host__ __device__ constexpr int r_owned() { return kRStrip - 8 * r_halo_lanes<TB>(); }
 constexpr int kRPhiRing = 8, kRRhoRing = 16;    // ring rows (powers of two)
 constexpr int kRWarps = 8;                      // warps per CTA
 constexpr int kRWarpFloats = (kRPhiRing + kRRhoRing) * kRStrip;
@@ -846,7 +852,7 @@ struct R2Task {
   int y0, lim, lmax;
 };
 
-template <int TB, int P, bool kEdge>
+template <int TB, int P, bool kEdge, bool kRB>
 __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
                                        const float* __restrict__ rho, float* __restrict__ out,
                                        float* ring, int ny, int64_t ld, int gx, bool own,
@@ -892,8 +898,16 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
       const float s1 = fmaf(-4.0f, c[x], (w1 + e1) + (b[x] + d[x]));
       q0[x] = fmaf(s0, k.ih2, -rh0[x]);
       q1[x] = fmaf(s1, k.ih2, -rh1[x]);
-      o0[x] = fmaf(k.c, q0[x], b[x]);
-      o1[x] = fmaf(k.c, q1[x], c[x]);
+      if constexpr (kRB) {
+        // red-black stages: row r0 - t has the parity of its stage's colour
+        // flipped at every stage, so the updated cells are the odd columns of
+        // the first row and the even ones of the second at every stage
+        o0[x] = (x & 1) ? fmaf(k.c, q0[x], b[x]) : b[x];
+        o1[x] = (x & 1) ? c[x] : fmaf(k.c, q1[x], c[x]);
+      } else {
+        o0[x] = fmaf(k.c, q0[x], b[x]);
+        o1[x] = fmaf(k.c, q1[x], c[x]);
+      }
     }
     // Residual of state t-1 at rows r0-t, r0-t+1: exact once the row index
     // is >= t (level t-1 is exact from index t-1 on, and at the bottom every
@@ -982,19 +996,23 @@ __device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips,
   return false;
 }
 
-template <int TB>
+template <int TB, bool kRB>
 __global__ void __launch_bounds__(kRWarps * 32)
 relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
             int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
             unsigned long long* sched) {
+  static_assert(TB + 2 * kR2Ahead + 2 <= kRRhoRing, "rho rows in use exceed the ring");
+  static_assert(!kRB || TB % 2 == 0, "red-black launches hold whole sweeps");
   extern __shared__ __align__(16) float rsm[];
   const int lane = threadIdx.x & 31;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   float* const ring = rsm + (threadIdx.x >> 5) * kRWarpFloats + lane * 4;
+  // report of stage t: Jacobi, sweep s0 + t; red-black, the red stage t = 2 i
+  // of sweep s0 + i (its input state is the sweep's)
   bool due[TB];
 #pragma unroll
-  for (int t = 0; t < TB; ++t) due[t] = rep.due(t);
+  for (int t = 0; t < TB; ++t) due[t] = kRB ? (t % 2 == 0 && rep.due(t / 2)) : rep.due(t);
   R2State<TB> S;
 #pragma unroll
   for (int t = 0; t < TB; ++t) S.mx[t] = 0.f;
@@ -1013,9 +1031,10 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
       }
       if (!have) break;
     }
-    const int col = s * kROwned - kRHalo + lane * 4;
+    constexpr int HL = r_halo_lanes<TB>();
+    const int col = s * r_owned<TB>() - 4 * HL + lane * 4;
     const int gx = wrapn(col, nx);
-    const bool own = lane > 0 && lane < 31 && col < nx;
+    const bool own = lane >= HL && lane < 32 - HL && col < nx;
     R2Task T;
     T.y0 = y0;
     T.lim = sched ? y0 : e;  // with sched, rows are claimed as the wavefront reaches them
@@ -1054,45 +1073,46 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
 #pragma unroll 1
     for (; r0 < kPro; r0 += 4) {
       if (!ready(r0)) goto task_done;
-      rstep2<TB, 0, true>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, true, kRB>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) goto task_done;
-      rstep2<TB, 1, true>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, true, kRB>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
     }
 #pragma unroll 1
     for (;; r0 += 4) {
       if (!ready(r0)) break;
-      rstep2<TB, 0, false>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, false, kRB>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) break;
-      rstep2<TB, 1, false>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, false, kRB>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
     }
   task_done:
     cp_wait<0>();  // the next task's prologue reuses the ring slots
     have = false;
   }
-  const bool edge_lane = lane == 0 || lane == 31;
+  const bool edge_lane = lane < r_halo_lanes<TB>() || lane >= 32 - r_halo_lanes<TB>();
 #pragma unroll
   for (int t = 0; t < TB; ++t) {
     if (due[t]) {
       const uint32_t m = warp_max(edge_lane ? 0u : __float_as_uint(S.mx[t]));
-      if (lane == 0) atomic_max_bits(rep.slot(t), to_f64_bits(m));
+      if (lane == 0) atomic_max_bits(rep.slot(kRB ? t / 2 : t), to_f64_bits(m));
     }
   }
 }
 
-template <int TB>
+template <int TB, bool kRB = false>
 cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
                           cudaStream_t st) {
   static int occ = 0;
   if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB>,
+    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB>, kRWarps * 32, kRSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB>, kRWarps * 32,
+                                                      kRSmem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
   }
-  const int nstrips = (f.nx + kROwned - 1) / kROwned;
+  const int nstrips = (f.nx + r_owned<TB>() - 1) / r_owned<TB>();
   const int64_t resident = (int64_t)occ * device_sm_count();
   const int64_t warps = resident * kRWarps;
   // Dynamic balance needs one range per warp at most and rows that fit the
@@ -1103,11 +1123,14 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   const int64_t segs = std::max<int64_t>(1, warps / nstrips);
   int64_t H = std::max<int64_t>(32, (f.ny + segs - 1) / segs);
   if (!dyn) H = std::min<int64_t>(1024, H);
+  // red-black: every range starts on an even row (claims and steals keep the
+  // parity), which fixes each stage's updated columns at compile time
+  if (kRB) H += H & 1;
   const int nseg = (int)((f.ny + H - 1) / H);
   const int64_t tasks = (int64_t)nstrips * nseg;
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>((tasks + kRWarps - 1) / kRWarps, resident));
-  relaxR2_f32<TB><<<blocks, kRWarps * 32, kRSmem, st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
+  relaxR2_f32<TB, kRB><<<blocks, kRWarps * 32, kRSmem, st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
                                                         nstrips, nseg, k, rep, dyn ? sched : nullptr);
   return cudaGetLastError();
 }
@@ -1217,6 +1240,25 @@ int device_sm_count() {
     g_sms[dev] = n > 0 ? n : 148;
   }
   return g_sms[dev];
+}
+
+cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, const float* rho,
+                             double omega, int sweeps, double* resid, int s0, int every,
+                             unsigned long long* sched, int sched_cap, cudaStream_t st) {
+  Reports rep;
+  rep.resid = (resid && every > 0) ? resid : nullptr;
+  rep.s0 = s0;
+  rep.every = every > 0 ? every : 1;
+  Coef<float> k;
+  k.c = (float)(omega * f.h * f.h / 4.0);
+  k.ih2 = (float)(1.0 / (f.h * f.h));
+  switch (sweeps) {
+    case 1: return launch_reg2_t<2, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    case 2: return launch_reg2_t<4, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    case 3: return launch_reg2_t<6, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    case 4: return launch_reg2_t<8, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 bool vector_ok(const FieldDesc& f, const void* a, const void* b, const void* c) {
