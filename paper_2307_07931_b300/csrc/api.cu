@@ -113,14 +113,14 @@ px_status ensure_scratch(px_ctx* c, size_t bytes) {
 
 int auto_tblock(const px::FieldDesc& f) {
   // FP64 is bound by the FP64 pipe at depth 1, so deeper blocking only adds
-  // redundant halo work. FP32 is bound by HBM at depth 1; measured on B300
-  // (GLUP/s, 200-800 sweeps): depth 4 on the register wavefront wins from
-  // about 6144^2 up (1687 vs 1567 at depth 8; 1830 vs 1430 at 16384^2), depth 8
-  // below (1223 vs 1016 at 2048^2, 63 vs 42 at 256^2, 16 vs 5 at depth 1 on
-  // 128^2).
+  // redundant halo work. FP32 is bound by HBM at depth 1 and by instruction
+  // issue from depth 4 or so; measured on B300 (GLUP/s, 200 sweeps, a report
+  // every sweep), depth 8 is the fastest from 128^2 up: on the register
+  // wavefront 2406 vs 1989 at depth 4 (16384^2), 2067 vs 1679 (6144^2), 1431
+  // vs 1019 (3072^2); on the two-row wavefront 997 (2048^2), 63 vs 42 at
+  // depth 4 (256^2), 16 vs 5 at depth 1 (128^2).
   if (f.dtype == PX_F64) return 1;
   const int64_t cells = (int64_t)f.nx * f.ny;
-  if (cells >= ((int64_t)1 << 25)) return 4;
   return cells >= (1 << 10) ? 8 : 1;
 }
 
@@ -330,8 +330,9 @@ px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
 
 // Red-black sweeps per launch of the FP32 register wavefront (1..4; the
 // environment variable PX_RB_SWEEPS overrides the default for A/B timing).
-// Measured at 16384^2 with a report every sweep: 496, 984, 1542 and 1387
-// GLUP/s for 1..4 (four sweeps need two halo lanes per side and 140 registers).
+// Measured at 16384^2 with a report every sweep: 496, 984, 1542 and 1525
+// GLUP/s for 1..4 (four sweeps need two halo lanes per side and one CTA of 12
+// warps per SM).
 static int rb_sweeps() {
   static int v = 0;
   if (v == 0) {

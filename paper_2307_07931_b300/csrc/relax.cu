@@ -739,18 +739,19 @@ cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, con
   return cudaGetLastError();
 }
 
-// 2 = relaxW2_f32 (default), 1 = relaxW_f32; PX_WAVE_ROWS selects for A/B timing.
 // FP32 kernel family for depth >= 2, from PX_FP32_WAVE: "w1" the one-row
-// wavefront, "w2" the two-row wavefront, anything else (the default) the
-// fastest measured per depth (16384^2, a report every sweep): the register
-// wavefront for depths 3 and 4 (on fields of 2^24 cells or more; below, the
-// two-row one), the one-row wavefront for 6 and 7, the two-row wavefront for
-// 2, 5 and 8.
+// wavefront, "w2" the two-row wavefront, "r" the register wavefront at every
+// size, anything else (the default) the fastest measured (200 sweeps, a
+// report every sweep): the register wavefront at depths 3..8 on fields of
+// 2^23 cells or more (depth 8: 2406 vs 1424 GLUP/s on the two-row wavefront
+// at 16384^2, 1431 vs 912 at 3072^2); below, where the two-row wavefront wins
+// at depth 8 (997 vs 909 at 2048^2), the one-row wavefront for depths 6 and 7
+// and the two-row one for the others; depth 2 always the two-row one.
 int wave_kernel() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv("PX_FP32_WAVE");
-    v = (e && !strcmp(e, "w1")) ? 1 : (e && !strcmp(e, "w2")) ? 2 : 0;
+    v = (e && !strcmp(e, "w1")) ? 1 : (e && !strcmp(e, "w2")) ? 2 : (e && !strcmp(e, "r")) ? 3 : 0;
   }
   return v;
 }
@@ -804,9 +805,17 @@ constexpr int kRStrip = 128;
 template <int TB> __host__ __device__ constexpr int r_halo_lanes() { return (TB + 3) / 4; }
 template <int TB> __host__ __device__ constexpr int r_owned() { return kRStrip - 8 * r_halo_lanes<TB>(); }
 constexpr int kRPhiRing = 8, kRRhoRing = 16;    // ring rows (powers of two)
-constexpr int kRWarps = 8;                      // warps per CTA
+// Warps per CTA: 8 (two CTAs per SM up to 128 registers a thread), or 12
+// where a depth needs more registers: one CTA per SM then, three warps per
+// scheduler at up to 168 registers (each scheduler has 16K). Measured at
+// 16384^2, depth 8: 2570 GLUP/s with 12 warps, 2406 with 8 (183 registers).
+template <int TB, bool kRB> __host__ __device__ constexpr int r_warps() {
+  return (kRB ? TB >= 8 : TB >= 5) ? 12 : 8;
+}
 constexpr int kRWarpFloats = (kRPhiRing + kRRhoRing) * kRStrip;
-constexpr size_t kRSmem = (size_t)kRWarps * kRWarpFloats * sizeof(float);
+template <int TB, bool kRB> constexpr size_t r_smem() {
+  return (size_t)r_warps<TB, kRB>() * kRWarpFloats * sizeof(float);
+}
 
 __device__ __forceinline__ void cp16(float* sdst, const float* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
@@ -997,7 +1006,7 @@ __device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips,
 }
 
 template <int TB, bool kRB>
-__global__ void __launch_bounds__(kRWarps * 32)
+__global__ void __launch_bounds__(r_warps<TB, kRB>() * 32)
 relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
             int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
             unsigned long long* sched) {
@@ -1105,16 +1114,16 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   static int occ = 0;
   if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRSmem);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB>, kRWarps * 32,
-                                                      kRSmem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB>,
+                                                      r_warps<TB, kRB>() * 32, r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
   }
   const int nstrips = (f.nx + r_owned<TB>() - 1) / r_owned<TB>();
   const int64_t resident = (int64_t)occ * device_sm_count();
-  const int64_t warps = resident * kRWarps;
+  const int64_t warps = resident * r_warps<TB, kRB>();
   // Dynamic balance needs one range per warp at most and rows that fit the
   // range word; otherwise ranges are static (grid stride over tasks).
   const bool dyn = sched != nullptr && warps <= sched_cap && nstrips <= warps &&
@@ -1129,8 +1138,8 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   const int nseg = (int)((f.ny + H - 1) / H);
   const int64_t tasks = (int64_t)nstrips * nseg;
   const int blocks = (int)std::max<int64_t>(
-      1, std::min<int64_t>((tasks + kRWarps - 1) / kRWarps, resident));
-  relaxR2_f32<TB, kRB><<<blocks, kRWarps * 32, kRSmem, st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
+      1, std::min<int64_t>((tasks + r_warps<TB, kRB>() - 1) / r_warps<TB, kRB>(), resident));
+  relaxR2_f32<TB, kRB><<<blocks, r_warps<TB, kRB>() * 32, r_smem<TB, kRB>(), st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
                                                         nstrips, nseg, k, rep, dyn ? sched : nullptr);
   return cudaGetLastError();
 }
@@ -1189,10 +1198,19 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
   }
   if constexpr (sizeof(T) == 4) {
     const int fam = wave_kernel();
-    // the register wavefront needs many warps' worth of rows: from 2^24 cells
-    if (fam == 0 && (tb == 3 || tb == 4) && (int64_t)f.nx * f.ny >= ((int64_t)1 << 24))
-      return tb == 3 ? launch_reg2_t<3>(f, src, dst, rho, k, rep, sched, sched_cap, st)
-                     : launch_reg2_t<4>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    // the register wavefront needs many warps' worth of rows: from 2^23 cells
+    if (fam == 3 || (fam == 0 && tb >= 3 && (int64_t)f.nx * f.ny >= ((int64_t)1 << 23))) {
+      switch (tb) {
+        case 2: return launch_reg2_t<2>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 3: return launch_reg2_t<3>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 4: return launch_reg2_t<4>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 5: return launch_reg2_t<5>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 6: return launch_reg2_t<6>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 7: return launch_reg2_t<7>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        case 8: return launch_reg2_t<8>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
     if (fam == 2 || (fam == 0 && tb != 6 && tb != 7)) {
       switch (tb) {
         case 2: return launch_wave2_t<2>(f, src, dst, rho, k, rep, st);

@@ -49,7 +49,7 @@ def test_static_entry_point_matches_relax_n_two_calls_in_a_row(px):
     rng = np.random.default_rng(2024)
     cases = [
         # (nx, ny, dtype, nsweeps, tblock, in_place, every, tol per sweep)
-        (1024, 512, torch.float32, 9, 0, False, 1, 2e-6),   # depth 4: launches 4, 4, 1
+        (1024, 512, torch.float32, 9, 0, False, 1, 2e-6),   # automatic depth 8: launches 8, 1
         (300, 200, torch.float64, 5, 1, True, 2, 1e-12),    # in place, odd: staged copy
     ]
     for (nx, ny, dt, n, tb, inplace, every, tol) in cases:
