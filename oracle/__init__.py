@@ -14,7 +14,8 @@ Functions and the passages they follow:
   relax_omp        OpenMP fused sweeps, used only to time the CPU baseline
   apply_stencil    L phi = s / h^2
   residual_norm    ||rho - L phi||_inf and ||rho||_inf
-Refinement and CNN pieces live in oracle/refine.py and oracle/cnn.py.
+Refinement, CNN and multigrid pieces live in oracle/refine.py, oracle/cnn.py
+and oracle/mg.py.
 """
 from __future__ import annotations
 
