@@ -181,6 +181,40 @@ px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* ph
                      const void* rho, double omega, int nsweeps, double* resid_dev,
                      int report_every, void* stream);
 
+/* ncycles geometric multigrid V-cycles on phi, in place: the multigrid with a
+ * red-black SOR smoother that the paper builds on Proto's operators (Sec. VI,
+ * future work), as the textbook cell-centred V-cycle. On level l (cells of
+ * width 2^l h) one cycle is: nu1 red-black SOR sweeps (px_rbsor_n's sweep);
+ * r = rho_l - L phi_l; rho_{l+1} = mean of each 2 x 2 block of r; a cycle on
+ * level l+1 from e = 0; phi_l += bilinear interpolation of e between cell
+ * centres (weights 9/16, 3/16, 3/16, 1/16, periodic); nu2 sweeps. The
+ * coarsest level runs coarse_sweeps sweeps instead. Levels halve both extents
+ * while both halves stay even (a 2^k x 2^k grid goes down to 2 x 2), up to
+ * max_levels levels (0: no limit).
+ *
+ *  g              unghosted layout (PX_EUNSUPPORTED otherwise), nx and ny even
+ *                 (PX_EINVAL otherwise), FP64 or FP32; level 0 keeps g's pitch,
+ *                 coarser levels are contiguous.
+ *  phi            device field, read and overwritten (the cycle's state).
+ *  rho            device field, same layout; must not overlap phi. For the
+ *                 periodic problem it should have zero mean (the constant
+ *                 mode of phi is left free).
+ *  ncycles        >= 0. nu1, nu2 >= 0 smoothing sweeps per level.
+ *  omega          the smoother's relaxation factor (1: Gauss-Seidel).
+ *  coarse_sweeps  sweeps on the coarsest level; 0 picks 1 for a 2 x 2 level
+ *                 (solved exactly) and 2 n^2 otherwise (n its larger extent).
+ *  max_levels     >= 0; 0 = as many as the extents allow.
+ *  resid_dev      NULL, or ncycles + 1 device doubles: [k] = ||rho - L phi_k||
+ *                 (max-norm) of the state after k cycles. [k < ncycles] comes
+ *                 from the cycle's first kernel in the storage precision;
+ *                 [ncycles] is evaluated in FP64 on the final state.
+ * Working memory: the context's scratch field (phi's span) and one allocation
+ * of three fields per coarser level (a field's size in all), kept by the
+ * context; PX_ENOMEM when it cannot be had. Asynchronous. */
+px_status px_mg_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho, int ncycles,
+                      int nu1, int nu2, double omega, int coarse_sweeps, int max_levels,
+                      double* resid_dev, void* stream);
+
 /* The launch plan px_relax_n would use for these arguments, without running
  * it: *tblock_used = sweeps fused per launch (after auto choice and layout
  * fallback), *launches = relax kernel launches (excluding the zero-fill of

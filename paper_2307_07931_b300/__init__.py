@@ -79,6 +79,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_apply_stencil.argtypes = [_vp, gp, _vp, _vp, _vp]
     lib.px_relax_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
     lib.px_rbsor_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, _vp, i, _vp]
+    lib.px_mg_solve.argtypes = [_vp, gp, _vp, _vp, i, i, i, d, i, i, _vp, _vp]
     lib.px_residual_norm.argtypes = [_vp, gp, _vp, _vp, dp, dp, _vp]
     lib.px_residual_norm_async.argtypes = [_vp, gp, _vp, _vp, _vp, _vp]
     ip = ctypes.POINTER(ctypes.c_int)
@@ -112,6 +113,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
                              ctypes.POINTER(SolveInfo), _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n", "px_rbsor_n",
+                 "px_mg_solve",
                  "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
                  "px_relax_n_static", "px_solve", "px_batch_plan", "px_batch_run",
                  "px_batch_destroy"):
@@ -255,6 +257,27 @@ def rbsor_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, resid=No
                                         _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
                                         _ptr(resid), int(report_every), _stream(stream)))
     return phi_out
+
+
+def mg_solve(phi, rho, h: float, ncycles: int, nu1: int = 2, nu2: int = 2, omega: float = 1.0,
+             coarse_sweeps: int = 0, max_levels: int = 0, resid=None,
+             ctx: Context | None = None, stream=None):
+    """ncycles multigrid V-cycles on phi in place (px_mg_solve). `resid`, if
+    given, is a float64 CUDA tensor of ncycles + 1 entries: the residual
+    max-norm after 0, 1, ..., ncycles cycles."""
+    _same_layout(phi, rho)
+    ctx = ctx or context(phi.device.index)
+    g = grid_of(phi, h, 0)
+    if resid is not None:
+        import torch
+        if resid.dtype != torch.float64 or not resid.is_cuda or resid.numel() < ncycles + 1 \
+                or not resid.is_contiguous():
+            raise ValueError(f"resid must be a contiguous CUDA float64 tensor of >= {ncycles + 1}")
+    ctx.check(load_library().px_mg_solve(ctx.handle, ctypes.byref(g), _ptr(phi), _ptr(rho),
+                                         int(ncycles), int(nu1), int(nu2), float(omega),
+                                         int(coarse_sweeps), int(max_levels), _ptr(resid),
+                                         _stream(stream)))
+    return phi
 
 
 def relax_n_static(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int,

@@ -235,6 +235,7 @@ px_status px_destroy(px_ctx* c) {
   if (c->red) cudaFree(c->red);
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->sched) cudaFree(c->sched);
+  if (c->mg) cudaFree(c->mg);
   delete c;
   return PX_OK;
 }
@@ -420,6 +421,156 @@ px_status px_rbsor_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
   if (src != phi_out) {
     cudaError_t e = px::launch_copy_field(f, src, phi_out, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "copy launch");
+  }
+  return PX_OK;
+}
+
+namespace {
+
+// n red-black sweeps alternating between the buffers a and b, from *cur (one
+// of them); *cur ends on the buffer that holds the result. With slot, the
+// residual of the first sweep's input state is folded into *slot.
+cudaError_t rb_sweeps_ab(px_ctx* c, const px::FieldDesc& f, void* a, void* b, void** cur,
+                         const void* rho, double omega, int n, double* slot, cudaStream_t st) {
+  const bool vec = px::vector_ok(f, a, b, rho);
+  const bool reg = f.dtype == 1 && vec;
+  const int D = reg ? rb_sweeps() : 1;
+  for (int done = 0; done < n;) {
+    const int k = std::min(D, n - done);
+    void* src = *cur;
+    void* dst = src == a ? b : a;
+    double* s = done == 0 ? slot : nullptr;
+    cudaError_t e;
+    if (reg) {
+      e = px::launch_rbsor_reg(f, (const float*)src, (float*)dst, (const float*)rho, omega, k, s,
+                               0, n, c->sched, c->sched_cap, st);
+    } else {
+      e = px::launch_rbsor_pass(f, src, dst, rho, omega, true, vec, s, st);
+      if (e == cudaSuccess) e = px::launch_rbsor_pass(f, dst, dst, rho, omega, false, vec, nullptr, st);
+    }
+    if (e != cudaSuccess) return e;
+    *cur = dst;
+    done += k;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, int ncycles,
+                      int nu1, int nu2, double omega, int coarse_sweeps, int max_levels,
+                      double* resid_dev, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::FieldDesc f;
+  px_status s = check_grid(c, g, &f);
+  if (s != PX_OK) return s;
+  if (f.ghost) return fail(c, PX_EUNSUPPORTED, "multigrid takes unghosted layouts");
+  if (f.nx % 2 || f.ny % 2)
+    return fail(c, PX_EINVAL, "multigrid needs even nx and ny (got %d x %d)", f.nx, f.ny);
+  if (ncycles < 0 || nu1 < 0 || nu2 < 0 || coarse_sweeps < 0 || max_levels < 0)
+    return fail(c, PX_EINVAL, "negative ncycles, nu1, nu2, coarse_sweeps or max_levels");
+  if (!std::isfinite(omega)) return fail(c, PX_EINVAL, "omega must be finite");
+  const bool empty = f.nx == 0 || f.ny == 0;
+  const size_t span = field_span(f);
+  const size_t nrep = resid_dev ? (size_t)ncycles + 1 : 0;
+  if (!empty) {
+    if (!phi || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
+    if (overlap(rho, phi, span)) return fail(c, PX_EINVAL, "rho overlaps phi");
+    if (resid_dev && overlap2(resid_dev, sizeof(double) * nrep, phi, span))
+      return fail(c, PX_EINVAL, "resid_dev overlaps phi");
+  }
+  // levels: halve both extents while both halves stay even
+  std::vector<px::FieldDesc> lv(1, f);
+  while (!empty && lv.back().nx % 4 == 0 && lv.back().ny % 4 == 0 &&
+         (max_levels == 0 || (int)lv.size() < max_levels)) {
+    px::FieldDesc q = lv.back();
+    q.nx /= 2;
+    q.ny /= 2;
+    q.ld = q.nx;
+    q.off = 0;
+    q.h *= 2.0;
+    lv.push_back(q);
+  }
+  const int L = (int)lv.size();
+  const int nc = std::max(lv.back().nx, lv.back().ny);
+  const int cs = coarse_sweeps > 0 ? coarse_sweeps : (nc <= 2 ? 1 : 2 * nc * nc);
+  DeviceScope ds(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (resid_dev) {
+    cudaError_t e = cudaMemsetAsync(resid_dev, 0, sizeof(double) * nrep, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear resid_dev");
+  }
+  if (empty) return PX_OK;
+  // buffers: level 0 is phi, the context scratch and rho; every coarser level
+  // has its right-hand side r and two states, 256-byte aligned
+  s = ensure_scratch(c, span);
+  if (s != PX_OK) return s;
+  const size_t es = f.dtype == 0 ? 8 : 4;
+  auto level_bytes = [&](int l) {
+    return ((size_t)lv[l].nx * lv[l].ny * es + 255) & ~(size_t)255;
+  };
+  size_t total = 0;
+  for (int l = 1; l < L; ++l) total += 3 * level_bytes(l);
+  if (total > c->mg_bytes) {
+    if (c->mg) cudaFree(c->mg);
+    c->mg = nullptr;
+    c->mg_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->mg, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, PX_ENOMEM, "multigrid levels of %zu bytes: %s", total, cudaGetErrorString(e));
+    }
+    c->mg_bytes = total;
+  }
+  std::vector<void*> A(L), B(L), R(L), cur(L);
+  A[0] = phi;
+  B[0] = c->scratch;
+  R[0] = const_cast<void*>(rho);
+  char* base = (char*)c->mg;
+  for (int l = 1; l < L; ++l) {
+    const size_t one = level_bytes(l);
+    R[l] = base;
+    A[l] = base + one;
+    B[l] = base + 2 * one;
+    base += 3 * one;
+  }
+  auto chk = [&](cudaError_t e) -> px_status {
+    return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "multigrid launch");
+  };
+  for (int k = 0; k < ncycles; ++k) {
+    double* rep = resid_dev ? resid_dev + k : nullptr;  // residual of the cycle's input
+    cur[0] = phi;
+    for (int l = 0; l + 1 < L; ++l) {
+      double* pre = l == 0 && nu1 > 0 ? rep : nullptr;
+      s = chk(rb_sweeps_ab(c, lv[l], A[l], B[l], &cur[l], R[l], omega, nu1, pre, st));
+      if (s != PX_OK) return s;
+      double* rr = l == 0 && nu1 == 0 ? rep : nullptr;
+      s = chk(px::launch_mg_restrict(lv[l], cur[l], R[l], R[l + 1], A[l + 1], lv[l + 1].ld, rr,
+                                     st));
+      if (s != PX_OK) return s;
+      cur[l + 1] = A[l + 1];
+    }
+    s = chk(rb_sweeps_ab(c, lv[L - 1], A[L - 1], B[L - 1], &cur[L - 1], R[L - 1], omega, cs,
+                         L == 1 ? rep : nullptr, st));
+    if (s != PX_OK) return s;
+    for (int l = L - 2; l >= 0; --l) {
+      s = chk(px::launch_mg_prolong(lv[l], cur[l + 1], lv[l + 1].ld, cur[l], st));
+      if (s != PX_OK) return s;
+      s = chk(rb_sweeps_ab(c, lv[l], A[l], B[l], &cur[l], R[l], omega, nu2, nullptr, st));
+      if (s != PX_OK) return s;
+    }
+    if (cur[0] != phi) {
+      s = chk(px::launch_copy_field(f, cur[0], phi, st));
+      if (s != PX_OK) return s;
+    }
+  }
+  if (resid_dev) {
+    s = chk(px::launch_residual_norm(f, phi, rho, c->red, st));
+    if (s != PX_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(resid_dev + ncycles, c->red, sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy final residual");
   }
   return PX_OK;
 }

@@ -106,6 +106,16 @@ cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, c
                              double omega, int sweeps, double* resid, int s0, int every,
                              unsigned long long* sched, int sched_cap, cudaStream_t st);
 
+// Multigrid transfers (mg.cu). launch_mg_restrict: for the fine field f
+// (phi, rho), writes the block means of r = rho - L phi to rc and zeros to ec
+// (coarse row pitch ldc); folds max |r| into *slot when slot is not NULL.
+// launch_mg_prolong: adds the bilinear interpolation of the coarse e (pitch
+// ldc) to the fine phi described by f. Both need even nx and ny.
+cudaError_t launch_mg_restrict(const FieldDesc& f, const void* phi, const void* rho, void* rc,
+                               void* ec, int64_t ldc, double* slot, cudaStream_t st);
+cudaError_t launch_mg_prolong(const FieldDesc& f, const void* e, int64_t ldc, void* phi,
+                              cudaStream_t st);
+
 cudaError_t launch_rbsor_pass(const FieldDesc& f, const void* src, void* dst, const void* rho,
                               double omega, bool red_pass, bool vec, double* slot,
                               cudaStream_t st);
@@ -150,6 +160,8 @@ struct px_ctx {
   size_t ws_bytes = 0;
   unsigned long long* sched = nullptr;  // load-balance words of the relax kernels
   int sched_cap = 0;
+  void* mg = nullptr;        // multigrid levels 1..L-1: right-hand side and two states each
+  size_t mg_bytes = 0;
   std::string err;
 };
 
