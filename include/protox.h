@@ -205,9 +205,10 @@ px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* ph
  *                 (solved exactly) and 2 n^2 otherwise (n its larger extent).
  *  max_levels     >= 0; 0 = as many as the extents allow.
  *  resid_dev      NULL, or ncycles + 1 device doubles: [k] = ||rho - L phi_k||
- *                 (max-norm) of the state after k cycles. [k < ncycles] comes
- *                 from the cycle's first kernel in the storage precision;
- *                 [ncycles] is evaluated in FP64 on the final state.
+ *                 (max-norm) of the state after k cycles, evaluated in the
+ *                 storage precision (FMA form): [k < ncycles] by the cycle's
+ *                 first kernel, [ncycles] by a residual pass over the final
+ *                 state (in FP64 when the grid has a single level).
  * Working memory: the context's scratch field (phi's span) and one allocation
  * of three fields per coarser level (a field's size in all), kept by the
  * context; PX_ENOMEM when it cannot be had. Asynchronous. */

@@ -566,11 +566,19 @@ px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, i
     }
   }
   if (resid_dev) {
-    s = chk(px::launch_residual_norm(f, phi, rho, c->red, st));
-    if (s != PX_OK) return s;
-    cudaError_t e = cudaMemcpyAsync(resid_dev + ncycles, c->red, sizeof(double),
-                                    cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy final residual");
+    // the final state's residual in the storage precision: the residual and
+    // restriction pass (its coarse outputs land in level-1 buffers that no
+    // one reads), or, on a single level, the FP64 residual pass
+    if (L >= 2) {
+      s = chk(px::launch_mg_restrict(f, phi, rho, R[1], A[1], lv[1].ld, resid_dev + ncycles, st));
+      if (s != PX_OK) return s;
+    } else {
+      s = chk(px::launch_residual_norm(f, phi, rho, c->red, st));
+      if (s != PX_OK) return s;
+      cudaError_t e = cudaMemcpyAsync(resid_dev + ncycles, c->red, sizeof(double),
+                                      cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copy final residual");
+    }
   }
   return PX_OK;
 }

@@ -47,24 +47,27 @@ __global__ void apply_stencil_k(const T* __restrict__ phi, T* __restrict__ out, 
   }
 }
 
+// A thread owns one column and strides over rows (gridDim.y), so no cell
+// index needs a division; the arithmetic is the oracle's FP64 order.
 template <typename T>
 __global__ void residual_norm_k(const T* __restrict__ phi, const T* __restrict__ rho, int nx,
                                 int ny, int64_t ld, double ih2, double* __restrict__ out2) {
-  const int64_t n = (int64_t)nx * ny;
   uint64_t mr = 0, mp = 0;
-  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(c / nx), i = (int)(c - (int64_t)j * nx);
-    const T* row = phi + (int64_t)j * ld;
-    const double C = (double)row[i];
-    const double W = (double)row[wrap1(i - 1, nx)], E = (double)row[wrap1(i + 1, nx)];
-    const double S = (double)phi[(int64_t)wrap1(j - 1, ny) * ld + i];
-    const double N = (double)phi[(int64_t)wrap1(j + 1, ny) * ld + i];
-    const double s = __dsub_rn(__dadd_rn(__dadd_rn(W, E), __dadd_rn(S, N)), __dmul_rn(4.0, C));
-    const double rv = (double)rho[(int64_t)j * ld + i];
-    const double r = __dsub_rn(__dmul_rn(ih2, s), rv);
-    mr = umax(mr, absbits(r));
-    mp = umax(mp, absbits(rv));
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nx) {
+    const int iw = i == 0 ? nx - 1 : i - 1, ie = i + 1 == nx ? 0 : i + 1;
+    for (int j = blockIdx.y; j < ny; j += gridDim.y) {
+      const T* row = phi + (int64_t)j * ld;
+      const double C = (double)row[i];
+      const double W = (double)row[iw], E = (double)row[ie];
+      const double S = (double)phi[(int64_t)(j == 0 ? ny - 1 : j - 1) * ld + i];
+      const double N = (double)phi[(int64_t)(j + 1 == ny ? 0 : j + 1) * ld + i];
+      const double s = __dsub_rn(__dadd_rn(__dadd_rn(W, E), __dadd_rn(S, N)), __dmul_rn(4.0, C));
+      const double rv = (double)rho[(int64_t)j * ld + i];
+      const double r = __dsub_rn(__dmul_rn(ih2, s), rv);
+      mr = umax(mr, absbits(r));
+      mp = umax(mp, absbits(rv));
+    }
   }
   __shared__ uint64_t sm[2][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,9 +124,11 @@ cudaError_t launch_residual_norm(const FieldDesc& f, const void* phi, const void
                                  double* out2, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  const int64_t n = (int64_t)f.nx * f.ny;
-  if (n == 0) return cudaSuccess;
-  const int blocks = grid_for(n, 256);
+  if (f.nx == 0 || f.ny == 0) return cudaSuccess;
+  const int bx = (f.nx + 255) / 256;
+  const int by = (int)std::max<int64_t>(
+      1, std::min<int64_t>({(int64_t)f.ny, 65535, (int64_t)device_sm_count() * 8 / bx}));
+  const dim3 blocks(bx, by);
   const double ih2 = 1.0 / (f.h * f.h);
   if (f.dtype == 0)
     residual_norm_k<double><<<blocks, 256, 0, st>>>((const double*)phi + f.off,
