@@ -14,6 +14,8 @@ Functions and the passages they follow:
   relax_omp        OpenMP fused sweeps, used only to time the CPU baseline
   apply_stencil    L phi = s / h^2
   residual_norm    ||rho - L phi||_inf and ||rho||_inf
+  sweep3, relax3_n the fused sweep in 3D (7-point Laplacian, Eq. "jacobi"
+                   with D = 3: weight omega h^2 / 6)
 Refinement, CNN and multigrid pieces live in oracle/refine.py, oracle/cnn.py
 and oracle/mg.py.
 """
@@ -62,6 +64,10 @@ def bind(lib):
         lib.oracle_relax_ghosted.restype = i
         lib.oracle_relax_n_omp.argtypes = [i, i, d, d, _dp, _dp, _dp, i, i, _dp]
         lib.oracle_relax_n_omp.restype = i
+        lib.oracle_sweep3.argtypes = [i, i, i, d, d, _dp, _dp, _dp]
+        lib.oracle_sweep3.restype = d
+        lib.oracle_relax3_n.argtypes = [i, i, i, d, d, _dp, _dp, i, i, _dp, _dp]
+        lib.oracle_relax3_n.restype = i
     return lib
 
 
@@ -152,6 +158,38 @@ def rbsor_n(phi0, rho, h: float, omega: float, nsweeps: int, every: int = 0
                                 _ptr(out), _ptr(rep))
     if rc != 0:
         raise MemoryError("oracle_rbsor_n: allocation failed")
+    return out, rep[:report_count(nsweeps, every)]
+
+
+def _shape3(a: np.ndarray) -> tuple[int, int, int]:
+    if a.ndim != 3:
+        raise ValueError("3D fields are (nz, ny, nx) arrays")
+    nz, ny, nx = a.shape
+    return nx, ny, nz
+
+
+def sweep3(phi, rho, h: float, omega: float) -> tuple[np.ndarray, float]:
+    """One fused 3D sweep (7-point Laplacian, Jacobi weight omega h^2 / 6):
+    (phi', R) with R the residual max-norm of the input phi."""
+    phi, rho = _f64(phi), _f64(rho)
+    nx, ny, nz = _shape3(phi)
+    out = np.empty_like(phi)
+    R = _load().oracle_sweep3(nx, ny, nz, h, omega, _ptr(phi), _ptr(rho), _ptr(out))
+    return out, R
+
+
+def relax3_n(phi0, rho, h: float, omega: float, nsweeps: int, every: int = 0
+             ) -> tuple[np.ndarray, np.ndarray]:
+    """nsweeps fused 3D sweeps from phi0 (nz, ny, nx); returns (phi^n, reports)
+    with reports[k] = ||rho - L phi^(k*every)||_inf."""
+    phi0, rho = _f64(phi0), _f64(rho)
+    nx, ny, nz = _shape3(phi0)
+    out = np.empty_like(phi0)
+    rep = np.zeros(max(1, report_count(nsweeps, every)), dtype=np.float64)
+    rc = _load().oracle_relax3_n(nx, ny, nz, h, omega, _ptr(phi0), _ptr(rho), nsweeps, every,
+                                 _ptr(out), _ptr(rep))
+    if rc != 0:
+        raise MemoryError("oracle_relax3_n: allocation failed")
     return out, rep[:report_count(nsweeps, every)]
 
 

@@ -293,3 +293,61 @@ int oracle_rbsor_n(int nx, int ny, double h, double omega, const double* phi0,
   free(a);
   return 0;
 }
+
+/* ---------------------------------------------------------------------------
+ * 3D periodic Poisson, 7-point stencil (the paper's Eq. "jacobi" in D = 3
+ * dimensions: lambda = h^2 / (4 D) is the omega = 1/2 case of the weight
+ * omega h^2 / (2 D) = omega h^2 / 6). Arrays are contiguous [z][y][x].
+ * Unscaled tap sum s = ((W + E) + (S + N)) + (B + T) - 6 C. */
+static double taps3(int nx, int ny, int nz, const double* p, int i, int j, int k) {
+  int64_t pl = (int64_t)nx * ny;
+  int64_t im = wrapi(i - 1, nx), ip = wrapi(i + 1, nx);
+  int64_t jm = wrapi(j - 1, ny), jp = wrapi(j + 1, ny);
+  int64_t km = wrapi(k - 1, nz), kp = wrapi(k + 1, nz);
+  int64_t row = (int64_t)k * pl + (int64_t)j * nx;
+  double pC = p[row + i];
+  double pW = p[row + im], pE = p[row + ip];
+  double pS = p[(int64_t)k * pl + jm * nx + i], pN = p[(int64_t)k * pl + jp * nx + i];
+  double pB = p[km * pl + (int64_t)j * nx + i], pT = p[kp * pl + (int64_t)j * nx + i];
+  return (((pW + pE) + (pS + pN)) + (pB + pT)) - 6.0 * pC;
+}
+
+/* One fused 3D sweep: phinew = (C + w s) - lam rho with w = omega / 6,
+ * lam = omega h^2 / 6; returns ||s/h^2 - rho||_inf of the input state. */
+double oracle_sweep3(int nx, int ny, int nz, double h, double omega, const double* phi,
+                     const double* rho, double* phinew) {
+  double ih2 = 1.0 / (h * h);
+  double w = omega / 6.0, lam = omega * h * h / 6.0;
+  double R = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        int64_t c = ((int64_t)k * ny + j) * nx + i;
+        double s = taps3(nx, ny, nz, phi, i, j, k);
+        double rv = rho[c];
+        phinew[c] = (phi[c] + w * s) - lam * rv;
+        double r = fabs(ih2 * s - rv);
+        R = maxnan(R, r);
+      }
+  return R;
+}
+
+/* n fused 3D sweeps from phi0 into phi_out; reports as oracle_relax_n.
+ * Returns 0, or -1 on allocation failure. */
+int oracle_relax3_n(int nx, int ny, int nz, double h, double omega, const double* phi0,
+                    const double* rho, int nsweeps, int every, double* phi_out,
+                    double* resid) {
+  size_t n = (size_t)nx * (size_t)ny * (size_t)nz;
+  double* a = (double*)malloc(n * sizeof(double));
+  double* b = (double*)malloc(n * sizeof(double));
+  if (!a || !b) { free(a); free(b); return -1; }
+  memcpy(a, phi0, n * sizeof(double));
+  for (int s = 0; s < nsweeps; ++s) {
+    double R = oracle_sweep3(nx, ny, nz, h, omega, a, rho, b);
+    if (resid && every > 0 && s % every == 0) resid[s / every] = R;
+    double* t = a; a = b; b = t;
+  }
+  memcpy(phi_out, a, n * sizeof(double));
+  free(a); free(b);
+  return 0;
+}
