@@ -78,6 +78,16 @@ typedef struct {
   double h;        /* mesh spacing, finite and > 0 */
 } px_grid;
 
+/* Layout of a 3D periodic field (px_relax3_n): nz planes of ny rows of nx
+ * cells, x fastest, no ghost cells. */
+typedef struct {
+  int32_t nx, ny, nz;  /* cells along x, y, z; >= 0 (a zero extent: empty, no-op) */
+  int64_t ld;          /* elements between row starts; >= nx */
+  int64_t lp;          /* elements between plane starts; >= (ny - 1) * ld + nx */
+  int32_t dtype;       /* px_dtype of every field of the call */
+  double h;            /* mesh spacing, finite and > 0 */
+} px_grid3;
+
 typedef struct px_ctx px_ctx;
 
 /* Create a context on CUDA device `device`. *out is NULL on failure. */
@@ -215,6 +225,26 @@ px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* ph
 px_status px_mg_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho, int ncycles,
                       int nu1, int nu2, double omega, int coarse_sweeps, int max_levels,
                       double* resid_dev, void* stream);
+
+/* nsweeps fused sweeps of the 3D periodic Poisson problem, phi_in -> phi_out:
+ * Eq. "jacobi" in D = 3 dimensions. Per cell, the 7-point Laplacian
+ * L phi = (W + E + S + N + B + T - 6 C) / h^2 of the periodic neighbours, the
+ * update phi' = phi + (omega h^2 / 6)(L phi - rho) (the paper's
+ * lambda = h^2 / (4 D) = h^2 / 12 is omega = 1/2; 0 < omega <= 1 converges on
+ * the mean-zero problem), and the residual max-norm of the input state, in one
+ * pass per sweep.
+ *
+ *  g            px_grid3 layout, FP64 or FP32.
+ *  phi_in, phi_out, rho, omega, nsweeps, resid_dev, report_every, stream
+ *               as in px_relax_n (resid_dev[k] is the residual of the input
+ *               state of sweep k * report_every); phi_in == phi_out runs in
+ *               place through the context's scratch field.
+ * 16-byte vectors when nx, ld and lp are multiples of 16 / element size and
+ * the three pointers are 16-byte aligned; a scalar path otherwise.
+ * Asynchronous. */
+px_status px_relax3_n(px_ctx* ctx, const px_grid3* g, const void* phi_in, void* phi_out,
+                      const void* rho, double omega, int nsweeps, double* resid_dev,
+                      int report_every, void* stream);
 
 /* The launch plan px_relax_n would use for these arguments, without running
  * it: *tblock_used = sweeps fused per launch (after auto choice and layout

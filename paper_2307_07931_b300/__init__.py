@@ -52,6 +52,12 @@ class Grid(ctypes.Structure):
                 ("ghost", ctypes.c_int32), ("dtype", ctypes.c_int32), ("h", ctypes.c_double)]
 
 
+class Grid3(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("ld", ctypes.c_int64), ("lp", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("h", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 
@@ -80,6 +86,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_relax_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, i, _vp, i, _vp]
     lib.px_rbsor_n.argtypes = [_vp, gp, _vp, _vp, _vp, d, i, _vp, i, _vp]
     lib.px_mg_solve.argtypes = [_vp, gp, _vp, _vp, i, i, i, d, i, i, _vp, _vp]
+    lib.px_relax3_n.argtypes = [_vp, ctypes.POINTER(Grid3), _vp, _vp, _vp, d, i, _vp, i, _vp]
     lib.px_residual_norm.argtypes = [_vp, gp, _vp, _vp, dp, dp, _vp]
     lib.px_residual_norm_async.argtypes = [_vp, gp, _vp, _vp, _vp, _vp]
     ip = ctypes.POINTER(ctypes.c_int)
@@ -113,7 +120,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_solve.argtypes = [_vp, gp, _vp, _vp, ctypes.POINTER(SolveOpts),
                              ctypes.POINTER(SolveInfo), _vp]
     for name in ("px_create", "px_destroy", "px_apply_stencil", "px_relax_n", "px_rbsor_n",
-                 "px_mg_solve",
+                 "px_mg_solve", "px_relax3_n",
                  "px_residual_norm", "px_residual_norm_async", "px_relax_plan",
                  "px_relax_n_static", "px_solve", "px_batch_plan", "px_batch_run",
                  "px_batch_destroy"):
@@ -278,6 +285,46 @@ def mg_solve(phi, rho, h: float, ncycles: int, nu1: int = 2, nu2: int = 2, omega
                                          int(coarse_sweeps), int(max_levels), _ptr(resid),
                                          _stream(stream)))
     return phi
+
+
+def grid3_of(t, h: float) -> Grid3:
+    """px_grid3 describing a 3D tensor t of shape (nz, ny, nx)."""
+    import torch
+    if t.dim() != 3:
+        raise ValueError("3D fields are tensors (nz, ny, nx)")
+    if t.stride(2) != 1:
+        raise ValueError("fields need unit stride along x")
+    if t.dtype == torch.float64:
+        dt = PX_F64
+    elif t.dtype == torch.float32:
+        dt = PX_F32
+    else:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    nz, ny, nx = t.shape
+    ld = t.stride(1) if ny > 1 else nx
+    lp = t.stride(0) if nz > 1 else max(ny - 1, 0) * ld + nx
+    return Grid3(nx, ny, nz, ld, lp, dt, float(h))
+
+
+def relax3_n(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int, resid=None,
+             report_every: int = 0, ctx: Context | None = None, stream=None):
+    """nsweeps fused 3D sweeps phi_in -> phi_out (px_relax3_n); tensors of
+    shape (nz, ny, nx). `resid`, if given, is a float64 CUDA tensor of
+    ceil(nsweeps / report_every) entries."""
+    _same_layout(phi_in, phi_out)
+    _same_layout(phi_in, rho)
+    ctx = ctx or context(phi_in.device.index)
+    g = grid3_of(phi_in, h)
+    if resid is not None:
+        import torch
+        need = (nsweeps + report_every - 1) // report_every if report_every > 0 else 0
+        if resid.dtype != torch.float64 or not resid.is_cuda or resid.numel() < need \
+                or not resid.is_contiguous():
+            raise ValueError(f"resid must be a contiguous CUDA float64 tensor of >= {need}")
+    ctx.check(load_library().px_relax3_n(ctx.handle, ctypes.byref(g), _ptr(phi_in),
+                                         _ptr(phi_out), _ptr(rho), float(omega), int(nsweeps),
+                                         _ptr(resid), int(report_every), _stream(stream)))
+    return phi_out
 
 
 def relax_n_static(phi_in, phi_out, rho, h: float, omega: float, nsweeps: int,

@@ -583,6 +583,80 @@ px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, i
   return PX_OK;
 }
 
+px_status px_relax3_n(px_ctx* c, const px_grid3* g, const void* phi_in, void* phi_out,
+                      const void* rho, double omega, int nsweeps, double* resid_dev,
+                      int report_every, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  if (!g) return fail(c, PX_EINVAL, "grid is NULL");
+  if (g->dtype != PX_F64 && g->dtype != PX_F32)
+    return fail(c, PX_EINVAL, "dtype %d is not PX_F64 or PX_F32", (int)g->dtype);
+  if (g->nx < 0 || g->ny < 0 || g->nz < 0)
+    return fail(c, PX_EINVAL, "negative extent %d x %d x %d", g->nx, g->ny, g->nz);
+  if (g->nx > (1 << 29) || g->ny > (1 << 22) || g->nz > (1 << 22))
+    return fail(c, PX_EINVAL, "extent %d x %d x %d too large", g->nx, g->ny, g->nz);
+  if (g->ld < g->nx) return fail(c, PX_EINVAL, "ld %lld < nx", (long long)g->ld);
+  if (g->ny > 0 && g->lp < (int64_t)(g->ny - 1) * g->ld + g->nx)
+    return fail(c, PX_EINVAL, "lp %lld < (ny - 1) * ld + nx", (long long)g->lp);
+  if (!(std::isfinite(g->h) && g->h > 0.0) || !std::isfinite(1.0 / (g->h * g->h)))
+    return fail(c, PX_EINVAL, "h must be finite and > 0 with a finite 1/h^2");
+  if (nsweeps < 0 || report_every < 0) return fail(c, PX_EINVAL, "negative nsweeps or report_every");
+  if (!std::isfinite(omega)) return fail(c, PX_EINVAL, "omega must be finite");
+  px::Field3 f{g->nx, g->ny, g->nz, g->ld, g->lp, g->dtype, g->h};
+  const bool empty = f.nx == 0 || f.ny == 0 || f.nz == 0;
+  const size_t es = elem_size(g->dtype);
+  const double spand = empty ? 0.0 : ((double)(f.nz - 1) * f.lp + (double)(f.ny - 1) * f.ld + f.nx) * es;
+  if (spand > 9.0e18) return fail(c, PX_EINVAL, "field too large");
+  const size_t span = (size_t)spand;
+  const bool reports = resid_dev && report_every > 0 && nsweeps > 0;
+  const int nrep = reports ? (nsweeps + report_every - 1) / report_every : 0;
+  const bool inplace = phi_in == phi_out;
+  if (!empty) {
+    if (!phi_in || !phi_out || !rho) return fail(c, PX_EINVAL, "NULL field pointer");
+    if (!inplace && overlap(phi_in, phi_out, span))
+      return fail(c, PX_EINVAL, "phi_in and phi_out overlap without being equal");
+    if (overlap(rho, phi_out, span)) return fail(c, PX_EINVAL, "rho overlaps phi_out");
+    if (reports && overlap2(resid_dev, sizeof(double) * (size_t)nrep, phi_out, span))
+      return fail(c, PX_EINVAL, "resid_dev overlaps phi_out");
+  }
+  DeviceScope ds(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (reports) {
+    cudaError_t e = cudaMemsetAsync(resid_dev, 0, sizeof(double) * (size_t)nrep, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear resid_dev");
+  }
+  if (empty) return PX_OK;
+  if (nsweeps == 0) {
+    if (inplace) return PX_OK;
+    cudaError_t e = px::launch_copy3(f, phi_in, phi_out, st);
+    return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "copy launch");
+  }
+  // sweeps alternate between phi_out and scratch: out of place so that the
+  // last lands in phi_out, in place starting with scratch (an odd count ends
+  // with a copy back)
+  if (inplace || nsweeps >= 2) {
+    px_status s = ensure_scratch(c, span);
+    if (s != PX_OK) return s;
+  }
+  void* scratch = c->scratch;
+  const bool vec = px::vector_ok3(f, phi_in, phi_out, rho) &&
+                   (!scratch || px::vector_ok3(f, scratch, scratch, scratch));
+  const void* src = phi_in;
+  for (int k = 0; k < nsweeps; ++k) {
+    void* dst = inplace ? (k % 2 == 0 ? scratch : phi_out)
+                        : ((nsweeps - 1 - k) % 2 == 0 ? phi_out : scratch);
+    double* slot = reports && k % report_every == 0 ? resid_dev + k / report_every : nullptr;
+    cudaError_t e = px::launch_relax3(f, src, dst, rho, omega, vec, slot, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "3D relax launch");
+    src = dst;
+  }
+  if (src != phi_out) {
+    cudaError_t e = px::launch_copy3(f, src, phi_out, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy launch");
+  }
+  return PX_OK;
+}
+
 px_status px_relax_plan(px_ctx* c, const px_grid* g, const void* phi_in,
                         const void* phi_out, const void* rho, int nsweeps, int tblock,
                         int* tblock_used, int* launches) {

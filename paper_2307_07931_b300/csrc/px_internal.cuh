@@ -106,6 +106,21 @@ cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, c
                              double omega, int sweeps, double* resid, int s0, int every,
                              unsigned long long* sched, int sched_cap, cudaStream_t st);
 
+// 3D fields (relax3.cu): unghosted, contiguous x, pitches ld (rows) and lp
+// (planes) in elements.
+struct Field3 {
+  int nx, ny, nz;
+  int64_t ld, lp;
+  int dtype;  // 0 = f64, 1 = f32
+  double h;
+};
+bool vector_ok3(const Field3& f, const void* a, const void* b, const void* c);
+// One fused 3D sweep src -> dst (src != dst); folds the input state's
+// residual max-norm into *slot when slot is not NULL.
+cudaError_t launch_relax3(const Field3& f, const void* src, void* dst, const void* rho,
+                          double omega, bool vec, double* slot, cudaStream_t st);
+cudaError_t launch_copy3(const Field3& f, const void* src, void* dst, cudaStream_t st);
+
 // Multigrid transfers (mg.cu). launch_mg_restrict: for the fine field f
 // (phi, rho), writes the block means of r = rho - L phi to rc and zeros to ec
 // (coarse row pitch ldc); folds max |r| into *slot when slot is not NULL.

@@ -13,7 +13,7 @@ Arrays are returned with shape (ny, nx).
 The default seed of workload c is 20230717 + c, with c the workload index:
 0 = 64x64 8-mode field, 1 = 16384x16384 64-mode field plus noise,
 2 = 8192x8192 refinement field, 3 = 1024 uneven batched instances,
-4 = 256x256 learned-guess fields.
+4 = 256x256 learned-guess fields, 5 = 512^3 3D field.
 """
 from __future__ import annotations
 
@@ -166,3 +166,32 @@ def random_field(rng: np.random.Generator, nx: int, ny: int,
     """Uniform(-1, 1) white field (tests only)."""
     a = rng.uniform(-1.0, 1.0, size=(ny, nx))
     return remove_mean(a) if zero_mean else a
+
+
+def field3_rho(n: int = 512, nmodes: int = 8, kmax: int = 64, noise_sigma: float = 0.1,
+               seed: int | None = None) -> np.ndarray:
+    """The 3D workload's right-hand side on an n^3 periodic grid (shape
+    (n, n, n), z slowest): nmodes seeded plane waves cos(2 pi (k x + l y + m z)
+    + phase) with integer wavenumbers in [-kmax, kmax] (not all zero) and
+    N(0, 1) amplitudes, plus N(0, noise_sigma^2) white noise, mean-zeroed.
+    Workload index 5."""
+    rng = np.random.Generator(np.random.PCG64(workload_seed(5) if seed is None else seed))
+    t = 2 * np.pi * (np.arange(n) + 0.5) / n
+    rho = np.zeros((n, n, n), dtype=np.float64)
+    for _ in range(nmodes):
+        k, l, m = (int(v) for v in rng.integers(-kmax, kmax + 1, 3))
+        if k == 0 and l == 0 and m == 0:
+            k = 1
+        a, ph = float(rng.normal()), float(rng.uniform(0, 2 * np.pi))
+        ex, ey, ez = np.exp(1j * k * t), np.exp(1j * l * t), np.exp(1j * (m * t + ph))
+        rho += a * np.real(ez[:, None, None] * (ey[:, None] * ex[None, :])[None, :, :])
+    if noise_sigma > 0:
+        rho += noise_sigma * rng.standard_normal((n, n, n))
+    return rho - rho.mean()
+
+
+def random_field3(rng: np.random.Generator, nx: int, ny: int, nz: int,
+                  zero_mean: bool = True) -> np.ndarray:
+    """Uniform(-1, 1) white 3D field of shape (nz, ny, nx) (tests only)."""
+    a = rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
+    return a - a.mean() if zero_mean else a
