@@ -187,11 +187,18 @@ cudaError_t launch3_t(const Field3& f, const T* src, T* dst, const T* rho, doubl
   k.ih2 = (T)(1.0 / (f.h * f.h));
   const int64_t bx = (f.nx + TX - 1) / TX, by = (f.ny + kTY - 1) / kTY;
   if (by > 65535) return cudaErrorInvalidConfiguration;
-  // planes split into segments so that the tiles fill the resident CTA slots
-  // (a segment restarts the plane ring: two extra planes of reads)
+  // planes split into segments: minimise (waves of CTAs) x (planes per CTA +
+  // the ring's two-plane restart), so that the tiles fill the resident slots
   const int64_t resident = (int64_t)occ[ri] * device_sm_count();
-  const int64_t segs = std::max<int64_t>(1, std::min<int64_t>(f.nz, resident / (bx * by)));
-  const int seg = (int)((f.nz + segs - 1) / segs);
+  const int64_t tiles = bx * by;
+  int seg = f.nz;
+  double best = 1e300;
+  for (int64_t segs = 1; segs <= std::min<int64_t>(f.nz, 64); ++segs) {
+    const int sl = (int)((f.nz + segs - 1) / segs);
+    const int64_t ctas = tiles * ((f.nz + sl - 1) / sl);
+    const double cost = (double)((ctas + resident - 1) / resident) * (sl + 2);
+    if (cost < best) { best = cost; seg = sl; }
+  }
   const int bz = (f.nz + seg - 1) / seg;
   if (bx > 0x7fffffffLL || bz > 65535) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)bx, (unsigned)by, (unsigned)bz);
