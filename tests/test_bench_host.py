@@ -1,0 +1,42 @@
+"""Host-side logic of the benchmark (no GPU): the kernel names it reports for
+the library's dispatch, the multigrid cycle's algorithmic bytes, and the 3D
+workload generator's shape and mean."""
+import numpy as np
+
+import bench
+import synth
+
+
+def test_kernel_names_follow_the_dispatch():
+    big, small = 16384 * 16384, 2048 * 2048
+    assert bench.kernel_name("f32", 1, big) == "relax1_stream<float,4>"
+    assert bench.kernel_name("f64", 1, big) == "relax1_stream<double,2>"
+    assert bench.kernel_name("f64", 4, big) == "relaxT_tile<double,4>"
+    # the register wavefront from 2^23 cells at depths 3..8
+    for tb in range(3, 9):
+        assert bench.kernel_name("f32", tb, 1 << 23) == f"relaxR2_f32<{tb}>"
+    assert bench.kernel_name("f32", 2, big) == "relaxW2_f32<2>"
+    # below 2^23 cells: the one-row wavefront at 6 and 7, the two-row one otherwise
+    assert bench.kernel_name("f32", 6, small) == "relaxW_f32<6>"
+    assert bench.kernel_name("f32", 8, small) == "relaxW2_f32<8>"
+
+
+def test_multigrid_algorithmic_bytes():
+    """10.75 elements per cell on every level but the coarsest (levels halve
+    while the extent is a multiple of 4)."""
+    for n, es in ((16384, 4), (256, 8), (96, 4)):
+        cells, m = 0, n
+        while m % 4 == 0:
+            cells += m * m
+            m //= 2
+        assert bench.mg_algo_bytes(n, es) == es * 10.75 * cells
+    # 16384^2 FP32: 15.39 GB per V(2,2) cycle (4/3 of the finest level's 43 B per cell)
+    assert abs(bench.mg_algo_bytes(16384, 4) / 1e9 - 15.39) < 0.01
+
+
+def test_field3_workload():
+    r = synth.field3_rho(32, nmodes=4, kmax=8, seed=1)
+    assert r.shape == (32, 32, 32)
+    assert abs(r.mean()) < 1e-12
+    r2 = synth.field3_rho(32, nmodes=4, kmax=8, seed=1)
+    assert np.array_equal(r, r2)  # seeded
