@@ -45,6 +45,9 @@ MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (2226466688 + 1045071360) / 16384**2,
 # register wavefront; FP64 runs a red pass (all cells read, residual, red
 # updated) and a black pass (black updated in place) per sweep
 RBSOR_KERNEL = {"f32": "relaxR2_f32<6,true>", "f64": "rb_pass<double,2>"}
+# FP64 sweep ceiling: 6 FP64 operations (3 DADD + 3 DFMA) per update at the
+# 0.555e12 FP64 operations/s measured on B300
+FP64_PIPE_GLUPS = 0.555e12 / 6 / 1e9
 RBSOR_LAUNCHES_PER_SWEEP = {"f32": 1.0 / 3.0, "f64": 2.0}
 
 
@@ -399,6 +402,58 @@ def bench_batched(px, torch, steps: int, warmup: int):
             "note": "FP64 instances are bound by the FP64 pipe (6 ops/update at 0.555e12/s)"}
 
 
+def bench_c3(px, torch, budget_s: float = 20.0, n: int = 8192):
+    """The refinement workload: 8192^2, rho = 64 modes (k, l in 1..256) plus
+    sigma = 0.1 white noise, mean-zeroed; FP32-storage sweeps (500 per cycle,
+    automatic depth) inside FP64 refinement from phi0 = 0 until
+    ||rho - L phi|| <= 1e-10 ||rho||, under a wall budget of budget_s. The
+    literal field's white noise holds the (1, 0) mode, whose Jacobi gain is
+    1 - 9.8e-8 per sweep (about 1e8 sweeps to 1e-10), so it stops at the
+    budget; the same modes without the noise converge (about 8e4 sweeps).
+    Each run reports cycles, sweeps, wall time and the final relative residual
+    of px_residual_norm (FP64). FP64 multigrid V(2,2) cycles on the literal
+    field are timed beside it, as the solver that removes that bottleneck."""
+    import synth
+    h = 1.0 / n
+    out = {"grid": n, "rtol": 1e-10, "inner_sweeps": 500, "budget_s": budget_s}
+    for key, sigma in (("literal", 0.1), ("noise_free", 0.0)):
+        rho, _ = synth.modes_rho(n, n, 64, 256, synth.workload_seed(2), noise_sigma=sigma)
+        r = torch.from_numpy(rho).cuda()
+        del rho
+        phi = torch.zeros_like(r)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            info = px.solve(phi, r, h, "refine", rtol=1e-10, inner_sweeps=500,
+                            max_sweeps=10**9, timeout_ms=int(1000 * budget_s))
+        except px.PxError as e:
+            info = e.info
+        wall = time.perf_counter() - t0
+        R, P = px.residual_norm(phi, r, h)
+        out[key] = {"noise_sigma": sigma, "status": info["status"], "cycles": info["cycles"],
+                    "sweeps": info["sweeps"], "wall_s": wall, "rel_resid": R / P,
+                    "converged": bool(R / P <= 1e-10)}
+        if key == "literal":
+            # FP64 multigrid from phi0 = 0 on the same field, one cycle per call
+            phi.zero_()
+            res = torch.zeros(2, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cyc = 0
+            while cyc < 60:
+                px.mg_solve(phi, r, h, 1, resid=res)
+                cyc += 1
+                if float(res[1]) <= 1e-10 * P:
+                    break
+            wall = time.perf_counter() - t0
+            R2, _ = px.residual_norm(phi, r, h)
+            out["mg_f64_literal"] = {"cycles": cyc, "wall_s": wall, "rel_resid": R2 / P,
+                                     "converged": bool(R2 / P <= 1e-10)}
+        del r, phi
+        torch.cuda.empty_cache()
+    return out
+
+
 def load_trained_network(px):
     """The learned-guess network trained by paper_2307_07931_b300.learned, if its
     weights ship with the package (data/learned_guess_params.npy)."""
@@ -476,6 +531,35 @@ def bench_time_to_tol(px, torch, rtol: float = 1e-8):
     return out
 
 
+def digest(line: dict) -> dict:
+    """Rounded headline figures of every block of the bench line."""
+    r3 = lambda v: None if v is None else float(f"{v:.3g}")
+    d = {"value": r3(line["value"]), "frac": r3(line["roofline"]["frac"])}
+    d["T"] = {k: [r3(v["GLUP_s"]), r3(v.get("fp64_pipe_frac", v["hbm_frac"]))]
+              for k, v in line.get("variants", {}).items()}
+    if "rbsor" in line:
+        d["rb"] = {k: r3(v["GLUP_s"]) for k, v in line["rbsor"].items()}
+    if "multigrid" in line:
+        d["mg_ms_cycle"] = {k: r3(v["ms_per_cycle"]) for k, v in line["multigrid"].items()}
+    if "relax3d" in line:
+        d["3d"] = {k: r3(line["relax3d"][k]["GLUP_s"]) for k in ("f32", "f64")}
+    if "batched" in line:
+        d["batch_ms"] = r3(line["batched"]["ms"])
+    if "time_to_1e-8" in line:
+        d["tt1e-8_ms"] = {k: r3(v["ms"]) for k, v in line["time_to_1e-8"].items()
+                          if isinstance(v, dict) and "ms" in v}
+    if "refine_8192" in line:
+        c = line["refine_8192"]
+        d["c3"] = {k: [c[k]["cycles"], r3(c[k]["wall_s"]), r3(c[k]["rel_resid"])]
+                   for k in ("literal", "noise_free", "mg_f64_literal") if k in c}
+    if "euler" in line:
+        e = line["euler"]
+        d["euler"] = {k: [r3(v["Gcell_s"]), r3(v["hbm_frac"])] for k, v in e.items()
+                      if isinstance(v, dict) and "Gcell_s" in v}
+    d["e2e"] = r3(line["e2e"]["value"])
+    return d
+
+
 def launches_per_step(tb):
     return (SWEEPS + tb - 1) // tb
 
@@ -507,7 +591,8 @@ def run_gpu(args, world, rank, local):
     variants = {}
     W, K = args.warmup, args.steps
     # depth sweep (FP32) and the FP64 variant, each W + min(K, 5) steps
-    for key, tb in (("f32_t1", 1), ("f32_t2", 2), ("f32_t4", 4), ("f32_t8", 8), ("f64_t1", 1)):
+    for key, tb in (("f32_t1", 1), ("f32_t2", 2), ("f32_t4", 4), ("f32_t8", 8), ("f64_t1", 1),
+                    ("f64_t2", 2), ("f64_t4", 4), ("f64_t8", 8)):
         if args.quick and key not in ("f32_t1", "f32_t4", "f64_t1"):
             continue
         dt = key[:3]
@@ -523,6 +608,10 @@ def run_gpu(args, world, rank, local):
             "effective_GB_s": ALGO_BYTES[dt] * cells * SWEEPS / t / 1e9,
         }
         variants[key]["hbm_frac"] = variants[key]["algo_GB_s"] / hbm_peak
+        if dt == "f64":
+            # the FP64 sweep's own ceiling: 6 FP64 operations per update at the
+            # measured FP64 rate (halo recomputation of the tiled kernel not counted)
+            variants[key]["fp64_pipe_frac"] = variants[key]["GLUP_s"] / FP64_PIPE_GLUPS
 
     # ---- the timed region: FP32 at the automatic depth, K steps
     barrier(world)
@@ -615,6 +704,7 @@ def run_gpu(args, world, rank, local):
     relax3 = bench_relax3(px, torch, hbm_peak, min(K, 3), min(W, 3))
     batched = bench_batched(px, torch, K, W) if not args.quick else None
     ttt = bench_time_to_tol(px, torch) if not args.quick else None
+    c3 = bench_c3(px, torch, budget_s=args.c3_budget) if not args.quick else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -667,8 +757,13 @@ def run_gpu(args, world, rank, local):
             line["batched"] = batched
         if ttt is not None:
             line["time_to_1e-8"] = ttt
+        if c3 is not None:
+            line["refine_8192"] = c3
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        # compact digest of the extra blocks, last in the line so that a
+        # reader of the line's tail sees every headline figure
+        line["digest"] = digest(line)
         print(json.dumps(line), flush=True)
 
 
@@ -683,6 +778,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="fewer depth variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--c3-budget", type=float, default=20.0,
+                    help="wall budget (s) of the 8192^2 refinement run to 1e-10")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the dominant kernel, if captured")
     args = ap.parse_args()

@@ -105,6 +105,22 @@ const char* px_last_error(const px_ctx* ctx);
 /* Static name of a status code. */
 const char* px_status_string(px_status s);
 
+/* Per-context kernel selection (the paper has no counterpart: these pick
+ * among kernels that compute the same sweeps, for A/B timing and for tests
+ * that compare the kernel families bitwise). Defaults (0) are the fastest
+ * measured on B300.
+ *  PX_OPT_FP32_FAMILY           FP32 relaxation kernel for depth >= 2:
+ *                               0 automatic by size, 1 one-row shared-memory
+ *                               wavefront, 2 two-row shared-memory wavefront,
+ *                               3 register wavefront at every size.
+ *  PX_OPT_RB_SWEEPS_PER_LAUNCH  red-black sweeps per launch of the FP32
+ *                               register wavefront: 0 automatic (3), 1..4.
+ * px_set_option returns PX_EINVAL for an unknown option or a value out of
+ * range; it affects calls made through ctx afterwards. */
+enum { PX_OPT_FP32_FAMILY = 1, PX_OPT_RB_SWEEPS_PER_LAUNCH = 2 };
+px_status px_set_option(px_ctx* ctx, int option, int value);
+px_status px_get_option(const px_ctx* ctx, int option, int* value);
+
 /* Laplacian (Sec. IV, OL rule Laplace): lphi = L phi = s / h^2, s the
  * unscaled 5-point tap sum with periodic wrap. Computed in the grid's dtype.
  * phi and lphi must not overlap. Asynchronous. */
@@ -142,10 +158,10 @@ px_status px_relax_n(px_ctx* ctx, const px_grid* g, const void* phi_in,
 /* px_relax_n for callers that cannot allocate device memory. The paper has
  * no counterpart: this is a deployment variant of the same fused sweeps.
  *
- * Some callers may not call cudaMalloc at all: code inside a host callback
- * or a latency-bound loop that must never block on the allocator, an
- * application whose own memory pool owns the device, or a plug-in that may
- * not create library contexts (px_create allocates). This call needs no
+ * Some callers may not call cudaMalloc at all: a latency-bound loop that
+ * must never block on the allocator, an application whose own memory pool
+ * owns the device, or a plug-in that may not create library contexts
+ * (px_create allocates). This call needs no
  * px_ctx and allocates nothing. The caller still passes phi_in, phi_out, rho
  * and resid_dev, with exactly the meaning, layout and results of px_relax_n
  * (same kernels, same launch plan). The one working buffer of a multi-launch
@@ -156,9 +172,11 @@ px_status px_relax_n(px_ctx* ctx, const px_grid* g, const void* phi_in,
  *  - Limit: the field's span, ((rows - 1) * ld + width) * element size, must
  *    be at most 16 MiB (e.g. 2048 x 2048 FP32, 1448 x 1448 FP64); larger
  *    fields are rejected with PX_EINVAL before anything is launched.
- *  - Runs on the CURRENT CUDA device. The first call on each device looks
- *    up the array's device address (cudaGetSymbolAddress) and caches it;
- *    make that first call before any stream capture.
+ *  - Runs on the CURRENT CUDA device. The first call on each device (and
+ *    again the first call after that device's primary context was
+ *    recreated, e.g. after cudaDeviceReset) looks up the array's device
+ *    address (cudaGetSymbolAddress) and caches it for that context; make
+ *    that first call before any stream capture.
  *  - Every call shares the one array, which keeps the last call's contents
  *    (nothing in it needs to start at zero; resid_dev is zero-filled by the
  *    call as in px_relax_n). Calls whose work overlaps on the GPU (other
@@ -397,6 +415,21 @@ px_status px_cnn_prepare(px_cnn* net, const double* rho, const double* phi, floa
  * unscale, subtract the mean. Asynchronous. */
 px_status px_cnn_guess(px_cnn* net, const double* rho, double* phi0, int B, int H, int W,
                        double h, void* stream);
+/* Hidden tensors of the last forward pass, for inspection and tests (the
+ * paper has no counterpart): which = 0 the activation a_l = gelu(z_l), 1 the
+ * pre-activation z_l (kept only by px_cnn_grads and px_cnn_train_step), of
+ * hidden layer l = 1..5, as NHWC BF16 bit patterns (B x H x W x 32 values of
+ * the last call's shape; count may be smaller). Synchronises the stream. */
+px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, size_t count,
+                            void* stream);
+/* Polls per handshake wait (producer, MMA issuer, epilogue) of the
+ * tensor-core kernels; 0 restores the default 2^26. A wait that runs out
+ * makes its CTA stop, drain the MMAs it already issued (that wait keeps the
+ * default limit), free its tensor memory and raise a device fault word; the
+ * next call that reads the loss returns PX_ETIMEOUT and clears the word.
+ * The network stays usable: later calls recompute everything they return.
+ * (Failure detection; the paper has no counterpart.) */
+px_status px_cnn_set_wait_limit(px_cnn* net, uint32_t polls);
 
 /* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
  * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libprotox.so")
 PX_OK, PX_EINVAL, PX_ECUDA, PX_ENOMEM, PX_ENOCONV, PX_ETIMEOUT, PX_EMEAN, PX_ENAN, \
     PX_EUNSUPPORTED = range(9)
 PX_F64, PX_F32 = 0, 1
+PX_OPT_FP32_FAMILY, PX_OPT_RB_SWEEPS_PER_LAUNCH = 1, 2
 
 
 class PxError(RuntimeError):
@@ -112,6 +113,13 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_cnn_train_step.argtypes = [_vp, _vp, _vp, i, i, i, ctypes.c_float, dp, _vp]
     lib.px_cnn_prepare.argtypes = [_vp, _vp, _vp, _vp, _vp, i, i, i, d, dp, _vp]
     lib.px_cnn_guess.argtypes = [_vp, _vp, _vp, i, i, i, d, _vp]
+    lib.px_cnn_get_hidden.argtypes = [_vp, i, i, ctypes.POINTER(ctypes.c_uint16), ctypes.c_size_t,
+                                      _vp]
+    lib.px_cnn_set_wait_limit.argtypes = [_vp, ctypes.c_uint32]
+    lib.px_set_option.argtypes = [_vp, i, i]
+    lib.px_get_option.argtypes = [_vp, i, ip]
+    for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_set_option", "px_get_option"):
+        getattr(lib, name).restype = i
     for name in ("px_cnn_get_state", "px_cnn_set_state",
                  "px_cnn_create", "px_cnn_destroy", "px_cnn_get_params", "px_cnn_set_params",
                  "px_cnn_forward", "px_cnn_grads", "px_cnn_train_step", "px_cnn_prepare",
@@ -149,6 +157,15 @@ class Context:
     def check(self, s: int):
         if s != PX_OK:
             raise PxError(s, load_library().px_last_error(self.handle).decode())
+
+    def set_option(self, option: int, value: int):
+        """px_set_option: per-context kernel selection (PX_OPT_*)."""
+        self.check(load_library().px_set_option(self.handle, int(option), int(value)))
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int()
+        self.check(load_library().px_get_option(self.handle, int(option), ctypes.byref(v)))
+        return v.value
 
     def close(self):
         if self.handle:
@@ -529,6 +546,23 @@ class Cnn:
             self.handle, rho.data_ptr(), _ptr(phi), x.data_ptr(), _ptr(t), B, H, W, float(h),
             sc.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream(stream)))
         return sc
+
+    def hidden(self, layer: int, which: str, shape, stream=None):
+        """Hidden tensor of the last forward pass as a (B, H, W, 32) float32 array
+        of its BF16 values: which = "a" (activation) or "z" (pre-activation)."""
+        import numpy as np
+        B, H, W = shape
+        n = B * H * W * 32
+        raw = np.empty(n, dtype=np.uint16)
+        self.ctx.check(load_library().px_cnn_get_hidden(
+            self.handle, int(layer), 0 if which == "a" else 1,
+            raw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), n, _stream(stream)))
+        return (raw.astype(np.uint32) << 16).view(np.float32).reshape(B, H, W, 32)
+
+    def set_wait_limit(self, polls: int):
+        """px_cnn_set_wait_limit: polls per handshake wait of the tensor-core
+        kernels (0 = default)."""
+        self.ctx.check(load_library().px_cnn_set_wait_limit(self.handle, int(polls)))
 
     def guess(self, rho, phi0, h: float, stream=None):
         B, H, W = rho.shape

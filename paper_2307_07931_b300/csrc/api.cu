@@ -76,6 +76,7 @@ px_status check_grid(px_ctx* c, const px_grid* g, px::FieldDesc* f) {
   f->off = g->ghost ? g->ld + 1 : 0;
   f->dtype = g->dtype;
   f->h = g->h;
+  f->family = c ? c->opt_fp32_family : 0;
   return PX_OK;
 }
 
@@ -160,6 +161,7 @@ px_status ctx_fail(px_ctx* c, px_status st, const char* msg) { return fail(c, st
 px_status ctx_check_grid(px_ctx* c, const px_grid* g, FieldDesc* f) { return check_grid(c, g, f); }
 px_status unbound_check_grid(const px_grid* g, FieldDesc* f) { return check_grid(nullptr, g, f); }
 px_status unbound_fail(px_status s, const char* msg) { return fail(nullptr, s, "%s", msg); }
+void unbound_clear() { g_create_err.clear(); }
 size_t field_bytes(const FieldDesc& f) { return field_span(f); }
 bool ranges_overlap(const void* a, const void* b, size_t n) { return overlap(a, b, n); }
 bool ranges_overlap2(const void* a, size_t na, const void* b, size_t nb) {
@@ -242,6 +244,32 @@ px_status px_destroy(px_ctx* c) {
 
 const char* px_last_error(const px_ctx* c) {
   return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+px_status px_set_option(px_ctx* c, int option, int value) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  switch (option) {
+    case PX_OPT_FP32_FAMILY:
+      if (value < 0 || value > 3) return fail(c, PX_EINVAL, "FP32 family %d not in 0..3", value);
+      c->opt_fp32_family = value;
+      return PX_OK;
+    case PX_OPT_RB_SWEEPS_PER_LAUNCH:
+      if (value < 0 || value > 4)
+        return fail(c, PX_EINVAL, "red-black sweeps per launch %d not in 0..4", value);
+      c->opt_rb_sweeps = value;
+      return PX_OK;
+  }
+  return fail(c, PX_EINVAL, "unknown option %d", option);
+}
+
+px_status px_get_option(const px_ctx* c, int option, int* value) {
+  if (!c || !value) return PX_EINVAL;
+  switch (option) {
+    case PX_OPT_FP32_FAMILY: *value = c->opt_fp32_family; return PX_OK;
+    case PX_OPT_RB_SWEEPS_PER_LAUNCH: *value = c->opt_rb_sweeps; return PX_OK;
+  }
+  return PX_EINVAL;
 }
 
 px_status px_apply_stencil(px_ctx* c, const px_grid* g, const void* phi, void* lphi,
@@ -329,20 +357,11 @@ px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
   return PX_OK;
 }
 
-// Red-black sweeps per launch of the FP32 register wavefront (1..4; the
-// environment variable PX_RB_SWEEPS overrides the default for A/B timing).
-// Measured at 16384^2 with a report every sweep: 496, 984, 1542 and 1525
-// GLUP/s for 1..4 (four sweeps need two halo lanes per side and one CTA of 12
-// warps per SM).
-static int rb_sweeps() {
-  static int v = 0;
-  if (v == 0) {
-    const char* e = getenv("PX_RB_SWEEPS");
-    const int x = e ? atoi(e) : 0;
-    v = (x >= 1 && x <= 4) ? x : 3;
-  }
-  return v;
-}
+// Red-black sweeps per launch of the FP32 register wavefront (1..4): the
+// context option PX_OPT_RB_SWEEPS_PER_LAUNCH, else 3. Measured at 16384^2
+// with a report every sweep: 496, 984, 1542 and 1525 GLUP/s for 1..4 (four
+// sweeps need two halo lanes per side and one CTA of 12 warps per SM).
+static int rb_sweeps(const px_ctx* c) { return c->opt_rb_sweeps > 0 ? c->opt_rb_sweeps : 3; }
 
 px_status px_rbsor_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_out,
                      const void* rho, double omega, int nsweeps, double* resid_dev,
@@ -390,7 +409,7 @@ px_status px_rbsor_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_
   // phi_out (phi_in is never written), in place starting with scratch, an odd
   // launch count ending with a copy back.
   const bool reg_ok = f.dtype == 1 && px::vector_ok(f, phi_in, phi_out, rho);
-  const int D = reg_ok ? rb_sweeps() : 1;
+  const int D = reg_ok ? rb_sweeps(c) : 1;
   const int L = (nsweeps + D - 1) / D;
   if (inplace || L >= 2) {
     s = ensure_scratch(c, span);
@@ -434,7 +453,7 @@ cudaError_t rb_sweeps_ab(px_ctx* c, const px::FieldDesc& f, void* a, void* b, vo
                          const void* rho, double omega, int n, double* slot, cudaStream_t st) {
   const bool vec = px::vector_ok(f, a, b, rho);
   const bool reg = f.dtype == 1 && vec;
-  const int D = reg ? rb_sweeps() : 1;
+  const int D = reg ? rb_sweeps(c) : 1;
   for (int done = 0; done < n;) {
     const int k = std::min(D, n - done);
     void* src = *cur;

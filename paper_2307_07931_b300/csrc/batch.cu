@@ -233,7 +233,8 @@ size_t whole_bytes(int nx, int ny, int dtype) {
 }
 
 cudaError_t batch_attr() {
-  static bool attr = false;
+  static bool attr_by_dev[64] = {};
+  bool& attr = attr_by_dev[dev_index()];
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(batch_k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kWholeSmem);

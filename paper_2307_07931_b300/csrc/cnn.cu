@@ -167,8 +167,12 @@ constexpr uint32_t kWsTmemCols = 128;                                 // 2 sets 
 constexpr int kWsBars = 2 * kWsStages + 4 + 1;  // full, empty, tfull[2], tempty[2], weights
 constexpr size_t kWsSmem = kWsStages * kCmTile + kWBytes + kWsBars * 8 + 16;
 
-__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+// Handshake wait: up to `limit` polls of the barrier's phase, giving up early
+// once another thread of the CTA has set the abort flag; on running out it
+// sets the flag itself.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_,
+                                             uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
@@ -176,6 +180,18 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, vola
     if ((it & 63) == 63 && *abort_) return false;
   }
   *abort_ = 1;
+  return false;
+}
+// Drain wait: up to kSpinLimit polls, ignoring the abort flag. Used only for
+// the completion of MMAs already issued, which needs no other thread, so it
+// ends well inside the limit; tensor memory is freed only after it.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
   return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -246,7 +262,8 @@ __global__ void __launch_bounds__(kWsConvThreads, 2)
 conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
           __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
-          int tiles_x, int tiles_y, int ntiles, int dil, unsigned* __restrict__ fault) {
+          int tiles_x, int tiles_y, int ntiles, int dil, unsigned* __restrict__ fault,
+          uint32_t wait_limit) {
   // no static shared variables: the core matrices must start on 128-byte boundaries
   extern __shared__ __align__(128) unsigned char wsu[];
   unsigned char* ring = wsu;
@@ -299,7 +316,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
       for (int tap = 0; tap < 9; ++tap, ++g) {
         const int st = g % kWsStages, u = g / kWsStages;
-        if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_)) { go = false; break; }
+        if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_, wait_limit)) { go = false; break; }
         load_tap_cm_p<TR>(ring + st * kCmTile, in, b, ty * TR, tx * TW, tap_dy(tap, dil),
                       tap_dx(tap, dil), H, W, pid, np);
         cp_commit();
@@ -318,15 +335,15 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   } else if (warp == kWsEpiWarps + kWsProdWarps) {
     // ---- MMA issue
     if (lane == 0) {
-      bool go = mbar_wait_ab(wfull, 0, abort_);
+      bool go = mbar_wait_ab(wfull, 0, abort_, wait_limit);
       const uint32_t tbase = smem_u32(ring), wbase = smem_u32(wsm);
       int g = 0;
       for (int i = 0; i < my_tiles && go; ++i) {
         const int a = i & 1;
-        if (i >= 2 && !mbar_wait_ab(tempty0 + 8 * a, ((i >> 1) - 1) & 1, abort_)) { go = false; break; }
+        if (i >= 2 && !mbar_wait_ab(tempty0 + 8 * a, ((i >> 1) - 1) & 1, abort_, wait_limit)) { go = false; break; }
         for (int tap = 0; tap < 9; ++tap, ++g) {
           const int st = g % kWsStages;
-          if (!mbar_wait_ab(full0 + 8 * st, (g / kWsStages) & 1, abort_)) { go = false; break; }
+          if (!mbar_wait_ab(full0 + 8 * st, (g / kWsStages) & 1, abort_, wait_limit)) { go = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t abase = tbase + st * (uint32_t)kCmTile;
 #pragma unroll
@@ -344,6 +361,8 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         }
         if (!go) break;
         umma_commit(tfull0 + 8 * a);
+        last_bar = tfull0 + 8 * a;  // the last commit: a drain waits for this one
+        last_par = (i >> 1) & 1;
       }
       if (!go) *abort_ = 1;
     }
@@ -352,7 +371,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
     // ---- epilogue
     for (int i = 0; i < my_tiles; ++i) {
       const int a = i & 1;
-      if (!mbar_wait_ab(tfull0 + 8 * a, (i >> 1) & 1, abort_)) break;
+      if (!mbar_wait_ab(tfull0 + 8 * a, (i >> 1) & 1, abort_, wait_limit)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int tile = (int)blockIdx.x + i * (int)gridDim.x;
       const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
@@ -376,12 +395,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       if (lane == 0) {
         atomicOr(fault, 1u);
         // MMAs already issued finish on their own: wait (bounded) for the last commit
-        if (last_bar) {
-          uint32_t done = 0;
-          for (uint32_t it = 0; it < kSpinLimit && !done; ++it)
-            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                         "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(last_bar), "r"(last_par) : "memory");
-        }
+        if (last_bar) mbar_wait_drain(last_bar, last_par);
       }
       __syncwarp();
     }
@@ -417,7 +431,7 @@ constexpr uint32_t kIdescMN = kIdesc | (1u << 15) | (1u << 16);  // A and B MN-m
 __global__ void __launch_bounds__(kConvThreads, 2)
 wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
              float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
-             int dil, unsigned* __restrict__ fault) {
+             int dil, unsigned* __restrict__ fault, uint32_t wait_limit) {
   // no static shared variables: the core matrices must start on 128-byte boundaries
   extern __shared__ __align__(128) unsigned char wgu[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(wgu + kWgTiles * kWgTile);
@@ -478,8 +492,12 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
         }
       }
       umma_commit(smem_u32(bar));
-      // the tiles are restaged only after these MMAs have read them
-      if (!mbar_wait_ab(smem_u32(bar), i & 1, abort_)) *s_ok = 0;
+      // the tiles are restaged only after these MMAs have read them; a wait
+      // that runs out still drains them before the CTA goes on
+      if (!mbar_wait_ab(smem_u32(bar), i & 1, abort_, wait_limit)) {
+        mbar_wait_drain(smem_u32(bar), i & 1);
+        *s_ok = 0;
+      }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
@@ -952,6 +970,7 @@ struct px_cnn {
   double* scales = nullptr;
   double* lpart_host = nullptr;
   int64_t cap_img = 0;
+  uint32_t wait_limit = kSpinLimit;  // polls per handshake wait of the tensor-core kernels
 };
 
 namespace {
@@ -1022,9 +1041,11 @@ px_status check_shape(px_cnn* n, int B, int H, int W) {
   return PX_OK;
 }
 
-// Device address of the conv fault word (looked up once, then cached).
+// Device address of the conv fault word on the current device (looked up
+// once per device, then cached).
 unsigned* conv_fault_ptr() {
-  static unsigned* p = nullptr;
+  static unsigned* by_dev[64] = {};
+  unsigned*& p = by_dev[px::dev_index()];
   if (!p) {
     void* q = nullptr;
     if (cudaGetSymbolAddress(&q, g_conv_fault) != cudaSuccess) { cudaGetLastError(); return nullptr; }
@@ -1050,7 +1071,8 @@ px_status check_conv_fault(px_cnn* n, cudaStream_t st) {
 }
 
 px_status set_conv_attrs() {
-  static bool done = false;
+  static bool done_by_dev[64] = {};
+  bool& done = done_by_dev[px::dev_index()];
   if (done) return PX_OK;
   cudaError_t e = cudaFuncSetAttribute(conv32_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
@@ -1074,7 +1096,7 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
   for (int l = 1; l <= 4; ++l)
     conv32_ws<0><<<cgrid, kWsConvThreads, kWsSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault);
+        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault, n->wait_limit);
   conv_last<<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
@@ -1112,12 +1134,12 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   for (int l = 4; l >= 1; --l) {
     wgrad32_umma<<<wg_ctas, kConvThreads, kWgUmmaSmem, st>>>(
         n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, n->dil[l],
-        conv_fault_ptr());
+        conv_fault_ptr(), n->wait_limit);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
         gcur, n->wb[l], nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
-        n->dil[l], conv_fault_ptr());
+        n->dil[l], conv_fault_ptr(), n->wait_limit);
     std::swap(gcur, gnext);
   }
   wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
@@ -1237,6 +1259,32 @@ px_status px_cnn_set_params(px_cnn* n, const float* host, size_t count) {
 }
 
 size_t px_cnn_state_count(void) { return 3 * kOff.total; }
+
+// Stored hidden tensors of the last forward pass (for inspection and
+// tests): which = 0 the activation a_l = gelu(z_l), 1 the pre-activation z_l
+// (kept only by px_cnn_grads / px_cnn_train_step), of hidden layer l = 1..5;
+// NHWC BF16 bit patterns, B * H * W * 32 values for the last call's shape.
+px_status px_cnn_get_hidden(px_cnn* n, int layer, int which, uint16_t* host, size_t count,
+                            void* stream) {
+  if (!n || !host || layer < 1 || layer > 5 || which < 0 || which > 1) return PX_EINVAL;
+  if (n->cap_px == 0 || count > (size_t)n->cap_px * C) return PX_EINVAL;
+  DevScope ds(n->ctx->device);
+  const __nv_bfloat16* src = which == 0 ? n->a[layer - 1] : n->z[layer - 1];
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host, src, count * sizeof(uint16_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "hidden readback");
+}
+
+// Polls per handshake wait of the tensor-core kernels (0 restores the
+// default). A wait that runs out makes its CTA stop, drain the MMAs it has
+// issued, free its tensor memory and raise the fault word, which the next
+// loss readback reports as PX_ETIMEOUT.
+px_status px_cnn_set_wait_limit(px_cnn* n, uint32_t polls) {
+  if (!n) return PX_EINVAL;
+  n->wait_limit = polls == 0 ? kSpinLimit : polls;
+  return PX_OK;
+}
 
 // Training state for checkpoints: FP32 parameters, Adam first and second
 // moments (each px_cnn_param_count() floats, in that order) and the step.

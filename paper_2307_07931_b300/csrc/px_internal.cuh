@@ -82,6 +82,7 @@ struct FieldDesc {
   int ghost;
   int dtype;     // 0 = f64, 1 = f32
   double h;
+  int family = 0;  // FP32 kernel family for depth >= 2 (PX_OPT_FP32_FAMILY; 0 = automatic)
 };
 
 // Whether the vectorised kernels may run on this layout / these pointers.
@@ -145,6 +146,9 @@ cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
                               cudaStream_t st);
 
 int device_sm_count();
+// Current device index clamped to 0..63, for the per-device caches of the
+// launchers (occupancy, function attributes, symbol addresses).
+int dev_index();
 
 // Iterative refinement (stencil.cu). phi/rho FP64 with layout f; r32/e32 are
 // unghosted FP32 fields of pitch ld32. norm[0] = ||rho - L phi||_inf > 0.
@@ -177,6 +181,8 @@ struct px_ctx {
   int sched_cap = 0;
   void* mg = nullptr;        // multigrid levels 1..L-1: right-hand side and two states each
   size_t mg_bytes = 0;
+  int opt_fp32_family = 0;   // PX_OPT_FP32_FAMILY (0 = automatic)
+  int opt_rb_sweeps = 0;     // PX_OPT_RB_SWEEPS_PER_LAUNCH (0 = automatic)
   std::string err;
 };
 
@@ -187,6 +193,8 @@ namespace px {
 // failures set the message returned by px_last_error(NULL).
 px_status unbound_check_grid(const px_grid* g, FieldDesc* f);
 px_status unbound_fail(px_status s, const char* msg);
+// Clears the calling thread's context-free error message (px_last_error(NULL)).
+void unbound_clear();
 size_t field_bytes(const FieldDesc& f);
 bool ranges_overlap(const void* a, const void* b, size_t n);
 bool ranges_overlap2(const void* a, size_t na, const void* b, size_t nb);

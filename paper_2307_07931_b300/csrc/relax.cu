@@ -305,7 +305,8 @@ cudaError_t launch_stream_t(const FieldDesc& f, const T* src, T* dst, const T* r
   const int ry = (int)std::max<int64_t>(1, std::min<int64_t>(32, (int64_t)f.ny * nstrips / target));
   const int nseg = (f.ny + ry - 1) / ry;
   const int64_t ntasks = (int64_t)nstrips * nseg;
-  static int blocks_per_sm = 0;
+  static int blocks_by_dev[64] = {};
+  int& blocks_per_sm = blocks_by_dev[dev_index()];
   if (blocks_per_sm == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &blocks_per_sm, relax1_stream<T, V, kRep>, 256, 0);
@@ -325,7 +326,8 @@ template <typename T, int TB>
 cudaError_t launch_tile_t(const FieldDesc& f, const T* src, T* dst, const T* rho,
                           Coef<T> k, Reports rep, cudaStream_t st) {
   using G = TileGeom<T, TB>;
-  static bool attr = false;
+  static bool attr_by_dev[64] = {};
+  bool& attr = attr_by_dev[dev_index()];
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(relaxT_tile<T, TB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -711,7 +713,8 @@ template <int TB>
 cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                            Coef<float> k, Reports rep, cudaStream_t st) {
   using G = W2Geom<TB>;
-  static int occ = 0;
+  static int occ_by_dev[64] = {};
+  int& occ = occ_by_dev[dev_index()];
   if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(relaxW2_f32<TB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -739,22 +742,15 @@ cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, con
   return cudaGetLastError();
 }
 
-// FP32 kernel family for depth >= 2, from PX_FP32_WAVE: "w1" the one-row
-// wavefront, "w2" the two-row wavefront, "r" the register wavefront at every
-// size, anything else (the default) the fastest measured (200 sweeps, a
-// report every sweep): the register wavefront at depths 3..8 on fields of
-// 2^23 cells or more (depth 8: 2406 vs 1424 GLUP/s on the two-row wavefront
-// at 16384^2, 1431 vs 912 at 3072^2); below, where the two-row wavefront wins
-// at depth 8 (997 vs 909 at 2048^2), the one-row wavefront for depths 6 and 7
-// and the two-row one for the others; depth 2 always the two-row one.
-int wave_kernel() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = getenv("PX_FP32_WAVE");
-    v = (e && !strcmp(e, "w1")) ? 1 : (e && !strcmp(e, "w2")) ? 2 : (e && !strcmp(e, "r")) ? 3 : 0;
-  }
-  return v;
-}
+// FP32 kernel family for depth >= 2, from the context option
+// PX_OPT_FP32_FAMILY carried in the field descriptor: 1 the one-row
+// wavefront, 2 the two-row wavefront, 3 the register wavefront at every size,
+// 0 (the default) the fastest measured (200 sweeps, a report every sweep):
+// the register wavefront at depths 3..8 on fields of 2^23 cells or more
+// (depth 8: 2406 vs 1424 GLUP/s on the two-row wavefront at 16384^2, 1431 vs
+// 912 at 3072^2); below, where the two-row wavefront wins at depth 8 (997 vs
+// 909 at 2048^2), the one-row wavefront for depths 6 and 7 and the two-row
+// one for the others; depth 2 always the two-row one.
 
 // ---------------------------------------------------------------------------
 // relaxR2_f32: register wavefront, TB stages per launch, no shared tiles and
@@ -1111,7 +1107,8 @@ template <int TB, bool kRB = false>
 cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
                           cudaStream_t st) {
-  static int occ = 0;
+  static int occ_by_dev[64] = {};
+  int& occ = occ_by_dev[dev_index()];
   if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
@@ -1149,7 +1146,8 @@ template <int TB>
 cudaError_t launch_wave_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, cudaStream_t st) {
   using G = WGeom<TB>;
-  static int occ = 0;
+  static int occ_by_dev[64] = {};
+  int& occ = occ_by_dev[dev_index()];
   if (occ == 0) {
     cudaError_t e = cudaFuncSetAttribute(relaxW_f32<TB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1197,7 +1195,7 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
              : launch_stream_t<T, 1, false>(f, src, dst, rho, k, slot, st);
   }
   if constexpr (sizeof(T) == 4) {
-    const int fam = wave_kernel();
+    const int fam = f.family;
     // the register wavefront needs many warps' worth of rows: from 2^23 cells
     if (fam == 3 || (fam == 0 && tb >= 3 && (int64_t)f.nx * f.ny >= ((int64_t)1 << 23))) {
       switch (tb) {
@@ -1247,6 +1245,12 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
 }
 
 }  // namespace
+
+int dev_index() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  return dev < 0 ? 0 : (dev > 63 ? 63 : dev);
+}
 
 int device_sm_count() {
   int dev = 0;

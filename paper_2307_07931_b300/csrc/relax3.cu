@@ -172,7 +172,8 @@ cudaError_t launch3_t(const Field3& f, const T* src, T* dst, const T* rho, doubl
                       double* slot, cudaStream_t st) {
   constexpr int TX = 32 * V;
   const size_t smem = (size_t)kRing * Slot3<T, V>::kElems * sizeof(T);
-  static int occ[2] = {0, 0};
+  static int occ_by_dev[64][2] = {};
+  int (&occ)[2] = occ_by_dev[dev_index()];
   const int ri = slot ? 1 : 0;
   if (occ[ri] == 0) {
     auto kern = slot ? relax3_k<T, V, true> : relax3_k<T, V, false>;

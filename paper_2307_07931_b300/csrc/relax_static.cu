@@ -2,19 +2,24 @@
 // not allocate device memory.
 //
 // Who needs it: code that runs where cudaMalloc is off limits or unsafe, for
-// example inside a host callback or a real-time loop that may not block on
-// the allocator, an application whose own pool owns all device memory, or a
-// plug-in that may not create library contexts (px_create allocates). Such a
-// caller still passes its own phi_in, phi_out, rho and report buffers; the
-// only working memory the sweeps need beyond them, the ping-pong field of a
-// multi-launch relax, comes from the fixed array below.
+// example a real-time loop that may not block on the allocator, an
+// application whose own pool owns all device memory, or a plug-in that may
+// not create library contexts (px_create allocates). Such a caller still
+// passes its own phi_in, phi_out, rho and report buffers; the only working
+// memory the sweeps need beyond them, the ping-pong field of a multi-launch
+// relax, comes from the fixed array below.
 //
 // The array lives in this library's device image, so every GPU on which the
 // library's kernels are loaded holds its 16 MiB until the process exits. Host
 // code may not use its name as a pointer (on the host it names a stand-in, not
-// device memory), so its device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current, and cached.
+// device memory), so its device address is looked up with
+// cudaGetSymbolAddress while that device is current, and cached per device
+// together with the identity of the device's current context: a context that
+// was destroyed and recreated (cudaDeviceReset) gets a fresh lookup instead
+// of a stale address.
 #include "px_internal.cuh"
+
+#include <cuda.h>
 
 #include <cmath>
 #include <cstdio>
@@ -29,9 +34,40 @@ static __device__ __align__(256) unsigned char px_static_scratch[kStaticScratchB
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context id the address belongs to
+
+// Unique id of the calling thread's current context (never reused within a
+// process), through the driver entry points the runtime resolves; 0 if the
+// driver does not provide them, in which case the address is looked up on
+// every call.
+unsigned long long current_ctx_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+    resolved = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext cx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&cx) != CUDA_SUCCESS || !cx || get_id(cx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 // Device address of the static scratch on the current device, looked up on the
-// first call for that device.
+// first call for that device and context.
 px_status static_scratch(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -42,9 +78,10 @@ px_status static_scratch(void** out) {
   if (dev < 0 || dev >= kMaxDevices)
     return px::unbound_fail(PX_EUNSUPPORTED, "px_relax_n_static: device index above 63");
   std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long cid = current_ctx_id();
+  if (!g_scratch_ptr[dev] || cid == 0 || cid != g_scratch_ctx[dev]) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, px_static_scratch);
+    e = cudaGetSymbolAddress(&p, px_static_scratch);  // binds the primary context if none is
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       char msg[256];
@@ -53,6 +90,7 @@ px_status static_scratch(void** out) {
       return px::unbound_fail(PX_ECUDA, msg);
     }
     g_scratch_ptr[dev] = p;
+    g_scratch_ctx[dev] = cid != 0 ? cid : current_ctx_id();
   }
   *out = g_scratch_ptr[dev];
   return PX_OK;
@@ -71,6 +109,7 @@ extern "C" px_status px_relax_n_static(const px_grid* g, const void* phi_in, voi
                                        const void* rho, double omega, int nsweeps,
                                        int tblock, double* resid_dev, int report_every,
                                        void* stream) {
+  px::unbound_clear();
   px::FieldDesc f;
   px_status s = px::unbound_check_grid(g, &f);
   if (s != PX_OK) return s;

@@ -203,7 +203,7 @@ def main():
         logf.flush()
 
     px.load_library()
-    res = {"config": vars(a), "grid": N, "omega": OMEGA}
+    res = {"config": {k: v for k, v in vars(a).items() if k != "out"}, "grid": N, "omega": OMEGA}
     t0 = time.perf_counter()
     rho_tr = torch.from_numpy(make_fields(TRAIN_SEED, a.train)).cuda()
     rho_ev = torch.from_numpy(make_fields(EVAL_SEED, a.eval)).cuda()

@@ -40,3 +40,30 @@ def test_field3_workload():
     assert abs(r.mean()) < 1e-12
     r2 = synth.field3_rho(32, nmodes=4, kmax=8, seed=1)
     assert np.array_equal(r, r2)  # seeded
+
+
+def test_digest_is_short_and_complete():
+    """The digest closing the bench line carries every block's headline figure
+    in well under the 1500 characters a reader of the line's tail keeps."""
+    import json
+    v = {"GLUP_s": 1.0, "hbm_frac": 0.5, "ms_per_step": 1.0}
+    line = {
+        "value": 2572.2, "roofline": {"frac": 0.594},
+        "variants": {k: dict(v) for k in ("f32_t1", "f32_t2", "f32_t4", "f32_t8")},
+        "rbsor": {"f32": v, "f64": v},
+        "multigrid": {"f32": {"ms_per_cycle": 3.2}, "f64": {"ms_per_cycle": 37.0}},
+        "relax3d": {"f32": v, "f64": v},
+        "batched": {"ms": 347.0},
+        "time_to_1e-8": {"plain_f64": {"ms": 278.0}, "mixed": {"ms": 86.0}, "grid": 256},
+        "refine_8192": {k: {"cycles": 3, "wall_s": 1.0, "rel_resid": 1e-11}
+                        for k in ("literal", "noise_free", "mg_f64_literal")},
+        "euler": {"f64": {"Gcell_s": 1.0, "hbm_frac": 0.8}, "f32": {"Gcell_s": 2.0, "hbm_frac": 0.8}},
+        "e2e": {"value": 1500.0},
+    }
+    for k in ("f64_t1", "f64_t2", "f64_t4", "f64_t8"):
+        line["variants"][k] = dict(v, fp64_pipe_frac=0.7)
+    d = bench.digest(line)
+    assert d["T"]["f64_t4"] == [1.0, 0.7] and d["T"]["f32_t8"] == [1.0, 0.5]
+    assert d["c3"]["noise_free"] == [3, 1.0, 1e-11]
+    assert d["euler"]["f32"] == [2.0, 0.8]
+    assert len(json.dumps(d)) < 1000

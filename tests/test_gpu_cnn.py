@@ -1,15 +1,34 @@
 """GPU parity of the learned-guess network kernels (px_cnn_*) against the FP64
 network oracle (oracle/cnn.py), through the C ABI.
 
-Tolerances come from BF16: weights and activations are rounded to 8-bit
-mantissas (unit roundoff 2^-9 = 2.0e-3) at every layer and accumulated in
-FP32. A layer's output then carries a relative error of a few 2^-9 of its
-scale, and six layers give a few percent of the output scale:
-  forward y:    max|y - y_oracle| <= 3e-2 max|y_oracle|
-  gradients:    per layer, max|dW - dW_oracle| <= 5e-2 max|dW_oracle|
-  loss:         relative 2e-2
+Tolerances come from BF16 storage. BF16 keeps 8 significant bits, so one
+rounding has a relative error of at most u = 2^-8 = 3.9e-3. The hidden
+weights W2..W5 are BF16 on the GPU; the oracle gets the same BF16-rounded
+weights (W1, W6 and the biases stay FP32 on both sides), so what is left is
+the rounding of the five hidden activations (and, backwards, of the
+activation gradients) plus FP32 accumulation. A CPU emulation of that
+storage (FP64 arithmetic, BF16 rounding where the GPU stores BF16) against
+the plain oracle gives, over 15 seeded cases of the shapes below:
+  forward y:   max|y - y_oracle| / max|y_oracle| <= 6.5e-3  -> bound 1.25e-2
+  gradients:   per layer, err / max|dW_oracle| <= 4e-3 on 8-row images,
+               <= 1.6e-4 on 256^2 images (many pixels per sum)
+                                                             -> 1e-2 and 2e-3
+  loss:        relative <= 2.2e-4                            -> 2e-3
+One layer at a time the bound is tight and rigorous: with the GPU's own BF16
+input of a layer, z = bf16(fp32 sum) differs from the FP64 oracle's z by at
+most u |z| (the rounding) plus the FP32 accumulation error of 289 terms,
+289 * 2^-24 * sum|w x| <= 2e-5 S (S bounded by max|x| sum|w| per output
+channel; 5e-5 S is allowed for the tensor cores' accumulation order).
 Adam runs in FP32 on FP32 master weights: the update matches the oracle's
 FP64 Adam applied to the same gradients to 1e-5 relative.
+
+The multi-tile cases run the persistent kernels with several tiles per CTA:
+the 4 x 64 output tiles are dealt to min(tiles, 2 x SMs) CTAs (296 on
+B300), so B = 8 images of 256^2 (2048 tiles) give each CTA about seven
+tiles, alternating its two tensor-memory accumulator sets and flipping every
+barrier phase many times; the weight gradient's 2 x 64-pixel tiles at B = 2,
+256^2 (1024 tiles) make each CTA accumulate about 3.5 tiles in tensor memory
+before the fixed-order reduction of the 296 partials.
 """
 import numpy as np
 import pytest
@@ -18,6 +37,8 @@ from oracle import cnn as ocnn
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+U_BF16 = 2.0 ** -8
 
 
 @pytest.fixture(scope="module")
@@ -28,15 +49,24 @@ def px():
     return m
 
 
-def oracle_params(px, net):
-    return [(w.astype(np.float64), b.astype(np.float64)) for w, b in px.cnn_unflatten(net.params())]
-
-
 def bf16_round(a):
     return torch.from_numpy(np.asarray(a, dtype=np.float32)).bfloat16().float().numpy().astype(np.float64)
 
 
+def oracle_params(px, net, bf16_hidden=True):
+    """The network's FP32 master parameters in FP64; with bf16_hidden the
+    weights of the four 32 -> 32 layers rounded to BF16, as the GPU uses them."""
+    out = []
+    for li, (w, b) in enumerate(px.cnn_unflatten(net.params())):
+        w = w.astype(np.float64)
+        if bf16_hidden and 1 <= li <= 4:
+            w = bf16_round(w)
+        out.append((w, b.astype(np.float64)))
+    return out
+
+
 DIL = (1, 3, 9, 27, 81, 1)
+FWD_TOL, GRAD_TOL_SMALL, GRAD_TOL_LARGE, LOSS_TOL = 1.25e-2, 1e-2, 2e-3, 2e-3
 
 
 @pytest.mark.parametrize("B,H,W,dil", [(2, 8, 64, None), (1, 12, 128, None), (1, 256, 256, None),
@@ -52,7 +82,7 @@ def test_forward_matches_oracle(px, B, H, W, dil):
     ref, _ = ocnn.forward(oracle_params(px, net), x.astype(np.float64)[:, None], dil)
     ref = ref[:, 0]
     got = y.cpu().numpy().astype(np.float64)
-    assert np.max(np.abs(got - ref)) <= 3e-2 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= FWD_TOL * np.max(np.abs(ref))
     net.close()
 
 
@@ -68,11 +98,126 @@ def test_gradients_match_oracle(px, dil):
     y, cache = ocnn.forward(P, x.astype(np.float64)[:, None], dil)
     L, dy = ocnn.mse(y, t.astype(np.float64)[:, None])
     ref = ocnn.backward(P, cache, dy, dil)
-    assert abs(loss - L) <= 2e-2 * L
+    assert abs(loss - L) <= LOSS_TOL * L
+    check_grads(px, g, ref, GRAD_TOL_SMALL)
+    net.close()
+
+
+def check_grads(px, g, ref, tol):
     gl = px.cnn_unflatten(g)
     for li, ((dW, db), (gw, gb)) in enumerate(zip(ref, gl)):
-        assert np.max(np.abs(gw - dW)) <= 5e-2 * np.max(np.abs(dW)), li
-        assert np.max(np.abs(gb - db)) <= 5e-2 * max(np.max(np.abs(db)), 1e-3 * np.max(np.abs(dW))), li
+        assert np.max(np.abs(gw - dW)) <= tol * np.max(np.abs(dW)), li
+        assert np.max(np.abs(gb - db)) <= tol * max(np.max(np.abs(db)), 1e-3 * np.max(np.abs(dW))), li
+
+
+def _layer_bound(h, w, b, d):
+    """Per-element FP32 accumulation scale S of one conv: max|h| over the
+    image times sum |w| over (c, tap) of the output channel, plus |b|."""
+    amax = np.max(np.abs(h), axis=(1, 2, 3))                     # per image
+    wsum = np.sum(np.abs(w), axis=(1, 2, 3))                    # per output channel
+    return amax[:, None, None, None] * wsum[None, :, None, None] + np.abs(b)[None, :, None, None]
+
+
+@pytest.mark.parametrize("dil", [None, DIL])
+def test_forward_multitile_matches_oracle(px, dil):
+    """B = 8 images of 256^2: about seven tiles per CTA of every tensor-core
+    layer. The output is compared element by element with the FP64 oracle
+    (bound FWD_TOL), and every hidden layer of images 0, 3, 6 and 7 (the
+    first and the later tiles of the CTAs, both accumulator sets) with the
+    oracle's conv of the GPU's own BF16 input (rigorous per-element bound)."""
+    B, H, W = 8, 256, 256
+    d = dil or (1,) * 6
+    net = px.Cnn(seed=13, dilations=dil)
+    rng = np.random.default_rng(17)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    t = rng.standard_normal((B, H, W)).astype(np.float32)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    net.forward(xt, y)
+    torch.cuda.synchronize()
+    P = oracle_params(px, net)
+    ref, _ = ocnn.forward(P, x.astype(np.float64)[:, None], dil)
+    got = y.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref[:, 0])) <= FWD_TOL * np.max(np.abs(ref))
+    # training forward keeps z; its activations equal the inference ones
+    net.grads(xt, torch.from_numpy(t).cuda())
+    imgs = [0, 3, 6, 7]
+
+    def hidden(layer, which):
+        return net.hidden(layer, which, (B, H, W))[imgs].transpose(0, 3, 1, 2).astype(np.float64)
+    hin = x.astype(np.float64)[imgs][:, None]
+    for li in range(5):                                          # layers 1..5 (index li)
+        w, b = P[li]
+        zr = ocnn.conv(hin, w, b, d[li])
+        S = _layer_bound(hin, w, b, d[li])
+        zg = hidden(li + 1, "z")
+        assert np.all(np.abs(zg - zr) <= 1.01 * U_BF16 * np.abs(zr) + 5e-5 * S), li
+        del zg
+        ar = ocnn.gelu(zr)
+        ag = hidden(li + 1, "a")
+        assert np.all(np.abs(ag - ar) <= 1.01 * U_BF16 * np.abs(ar) + 1.13 * 5e-5 * S
+                      + 1e-6 * np.abs(zr)), li
+        hin = ag
+        del zr, ar, S
+    w6, b6 = P[5]
+    yr = ocnn.conv(hin, w6, b6, d[5])[:, 0]
+    S6 = _layer_bound(hin, w6, b6, d[5])[:, 0]
+    assert np.all(np.abs(got[imgs] - yr) <= 5e-5 * S6)
+    # inference output unchanged by the training forward's bookkeeping
+    y2 = torch.empty_like(xt)
+    net.forward(xt, y2)
+    torch.cuda.synchronize()
+    assert torch.equal(y, y2)
+    net.close()
+
+
+@pytest.mark.parametrize("dil", [None, DIL])
+def test_gradients_multitile_match_oracle(px, dil):
+    """B = 2 images of 256^2: the weight-gradient kernel accumulates about 3.5
+    tiles per CTA in tensor memory and reduces 296 partials; the input-gradient
+    convolution runs about 1.7 tiles per CTA. Every layer's dW and db against
+    the oracle's analytic backward, the loss against the oracle's MSE."""
+    B, H, W = 2, 256, 256
+    net = px.Cnn(seed=21, dilations=dil)
+    rng = np.random.default_rng(23)
+    x = rng.standard_normal((B, H, W)).astype(np.float32)
+    t = rng.standard_normal((B, H, W)).astype(np.float32)
+    g, loss = net.grads(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    P = oracle_params(px, net)
+    y, cache = ocnn.forward(P, x.astype(np.float64)[:, None], dil)
+    L, dy = ocnn.mse(y, t.astype(np.float64)[:, None])
+    ref = ocnn.backward(P, cache, dy, dil)
+    assert abs(loss - L) <= LOSS_TOL * L
+    check_grads(px, g, ref, GRAD_TOL_LARGE)
+    # deterministic: the same call gives bitwise the same gradients
+    g2, loss2 = net.grads(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    assert np.array_equal(g, g2) and loss == loss2
+    net.close()
+
+
+def test_bounded_wait_times_out_and_recovers(px):
+    """With one poll per handshake wait the tensor-core kernels give up (no
+    phase completes that fast everywhere), drain their issued MMAs, free
+    their tensor memory and raise the fault word: the call returns
+    PX_ETIMEOUT. With the default limit restored, the next call on the same
+    context gives bitwise the gradients of a call made before the timeout."""
+    B, H, W = 4, 64, 256
+    net = px.Cnn(seed=29, dilations=DIL)
+    rng = np.random.default_rng(31)
+    x = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+    g0, l0 = net.grads(x, t)
+    net.set_wait_limit(1)
+    with pytest.raises(px.PxError) as ei:
+        net.grads(x, t)
+    assert ei.value.status == px.PX_ETIMEOUT
+    net.set_wait_limit(0)
+    g1, l1 = net.grads(x, t)
+    assert np.array_equal(g0, g1) and l0 == l1
+    y = torch.empty_like(x)
+    net.forward(x, y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
     net.close()
 
 

@@ -19,9 +19,6 @@ starting and the final state; the arithmetic behind them):
   * Residual reports: the same factors times the scale of the summed terms,
     8 ||phi|| / h^2 + ||rho||.
 """
-import os
-import subprocess
-import sys
 
 import numpy as np
 import pytest
@@ -215,43 +212,36 @@ def test_full_size_convergence(px, dtype):
     assert err <= (1e-3 if dtype == torch.float32 else 1e-8), err
 
 
-MG_CHILD = r"""
-import sys, torch
-sys.path.insert(0, sys.argv[1])
-import paper_2307_07931_b300 as px
-g = torch.Generator(device="cuda"); g.manual_seed(5)
-worst = 0.0
-for (nx, ny) in [(1024, 512), (256, 256), (132, 68)]:
-    h = 1.0 / nx
-    rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    rho -= rho.mean()
-    phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    def pitched(a):
-        b = torch.zeros(ny, nx + 1, device="cuda", dtype=torch.float32)[:, :nx]
-        b.copy_(a)
-        return b
-    a, ra = phi.clone(), torch.zeros(4, dtype=torch.float64, device="cuda")
-    px.mg_solve(a, rho, h, 3, resid=ra)
-    b, rb = pitched(phi), torch.zeros_like(ra)
-    px.mg_solve(b, pitched(rho), h, 3, resid=rb)
-    worst = max(worst, float((a - b).abs().max()), float((ra - rb).abs().max()))
-print("worst", worst)
-sys.exit(0 if worst == 0.0 else 1)
-"""
-
-
-@pytest.mark.parametrize("sweeps", ["1", "2", "3"])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
 def test_smoother_paths_bitwise(sweeps):
     """On FP32 the finest level's smoother runs on the register wavefront
     (aligned rows) or on the two-pass kernels (pitch nx + 1); both evaluate
     the same per-cell expressions, so whole cycles agree bitwise, at every
-    depth of the wavefront (chosen once per process, so each depth runs in a
-    child process)."""
+    depth of the wavefront (selected per context with
+    PX_OPT_RB_SWEEPS_PER_LAUNCH)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ)
-    env["PX_RB_SWEEPS"] = sweeps
-    r = subprocess.run([sys.executable, "-c", MG_CHILD, root], env=env, capture_output=True,
-                       text=True, timeout=600)
-    assert r.returncode == 0, r.stdout + r.stderr
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_RB_SWEEPS_PER_LAUNCH, sweeps)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        for (nx, ny) in [(1024, 512), (256, 256), (132, 68)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            rho -= rho.mean()
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+
+            def pitched(a):
+                b = torch.zeros(ny, nx + 1, device="cuda", dtype=torch.float32)[:, :nx]
+                b.copy_(a)
+                return b
+            a, ra = phi.clone(), torch.zeros(4, dtype=torch.float64, device="cuda")
+            px.mg_solve(a, rho, h, 3, resid=ra, ctx=ctx)
+            b, rb = pitched(phi), torch.zeros_like(ra)
+            px.mg_solve(b, pitched(rho), h, 3, resid=rb, ctx=ctx)
+            torch.cuda.synchronize()
+            assert torch.equal(a, b) and torch.equal(ra, rb), (nx, ny)
+    finally:
+        ctx.close()

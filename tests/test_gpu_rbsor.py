@@ -251,48 +251,40 @@ def test_full_size_sampled(px, dtype):
         assert np.max(np.abs(got[c, c] - ref[c, c])) <= tol * scale, (j0, i0)
 
 
-RB_CHILD = r"""
-import sys, torch
-sys.path.insert(0, sys.argv[1])
-import paper_2307_07931_b300 as px
-g = torch.Generator(device="cuda"); g.manual_seed(3)
-worst = 0.0
-for (nx, ny) in [(4096, 4096), (1000, 1002), (260, 150), (16, 8), (4, 4), (124, 64), (8, 300)]:
-    h = 1.0 / nx
-    rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    # the pitched copies take the two-pass kernels (row pitch nx + 1)
-    def pitched(a):
-        b = torch.zeros(ny, nx + 1, device="cuda", dtype=torch.float32)[:, :nx]
-        b.copy_(a)
-        return b
-    pp, rp, op = pitched(phi), pitched(rho), pitched(torch.zeros_like(phi))
-    out = torch.empty_like(phi)
-    r1 = torch.zeros(11, dtype=torch.float64, device="cuda"); r2 = torch.zeros_like(r1)
-    for omega in (1.0, 1.6):
-        px.rbsor_n(pp, op, rp, h, omega, 11, r1, 1)
-        px.rbsor_n(phi, out, rho, h, omega, 11, r2, 1)
-        worst = max(worst, float((op - out).abs().max()), float((r1 - r2).abs().max()))
-print("worst", worst)
-sys.exit(0 if worst == 0.0 else 1)
-"""
-
-
-@pytest.mark.parametrize("sweeps", ["1", "2", "3", "4"])
+@pytest.mark.parametrize("sweeps", [1, 2, 3, 4])
 def test_register_wavefront_depths_bitwise(sweeps):
     """The FP32 register wavefront at 1..4 red-black sweeps per launch gives
     bitwise the states and reports of the two-pass kernels (the oracle tests
-    pin those); the depth is chosen once per process (PX_RB_SWEEPS), so each
-    runs in a child process. Sizes cover several strips and ranges, ragged
-    strips, strips wider than the grid and launches of dynamic balance."""
+    pin those); the depth is selected on a context of its own
+    (PX_OPT_RB_SWEEPS_PER_LAUNCH). Sizes cover several strips and ranges,
+    ragged strips, strips wider than the grid and launches of dynamic balance."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import os
-    import subprocess
-    import sys
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ)
-    env["PX_RB_SWEEPS"] = sweeps
-    r = subprocess.run([sys.executable, "-c", RB_CHILD, root], env=env, capture_output=True,
-                       text=True, timeout=600)
-    assert r.returncode == 0, r.stdout + r.stderr
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_RB_SWEEPS_PER_LAUNCH, sweeps)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(3)
+        for (nx, ny) in [(4096, 4096), (1000, 1002), (260, 150), (16, 8), (4, 4), (124, 64),
+                         (8, 300)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+
+            # the pitched copies take the two-pass kernels (row pitch nx + 1)
+            def pitched(a):
+                b = torch.zeros(ny, nx + 1, device="cuda", dtype=torch.float32)[:, :nx]
+                b.copy_(a)
+                return b
+            pp, rp, op = pitched(phi), pitched(rho), pitched(torch.zeros_like(phi))
+            out = torch.empty_like(phi)
+            r1 = torch.zeros(11, dtype=torch.float64, device="cuda")
+            r2 = torch.zeros_like(r1)
+            for omega in (1.0, 1.6):
+                px.rbsor_n(pp, op, rp, h, omega, 11, r1, 1, ctx=ctx)
+                px.rbsor_n(phi, out, rho, h, omega, 11, r2, 1, ctx=ctx)
+                torch.cuda.synchronize()
+                assert torch.equal(op, out) and torch.equal(r1, r2), (nx, ny, omega)
+    finally:
+        ctx.close()

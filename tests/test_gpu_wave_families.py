@@ -1,52 +1,56 @@
 """The FP32 wavefront kernel families (one-row, two-row, register at every depth) give
 bitwise the same states and residual reports as the single-sweep streaming
-kernel, which the oracle tests pin; each family runs in a child process
-because the family is chosen once per process (PX_FP32_WAVE)."""
-import os
-import subprocess
-import sys
-
+kernel, which the oracle tests pin; each family is selected on a context of
+its own through the PX_OPT_FP32_FAMILY option."""
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-
-CHILD = r"""
-import sys, torch
-sys.path.insert(0, sys.argv[1])
-import paper_2307_07931_b300 as px
-g = torch.Generator(device="cuda"); g.manual_seed(7)
-worst = 0.0
-for (nx, ny) in [(1000, 1000), (260, 150), (16, 8), (4, 4), (12, 37), (252, 40), (256, 33),
-                 (2052, 300), (124, 64)]:
-    h = 1.0 / nx
-    rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
-    o1, ot = torch.empty_like(phi), torch.empty_like(phi)
-    r1 = torch.zeros(11, dtype=torch.float64, device="cuda"); rt = torch.zeros_like(r1)
-    px.relax_n(phi, o1, rho, h, 2 / 3, 11, 1, r1, 1)
-    for tb in range(2, 9):
-        rt.zero_()
-        px.relax_n(phi, ot, rho, h, 2 / 3, 11, tb, rt, 1)
-        worst = max(worst, float((o1 - ot).abs().max()), float((r1 - rt).abs().max()))
-print("worst", worst)
-sys.exit(0 if worst == 0.0 else 1)
-"""
+FAMILIES = {"default": 0, "w1": 1, "w2": 2, "r": 3}
 
 
 @pytest.mark.parametrize("family", ["w1", "w2", "r", "default"])
 def test_family_bitwise_equals_single_sweep(family):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    env = dict(os.environ)
-    env.pop("PX_FP32_WAVE", None)
-    if family != "default":
-        env["PX_FP32_WAVE"] = family
-    r = subprocess.run([sys.executable, "-c", CHILD, ROOT], env=env, capture_output=True,
-                       text=True, timeout=600)
-    assert r.returncode == 0, r.stdout + r.stderr
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_FP32_FAMILY, FAMILIES[family])
+        assert ctx.get_option(px.PX_OPT_FP32_FAMILY) == FAMILIES[family]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(7)
+        for (nx, ny) in [(1000, 1000), (260, 150), (16, 8), (4, 4), (12, 37), (252, 40),
+                         (256, 33), (2052, 300), (124, 64)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            o1, ot = torch.empty_like(phi), torch.empty_like(phi)
+            r1 = torch.zeros(11, dtype=torch.float64, device="cuda")
+            rt = torch.zeros_like(r1)
+            px.relax_n(phi, o1, rho, h, 2 / 3, 11, 1, r1, 1, ctx=ctx)
+            for tb in range(2, 9):
+                px.relax_n(phi, ot, rho, h, 2 / 3, 11, tb, rt, 1, ctx=ctx)
+                torch.cuda.synchronize()
+                assert torch.equal(o1, ot) and torch.equal(r1, rt), (family, nx, ny, tb)
+    finally:
+        ctx.close()
+
+
+def test_option_values_are_checked():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        for opt, bad in ((px.PX_OPT_FP32_FAMILY, 4), (px.PX_OPT_FP32_FAMILY, -1),
+                         (px.PX_OPT_RB_SWEEPS_PER_LAUNCH, 5), (99, 0)):
+            with pytest.raises(px.PxError) as ei:
+                ctx.set_option(opt, bad)
+            assert ei.value.status == px.PX_EINVAL
+    finally:
+        ctx.close()
 
 
 def test_balanced_register_kernel_bitwise():
