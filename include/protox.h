@@ -431,6 +431,52 @@ px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, s
  * (Failure detection; the paper has no counterpart.) */
 px_status px_cnn_set_wait_limit(px_cnn* net, uint32_t polls);
 
+/* ----------------------------------------------------------------------------
+ * 2D Euler equations of gas dynamics by the finite-volume method: the paper's
+ * second workload (Sec. IV, the Euler result of Fig. "Euler"; Sec. V), whose
+ * many stencil and pointwise operations ProtoX fuses. The paper names no
+ * scheme; this is the textbook second-order one:
+ *   cell averages U = (rho, rho u, rho v, E) of an ideal gas,
+ *     p = (gamma - 1) (E - rho (u^2 + v^2) / 2), c = sqrt(gamma p / rho);
+ *   minmod-limited linear reconstruction of (rho, u, v, p) per direction,
+ *     slope_i = minmod(W_i - W_{i-1}, W_{i+1} - W_i), minmod(a, b) = 0 if
+ *     ab <= 0 else the argument of smaller magnitude;
+ *   Rusanov flux F = (F(W_L) + F(W_R)) / 2 - a (U_R - U_L) / 2,
+ *     a = max(|u_n| + c) of the two face states;
+ *   L(U) = -(F_{i+1/2} - F_{i-1/2}) / dx - (G_{j+1/2} - G_{j-1/2}) / dy;
+ *   SSP-RK2: U1 = U + dt L(U), U' = (U + (U1 + dt L(U1))) / 2;
+ *   dt = cfl / max over cells of (|u| + c) / dx + (|v| + c) / dy, from the
+ *     state the step starts from.
+ * Periodic in x and y. Each Runge-Kutta stage is one fused kernel (loads,
+ * primitives, slopes, face states, fluxes, divergence, update, and in the
+ * second stage the next step's max wave speed, all in one pass).
+ *
+ * Layout: four planes (rho, rho u, rho v, E) in this order, each ny rows of
+ * nx cells, x fastest, row pitch ld, the planes cs elements apart. */
+typedef struct {
+  int32_t nx, ny;  /* cells along x and y; >= 0 (0: empty, no-op) */
+  int64_t ld;      /* elements between row starts; >= nx */
+  int64_t cs;      /* elements between component planes; >= (ny - 1) * ld + nx */
+  int32_t dtype;   /* px_dtype of every plane (arithmetic in that precision) */
+  double dx, dy;   /* cell sizes, finite and > 0 */
+} px_euler_grid;
+
+/* nsteps SSP-RK2 steps from u_in into u_out (device pointers; u_out may equal
+ * u_in, otherwise they must not overlap). gamma > 1. dt_fixed > 0 fixes every
+ * step's dt; dt_fixed = 0 takes dt = cfl / (max wave speed) of each step's
+ * starting state (cfl > 0). dt_dev: NULL or nsteps doubles (device) that
+ * receive each step's dt. A non-physical state (rho <= 0 or p < 0) yields NaN
+ * there and in the state. The stage field lives in the context's scratch
+ * (grown on demand: such a call synchronises). Asynchronous. */
+px_status px_euler_step(px_ctx* ctx, const px_euler_grid* g, const void* u_in, void* u_out,
+                        double gamma, double cfl, int nsteps, double dt_fixed, double* dt_dev,
+                        void* stream);
+
+/* Conserved planes u = (rho, rho u, rho v, E) from primitive planes
+ * w = (rho, u, v, p), same layout; w and u must not overlap. Asynchronous. */
+px_status px_euler_conserved(px_ctx* ctx, const px_euler_grid* g, const void* w, void* u,
+                             double gamma, void* stream);
+
 /* Max-norm residual check (Sec. IV step 3, OL rule ||.||_inf with a = h):
  * *out_host = ||rho - L phi||_inf and, if rho_norm_host is not NULL,
  * *rho_norm_host = ||rho||_inf. Evaluated in FP64 for both dtypes (FP32 fields

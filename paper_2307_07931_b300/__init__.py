@@ -118,7 +118,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_cnn_set_wait_limit.argtypes = [_vp, ctypes.c_uint32]
     lib.px_set_option.argtypes = [_vp, i, i]
     lib.px_get_option.argtypes = [_vp, i, ip]
-    for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_set_option", "px_get_option"):
+    eg = ctypes.POINTER(EulerGrid)
+    lib.px_euler_step.argtypes = [_vp, eg, _vp, _vp, d, d, i, d, _vp, _vp]
+    lib.px_euler_conserved.argtypes = [_vp, eg, _vp, _vp, d, _vp]
+    for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_set_option", "px_get_option",
+                 "px_euler_step", "px_euler_conserved"):
         getattr(lib, name).restype = i
     for name in ("px_cnn_get_state", "px_cnn_set_state",
                  "px_cnn_create", "px_cnn_destroy", "px_cnn_get_params", "px_cnn_set_params",
@@ -422,6 +426,56 @@ def solve(phi, rho, h: float, mode: str = "plain", omega: float = 2.0 / 3.0, rto
         err.info = d
         raise err
     return d
+
+
+class EulerGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ld", ctypes.c_int64),
+                ("cs", ctypes.c_int64), ("dtype", ctypes.c_int32), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double)]
+
+
+def euler_grid_of(u, dx: float, dy: float) -> EulerGrid:
+    """px_euler_grid of a (4, ny, nx) tensor (component planes, x fastest)."""
+    import torch
+    if u.dim() != 3 or u.shape[0] != 4:
+        raise ValueError("Euler states are (4, ny, nx) tensors: rho, rho u, rho v, E")
+    if u.dtype not in (torch.float64, torch.float32) or not u.is_cuda:
+        raise ValueError("Euler states are CUDA float64 or float32 tensors")
+    if u.stride(2) != 1:
+        raise ValueError("x must be contiguous")
+    dt = PX_F64 if u.dtype == torch.float64 else PX_F32
+    return EulerGrid(int(u.shape[2]), int(u.shape[1]), int(u.stride(1)), int(u.stride(0)), dt,
+                     float(dx), float(dy))
+
+
+def euler_step(u_in, u_out, dx: float, dy: float, nsteps: int = 1, gamma: float = 1.4,
+               cfl: float = 0.4, dt_fixed: float = 0.0, dt=None, ctx: Context | None = None,
+               stream=None):
+    """nsteps fused SSP-RK2 finite-volume steps of the 2D Euler equations
+    u_in -> u_out (px_euler_step). `dt`, if given, is a float64 CUDA tensor of
+    nsteps entries receiving each step's time step."""
+    _same_layout(u_in, u_out)
+    ctx = ctx or context(u_in.device.index)
+    g = euler_grid_of(u_in, dx, dy)
+    if dt is not None:
+        import torch
+        if dt.dtype != torch.float64 or not dt.is_cuda or dt.numel() < nsteps or not dt.is_contiguous():
+            raise ValueError(f"dt must be a contiguous CUDA float64 tensor of >= {nsteps}")
+    ctx.check(load_library().px_euler_step(ctx.handle, ctypes.byref(g), _ptr(u_in), _ptr(u_out),
+                                           float(gamma), float(cfl), int(nsteps), float(dt_fixed),
+                                           _ptr(dt), _stream(stream)))
+    return u_out
+
+
+def euler_conserved(w, u, dx: float = 1.0, dy: float = 1.0, gamma: float = 1.4,
+                    ctx: Context | None = None, stream=None):
+    """Conserved planes (rho, rho u, rho v, E) from primitive planes (rho, u, v, p)."""
+    _same_layout(w, u)
+    ctx = ctx or context(w.device.index)
+    g = euler_grid_of(w, dx, dy)
+    ctx.check(load_library().px_euler_conserved(ctx.handle, ctypes.byref(g), _ptr(w), _ptr(u),
+                                                float(gamma), _stream(stream)))
+    return u
 
 
 class Batch:

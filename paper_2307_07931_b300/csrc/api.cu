@@ -238,6 +238,7 @@ px_status px_destroy(px_ctx* c) {
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->sched) cudaFree(c->sched);
   if (c->mg) cudaFree(c->mg);
+  if (c->ewave) cudaFree(c->ewave);
   delete c;
   return PX_OK;
 }
@@ -724,6 +725,118 @@ px_status px_residual_norm(px_ctx* c, const px_grid* g, const void* phi, const v
   *out_host = c->red_host[0];
   if (rho_norm_host) *rho_norm_host = c->red_host[1];
   return PX_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// 2D Euler finite-volume steps (euler.cu).
+namespace {
+
+px_status check_euler(px_ctx* c, const px_euler_grid* g, px::EulerDesc* d) {
+  if (!g) return fail(c, PX_EINVAL, "grid is NULL");
+  if (g->dtype != PX_F64 && g->dtype != PX_F32)
+    return fail(c, PX_EINVAL, "dtype %d is not PX_F64 or PX_F32", (int)g->dtype);
+  if (g->nx < 0 || g->ny < 0 || g->nx > (1 << 29) || g->ny > (1 << 29))
+    return fail(c, PX_EINVAL, "extent %d x %d not in 0..2^29", g->nx, g->ny);
+  if (g->ld < g->nx) return fail(c, PX_EINVAL, "ld %lld < nx", (long long)g->ld);
+  const int64_t plane = g->ny > 0 ? (int64_t)(g->ny - 1) * g->ld + g->nx : 0;
+  if (g->cs < plane) return fail(c, PX_EINVAL, "cs %lld < (ny - 1) * ld + nx", (long long)g->cs);
+  if (!(std::isfinite(g->dx) && g->dx > 0 && std::isfinite(g->dy) && g->dy > 0))
+    return fail(c, PX_EINVAL, "dx and dy must be finite and > 0");
+  if ((double)g->cs * 4.0 * elem_size(g->dtype) > 9.0e18) return fail(c, PX_EINVAL, "field too large");
+  d->nx = g->nx;
+  d->ny = g->ny;
+  d->ld = g->ld;
+  d->cs = g->cs;
+  d->dtype = g->dtype;
+  d->dx = g->dx;
+  d->dy = g->dy;
+  return PX_OK;
+}
+
+size_t euler_span(const px::EulerDesc& d) {
+  if (d.nx == 0 || d.ny == 0) return 0;
+  return (size_t)((3 * d.cs + (int64_t)(d.ny - 1) * d.ld + d.nx) * (int64_t)elem_size(d.dtype));
+}
+
+}  // namespace
+
+extern "C" {
+
+px_status px_euler_step(px_ctx* c, const px_euler_grid* g, const void* u_in, void* u_out,
+                        double gamma, double cfl, int nsteps, double dt_fixed, double* dt_dev,
+                        void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::EulerDesc d;
+  px_status s = check_euler(c, g, &d);
+  if (s != PX_OK) return s;
+  if (!(std::isfinite(gamma) && gamma > 1.0)) return fail(c, PX_EINVAL, "gamma must be > 1");
+  if (nsteps < 0) return fail(c, PX_EINVAL, "nsteps %d < 0", nsteps);
+  if (!(std::isfinite(dt_fixed) && dt_fixed >= 0.0)) return fail(c, PX_EINVAL, "dt_fixed must be >= 0");
+  if (dt_fixed == 0.0 && !(std::isfinite(cfl) && cfl > 0.0))
+    return fail(c, PX_EINVAL, "cfl must be finite and > 0 when dt_fixed is 0");
+  const size_t span = euler_span(d);
+  if (span == 0 || nsteps == 0) {
+    if (span > 0 && u_in != u_out) {
+      if (!u_in || !u_out) return fail(c, PX_EINVAL, "NULL field pointer");
+      if (overlap(u_in, u_out, span)) return fail(c, PX_EINVAL, "u_in and u_out overlap");
+      DeviceScope ds(c->device);
+      cudaError_t e = cudaMemcpyAsync(u_out, u_in, span, cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copy");
+    }
+    return PX_OK;
+  }
+  if (!u_in || !u_out) return fail(c, PX_EINVAL, "NULL field pointer");
+  if (u_in != u_out && overlap(u_in, u_out, span))
+    return fail(c, PX_EINVAL, "u_in and u_out overlap without being equal");
+  if (dt_dev && overlap2(dt_dev, sizeof(double) * (size_t)nsteps, u_out, span))
+    return fail(c, PX_EINVAL, "dt_dev overlaps u_out");
+  DeviceScope ds(c->device);
+  s = ensure_scratch(c, span);
+  if (s != PX_OK) return s;
+  if (!c->ewave) {
+    cudaError_t e = cudaMalloc(&c->ewave, 2 * sizeof(double));
+    if (e != cudaSuccess) {
+      c->ewave = nullptr;
+      return cuda_fail(c, e, "wave-speed slots");
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool adaptive = dt_fixed == 0.0;
+  if (adaptive) {
+    cudaError_t e = cudaMemsetAsync(c->ewave, 0, sizeof(double), st);
+    if (e == cudaSuccess) e = px::launch_euler_wave(d, u_in, gamma, c->ewave, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "wave-speed launch");
+  }
+  const void* src = u_in;
+  for (int k = 0; k < nsteps; ++k) {
+    double* cur = adaptive ? c->ewave + (k & 1) : nullptr;
+    double* next = adaptive ? c->ewave + ((k + 1) & 1) : nullptr;
+    cudaError_t e = px::launch_euler_step(d, src, u_out, c->scratch, gamma, cfl, dt_fixed, cur,
+                                          next, dt_dev ? dt_dev + k : nullptr, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "Euler step launch");
+    src = u_out;
+  }
+  return PX_OK;
+}
+
+px_status px_euler_conserved(px_ctx* c, const px_euler_grid* g, const void* w, void* u,
+                             double gamma, void* stream) {
+  if (!c) return PX_EINVAL;
+  c->err.clear();
+  px::EulerDesc d;
+  px_status s = check_euler(c, g, &d);
+  if (s != PX_OK) return s;
+  if (!(std::isfinite(gamma) && gamma > 1.0)) return fail(c, PX_EINVAL, "gamma must be > 1");
+  const size_t span = euler_span(d);
+  if (span == 0) return PX_OK;
+  if (!w || !u) return fail(c, PX_EINVAL, "NULL field pointer");
+  if (overlap(w, u, span)) return fail(c, PX_EINVAL, "w and u overlap");
+  DeviceScope ds(c->device);
+  cudaError_t e = px::launch_euler_conserved(d, w, u, gamma, (cudaStream_t)stream);
+  return e == cudaSuccess ? PX_OK : cuda_fail(c, e, "conversion launch");
 }
 
 }  // extern "C"

@@ -1,0 +1,365 @@
+// 2D Euler finite-volume step (the paper's second workload: Sec. IV, the
+// Euler result of Fig. "Euler"; Sec. V), fused: one kernel per Runge-Kutta
+// stage does what an operator library runs as separate passes over memory
+// (primitive variables, limited slopes, face states, Rusanov fluxes, flux
+// divergence, the stage update and, in the second stage, the maximum wave
+// speed of the new state for the next step's time step).
+//
+// Scheme (the paper gives none; the textbook second-order one): cell averages
+// U = (rho, rho u, rho v, E) of an ideal gas, p = (gamma - 1)(E - rho |u|^2 / 2);
+// minmod-limited piecewise-linear reconstruction of (rho, u, v, p); Rusanov
+// flux F = (F(W_L) + F(W_R)) / 2 - a (U_R - U_L) / 2 with
+// a = max(|u_n| + c) over the two face states; SSP-RK2
+//   U1 = U + dt L(U),   U' = (U + (U1 + dt L(U1))) / 2,
+// dt = cfl / max((|u| + c) / dx + (|v| + c) / dy) over the cells of U.
+//
+// Layout: four component planes (rho, rho u, rho v, E), each ny rows of nx
+// cells with row pitch ld, planes cs elements apart; periodic in x and y.
+//
+// Tiling: a CTA of 256 threads computes a TX x TY = 32 x 16 tile. It loads the
+// tile and a two-cell periodic halo, converts it to primitives in shared
+// memory, computes each of the (TX + 1) TY x-face and TX (TY + 1) y-face fluxes
+// once into shared memory, then updates its cells from the flux differences.
+// Grid-stride over tiles, one resident wave of CTAs.
+#include "px_internal.cuh"
+
+#include <algorithm>
+
+namespace px {
+namespace {
+
+constexpr int kETX = 32, kETY = 16, kEHalo = 2;
+constexpr int kEWX = kETX + 2 * kEHalo, kEWY = kETY + 2 * kEHalo;  // 36 x 20
+constexpr int kEThreads = 256;
+
+template <typename T>
+struct ESmem {
+  T w[4][kEWY][kEWX];        // primitives rho, u, v, p of the tile and its halo
+  T fx[4][kETY][kETX + 1];   // x-face fluxes: fx[.][j][k] at face k - 1/2 of row j
+  T fy[4][kETY + 1][kETX];   // y-face fluxes: fy[.][j][i] at face j - 1/2 of column i
+};
+
+template <typename T> __device__ __forceinline__ T tsqrt(T v);
+template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
+
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  return a * b <= T(0) ? T(0) : (fabs(a) < fabs(b) ? a : b);
+}
+
+template <typename T>
+struct EParams {
+  const T* u0;     // state at the start of the step
+  const T* u1;     // stage-1 state (stage 2 only)
+  T* out;
+  int nx, ny;
+  int64_t ld, cs;
+  T gamma, gm1, igm1;  // gamma, gamma - 1, 1 / (gamma - 1)
+  T idx, idy;          // 1 / dx, 1 / dy
+  double dx, dy;
+  double cfl, dt_fixed;
+  double* wave_cur;    // max wave speed of u0 (dt source when dt_fixed == 0)
+  double* wave_next;   // stage 1 zeroes it, stage 2 folds the new state's max into it
+  double* dt_out;      // this step's dt (stage 1 writes it) or null
+  int tiles_x, ntiles;
+};
+
+// Rusanov flux through one face from the four cells a, b | c, d along the face
+// normal (b | c straddle the face). Component order rho, u, v, p; `nx_dir`
+// selects the normal (u for x faces, v for y faces).
+template <typename T, bool kXFace>
+__device__ __forceinline__ void face_flux(const T (&a)[4], const T (&b)[4], const T (&c)[4],
+                                          const T (&d)[4], T gamma, T igm1, T (&f)[4]) {
+  T L[4], R[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T sb = minmod(b[q] - a[q], c[q] - b[q]);
+    const T sc = minmod(c[q] - b[q], d[q] - c[q]);
+    L[q] = b[q] + T(0.5) * sb;
+    R[q] = c[q] - T(0.5) * sc;
+  }
+  const T unL = kXFace ? L[1] : L[2], unR = kXFace ? R[1] : R[2];
+  const T EL = L[3] * igm1 + T(0.5) * L[0] * (L[1] * L[1] + L[2] * L[2]);
+  const T ER = R[3] * igm1 + T(0.5) * R[0] * (R[1] * R[1] + R[2] * R[2]);
+  const T cL = tsqrt(gamma * L[3] / L[0]), cR = tsqrt(gamma * R[3] / R[0]);
+  const T am = fmax(fabs(unL) + cL, fabs(unR) + cR);
+  const T mL = L[0] * unL, mR = R[0] * unR;  // mass fluxes
+  const T FL1 = mL * L[1] + (kXFace ? L[3] : T(0)), FR1 = mR * R[1] + (kXFace ? R[3] : T(0));
+  const T FL2 = mL * L[2] + (kXFace ? T(0) : L[3]), FR2 = mR * R[2] + (kXFace ? T(0) : R[3]);
+  const T FL3 = unL * (EL + L[3]), FR3 = unR * (ER + R[3]);
+  f[0] = T(0.5) * (mL + mR) - T(0.5) * am * (R[0] - L[0]);
+  f[1] = T(0.5) * (FL1 + FR1) - T(0.5) * am * (R[0] * R[1] - L[0] * L[1]);
+  f[2] = T(0.5) * (FL2 + FR2) - T(0.5) * am * (R[0] * R[2] - L[0] * L[2]);
+  f[3] = T(0.5) * (FL3 + FR3) - T(0.5) * am * (ER - EL);
+}
+
+template <typename T>
+__device__ __forceinline__ double wave_speed(T r, T mx, T my, T e, T gamma, T gm1, T idx, T idy) {
+  const T ir = T(1) / r;
+  const T u = mx * ir, v = my * ir;
+  const T p = gm1 * (e - T(0.5) * r * (u * u + v * v));
+  const T c = tsqrt(gamma * p / r);
+  return (double)((fabs(u) + c) * idx + (fabs(v) + c) * idy);
+}
+
+__device__ __forceinline__ uint64_t dbits(double v) {
+  return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+template <typename T, int kStage>
+__global__ void __launch_bounds__(kEThreads)
+euler_stage_k(EParams<T> P) {
+  extern __shared__ __align__(16) unsigned char esm_raw[];
+  ESmem<T>& S = *reinterpret_cast<ESmem<T>*>(esm_raw);
+  __shared__ uint64_t wmax_s[kEThreads / 32];
+  const int tid = threadIdx.x;
+  // this step's dt
+  double dtd = P.dt_fixed;
+  if (!(dtd > 0.0)) dtd = P.cfl / *P.wave_cur;
+  const T dt = (T)dtd;
+  if (kStage == 1 && blockIdx.x == 0 && tid == 0) {
+    if (P.dt_out) *P.dt_out = dtd;
+    if (P.wave_next) *P.wave_next = 0.0;
+  }
+  const T* src = kStage == 1 ? P.u0 : P.u1;
+  const bool near_x = P.nx >= kEWX, near_y = P.ny >= kEWY;
+  uint64_t wm = 0;
+
+  for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+    const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
+    const int x0 = tx * kETX, y0 = ty * kETY;
+    __syncthreads();  // the previous tile's fluxes are consumed
+    // ---- load the tile + halo, convert to primitives
+    for (int q = tid; q < kEWX * kEWY; q += kEThreads) {
+      const int ly = q / kEWX, lx = q - ly * kEWX;
+      const int gx = near_x ? wrap1(x0 + lx - kEHalo, P.nx) : wrapn(x0 + lx - kEHalo, P.nx);
+      const int gy = near_y ? wrap1(y0 + ly - kEHalo, P.ny) : wrapn(y0 + ly - kEHalo, P.ny);
+      const int64_t o = (int64_t)gy * P.ld + gx;
+      const T r = __ldg(src + o), mx = __ldg(src + P.cs + o), my = __ldg(src + 2 * P.cs + o),
+              e = __ldg(src + 3 * P.cs + o);
+      const T ir = T(1) / r;
+      const T u = mx * ir, v = my * ir;
+      S.w[0][ly][lx] = r;
+      S.w[1][ly][lx] = u;
+      S.w[2][ly][lx] = v;
+      S.w[3][ly][lx] = P.gm1 * (e - T(0.5) * r * (u * u + v * v));
+    }
+    __syncthreads();
+    // ---- face fluxes: x faces (kETX + 1) x kETY, then y faces kETX x (kETY + 1)
+    constexpr int kNX = (kETX + 1) * kETY, kNY = kETX * (kETY + 1);
+    for (int q = tid; q < kNX + kNY; q += kEThreads) {
+      T a[4], b[4], c[4], d[4], f[4];
+      if (q < kNX) {
+        const int j = q / (kETX + 1), k = q - j * (kETX + 1);  // face k - 1/2 of row j
+        const int yy = j + kEHalo, xb = k + kEHalo - 1;           // cell left of the face
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = S.w[m][yy][xb - 1];
+          b[m] = S.w[m][yy][xb];
+          c[m] = S.w[m][yy][xb + 1];
+          d[m] = S.w[m][yy][xb + 2];
+        }
+        face_flux<T, true>(a, b, c, d, P.gamma, P.igm1, f);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) S.fx[m][j][k] = f[m];
+      } else {
+        const int r = q - kNX;
+        const int j = r / kETX, i = r - j * kETX;                // face j - 1/2 of column i
+        const int xx = i + kEHalo, yb = j + kEHalo - 1;          // cell below the face
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          a[m] = S.w[m][yb - 1][xx];
+          b[m] = S.w[m][yb][xx];
+          c[m] = S.w[m][yb + 1][xx];
+          d[m] = S.w[m][yb + 2][xx];
+        }
+        face_flux<T, false>(a, b, c, d, P.gamma, P.igm1, f);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) S.fy[m][j][i] = f[m];
+      }
+    }
+    __syncthreads();
+    // ---- update the tile's cells
+    for (int q = tid; q < kETX * kETY; q += kEThreads) {
+      const int j = q / kETX, i = q - j * kETX;
+      const int gx = x0 + i, gy = y0 + j;
+      if (gx >= P.nx || gy >= P.ny) continue;
+      const int64_t o = (int64_t)gy * P.ld + gx;
+      T nv[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const T Lm = -(S.fx[m][j][i + 1] - S.fx[m][j][i]) * P.idx -
+                     (S.fy[m][j + 1][i] - S.fy[m][j][i]) * P.idy;
+        const T um = __ldg(src + m * P.cs + o);
+        if (kStage == 1) {
+          nv[m] = um + dt * Lm;
+        } else {
+          nv[m] = T(0.5) * (__ldg(P.u0 + m * P.cs + o) + (um + dt * Lm));
+        }
+        P.out[m * P.cs + o] = nv[m];
+      }
+      if (kStage == 2 && P.wave_next)
+        wm = umax(wm, dbits(wave_speed(nv[0], nv[1], nv[2], nv[3], P.gamma, P.gm1, P.idx, P.idy)));
+    }
+  }
+  if (kStage == 2 && P.wave_next) {
+    wm = warp_max(wm);
+    if ((tid & 31) == 0) wmax_s[tid >> 5] = wm;
+    __syncthreads();
+    if (tid == 0) {
+      uint64_t m = 0;
+#pragma unroll
+      for (int w = 0; w < kEThreads / 32; ++w) m = umax(m, wmax_s[w]);
+      atomic_max_bits(P.wave_next, m);
+    }
+  }
+}
+
+// Max wave speed of a state (the first step's dt source).
+template <typename T>
+__global__ void __launch_bounds__(kEThreads)
+euler_wave_k(const T* __restrict__ u, int nx, int ny, int64_t ld, int64_t cs, T gamma, T gm1,
+             T idx, T idy, double* slot) {
+  __shared__ uint64_t sm[kEThreads / 32];
+  uint64_t m = 0;
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t q = blockIdx.x * (int64_t)kEThreads + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * kEThreads) {
+    const int64_t y = q / nx, x = q - y * nx;
+    const int64_t o = y * ld + x;
+    m = umax(m, dbits(wave_speed(u[o], u[cs + o], u[2 * cs + o], u[3 * cs + o], gamma, gm1, idx, idy)));
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < kEThreads / 32; ++w) t = umax(t, sm[w]);
+    atomic_max_bits(slot, t);
+  }
+}
+
+// Conserved variables from primitives (rho, u, v, p), same layout.
+template <typename T>
+__global__ void euler_conserved_k(const T* __restrict__ w, T* __restrict__ u, int nx, int ny,
+                                  int64_t ld, int64_t cs, T igm1) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = q / nx, x = q - y * nx;
+    const int64_t o = y * ld + x;
+    const T r = w[o], vx = w[cs + o], vy = w[2 * cs + o], p = w[3 * cs + o];
+    u[o] = r;
+    u[cs + o] = r * vx;
+    u[2 * cs + o] = r * vy;
+    u[3 * cs + o] = p * igm1 + T(0.5) * r * (vx * vx + vy * vy);
+  }
+}
+
+template <typename T>
+cudaError_t euler_setup_t() {
+  static bool done_by_dev[64] = {};
+  bool& done = done_by_dev[dev_index()];
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(euler_stage_k<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(ESmem<T>));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(euler_stage_k<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ESmem<T>));
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <typename T>
+cudaError_t euler_step_t(const EulerDesc& g, const T* u0, T* out, T* s1, double gamma, double cfl,
+                         double dt_fixed, double* wave_cur, double* wave_next, double* dt_out,
+                         cudaStream_t st) {
+  cudaError_t e = euler_setup_t<T>();
+  if (e != cudaSuccess) return e;
+  static int occ_by_dev[64] = {};
+  int& occ = occ_by_dev[dev_index()];
+  if (occ == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, euler_stage_k<T, 2>, kEThreads,
+                                                      sizeof(ESmem<T>));
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+  }
+  EParams<T> P;
+  P.u0 = u0;
+  P.u1 = s1;
+  P.nx = g.nx;
+  P.ny = g.ny;
+  P.ld = g.ld;
+  P.cs = g.cs;
+  P.gamma = (T)gamma;
+  P.gm1 = (T)(gamma - 1.0);
+  P.igm1 = (T)(1.0 / (gamma - 1.0));
+  P.idx = (T)(1.0 / g.dx);
+  P.idy = (T)(1.0 / g.dy);
+  P.dx = g.dx;
+  P.dy = g.dy;
+  P.cfl = cfl;
+  P.dt_fixed = dt_fixed;
+  P.wave_cur = wave_cur;
+  P.wave_next = wave_next;
+  P.dt_out = dt_out;
+  P.tiles_x = (g.nx + kETX - 1) / kETX;
+  const int64_t tiles = (int64_t)P.tiles_x * ((g.ny + kETY - 1) / kETY);
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  P.ntiles = (int)tiles;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)occ * device_sm_count());
+  // stage 1: u0 -> s1
+  P.out = s1;
+  euler_stage_k<T, 1><<<grid, kEThreads, sizeof(ESmem<T>), st>>>(P);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // stage 2: (u0, s1) -> out, max wave speed of out -> wave_next
+  P.out = out;
+  P.dt_out = nullptr;
+  euler_stage_k<T, 2><<<grid, kEThreads, sizeof(ESmem<T>), st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_euler_wave(const EulerDesc& g, const void* u, double gamma, double* slot,
+                              cudaStream_t st) {
+  const int64_t n = (int64_t)g.nx * g.ny;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kEThreads - 1) / kEThreads,
+                                                                 (int64_t)device_sm_count() * 8));
+  if (g.dtype == 0)
+    euler_wave_k<double><<<blocks, kEThreads, 0, st>>>((const double*)u, g.nx, g.ny, g.ld, g.cs,
+                                                       gamma, gamma - 1.0, 1.0 / g.dx, 1.0 / g.dy, slot);
+  else
+    euler_wave_k<float><<<blocks, kEThreads, 0, st>>>((const float*)u, g.nx, g.ny, g.ld, g.cs,
+                                                      (float)gamma, (float)(gamma - 1.0),
+                                                      (float)(1.0 / g.dx), (float)(1.0 / g.dy), slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_euler_step(const EulerDesc& g, const void* u0, void* out, void* s1, double gamma,
+                              double cfl, double dt_fixed, double* wave_cur, double* wave_next,
+                              double* dt_out, cudaStream_t st) {
+  if (g.dtype == 0)
+    return euler_step_t<double>(g, (const double*)u0, (double*)out, (double*)s1, gamma, cfl,
+                                dt_fixed, wave_cur, wave_next, dt_out, st);
+  return euler_step_t<float>(g, (const float*)u0, (float*)out, (float*)s1, gamma, cfl, dt_fixed,
+                             wave_cur, wave_next, dt_out, st);
+}
+
+cudaError_t launch_euler_conserved(const EulerDesc& g, const void* w, void* u, double gamma,
+                                   cudaStream_t st) {
+  const int64_t n = (int64_t)g.nx * g.ny;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256,
+                                                                 (int64_t)device_sm_count() * 8));
+  if (g.dtype == 0)
+    euler_conserved_k<double><<<blocks, 256, 0, st>>>((const double*)w, (double*)u, g.nx, g.ny,
+                                                      g.ld, g.cs, 1.0 / (gamma - 1.0));
+  else
+    euler_conserved_k<float><<<blocks, 256, 0, st>>>((const float*)w, (float*)u, g.nx, g.ny, g.ld,
+                                                     g.cs, (float)(1.0 / (gamma - 1.0)));
+  return cudaGetLastError();
+}
+
+}  // namespace px

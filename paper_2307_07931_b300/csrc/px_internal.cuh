@@ -145,6 +145,28 @@ cudaError_t launch_residual_norm(const FieldDesc& f, const void* phi, const void
 cudaError_t launch_copy_field(const FieldDesc& f, const void* src, void* dst,
                               cudaStream_t st);
 
+// 2D Euler finite-volume fields (euler.cu): four component planes (rho,
+// rho u, rho v, E) of ny rows of nx cells, row pitch ld, plane pitch cs.
+struct EulerDesc {
+  int nx, ny;
+  int64_t ld, cs;
+  int dtype;  // 0 = f64, 1 = f32
+  double dx, dy;
+};
+// Max over cells of (|u| + c) / dx + (|v| + c) / dy folded into *slot (atomic max).
+cudaError_t launch_euler_wave(const EulerDesc& g, const void* u, double gamma, double* slot,
+                              cudaStream_t st);
+// One SSP-RK2 step u0 -> out through the stage field s1 (two launches). dt is
+// dt_fixed if > 0, else cfl / *wave_cur; stage 1 writes dt to *dt_out (if not
+// null) and zeroes *wave_next, stage 2 folds the new state's max wave speed
+// into *wave_next (if not null). out may equal u0.
+cudaError_t launch_euler_step(const EulerDesc& g, const void* u0, void* out, void* s1, double gamma,
+                              double cfl, double dt_fixed, double* wave_cur, double* wave_next,
+                              double* dt_out, cudaStream_t st);
+// Conserved variables from primitive planes (rho, u, v, p).
+cudaError_t launch_euler_conserved(const EulerDesc& g, const void* w, void* u, double gamma,
+                                   cudaStream_t st);
+
 int device_sm_count();
 // Current device index clamped to 0..63, for the per-device caches of the
 // launchers (occupancy, function attributes, symbol addresses).
@@ -181,6 +203,7 @@ struct px_ctx {
   int sched_cap = 0;
   void* mg = nullptr;        // multigrid levels 1..L-1: right-hand side and two states each
   size_t mg_bytes = 0;
+  double* ewave = nullptr;   // Euler: max wave speeds of the current and next state
   int opt_fp32_family = 0;   // PX_OPT_FP32_FAMILY (0 = automatic)
   int opt_rb_sweeps = 0;     // PX_OPT_RB_SWEEPS_PER_LAUNCH (0 = automatic)
   std::string err;

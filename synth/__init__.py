@@ -195,3 +195,31 @@ def random_field3(rng: np.random.Generator, nx: int, ny: int, nz: int,
     """Uniform(-1, 1) white 3D field of shape (nz, ny, nx) (tests only)."""
     a = rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
     return a - a.mean() if zero_mean else a
+
+
+def euler_kh_primitives(nx: int, ny: int, seed: int | None = None, delta: float = 0.01,
+                        nmodes: int = 8, kmax: int = 8) -> np.ndarray:
+    """Primitive planes (rho, u, v, p), shape (4, ny, nx), of a periodic double
+    shear layer on the unit square (cell centres): rho = 1 + b(y) and
+    u = b(y) - 1/2 with b(y) = (tanh((y - 1/4)/delta) - tanh((y - 3/4)/delta))/2,
+    p = 2.5, and v a seeded sum of `nmodes` sine modes in x (k in 1..kmax,
+    N(0, 1) amplitudes scaled to 0.01) localised at the two layers by
+    Gaussians of width 0.05."""
+    seed = workload_seed(6) if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = (np.arange(nx, dtype=np.float64) + 0.5) / nx
+    y = (np.arange(ny, dtype=np.float64) + 0.5) / ny
+    b = 0.5 * (np.tanh((y - 0.25) / delta) - np.tanh((y - 0.75) / delta))
+    amps = 0.01 * rng.standard_normal(nmodes)
+    ks = rng.integers(1, kmax + 1, size=nmodes)
+    phases = rng.uniform(0.0, 2.0 * np.pi, size=nmodes)
+    vx = np.zeros(nx)
+    for a, k, ph in zip(amps, ks, phases):
+        vx += a * np.sin(2.0 * np.pi * k * x + ph)
+    loc = np.exp(-((y - 0.25) / 0.05) ** 2) + np.exp(-((y - 0.75) / 0.05) ** 2)
+    W = np.empty((4, ny, nx))
+    W[0] = (1.0 + b)[:, None]
+    W[1] = (b - 0.5)[:, None]
+    W[2] = loc[:, None] * vx[None, :]
+    W[3] = 2.5
+    return W
