@@ -139,6 +139,7 @@ def test_uniform_state_preserved_and_conservation(px, dtype):
     rng = np.random.default_rng(8)
     U0 = blocky_state(rng, 64, 96)
     u = torch.from_numpy(U0).to(dtype).cuda()
+    out = torch.empty_like(u)
     px.euler_step(u, out, 1 / 96, 1 / 64, 10)
     torch.cuda.synchronize()
     s0 = u.double().sum(dim=(1, 2)).cpu().numpy()
