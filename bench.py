@@ -454,6 +454,56 @@ def bench_c3(px, torch, budget_s: float = 20.0, n: int = 8192):
     return out
 
 
+EULER_KERNEL = {"f32": "euler_stage_k<float,1|2>", "f64": "euler_stage_k<double,1|2>"}
+# algorithmic elements per cell and step: stage 1 reads U and writes U1 (8),
+# stage 2 reads U and U1 and writes U' (12)
+EULER_ELEMS_PER_STEP = 20
+
+
+def bench_euler(px, torch, hbm_peak, steps, warmup, n=8192, nsteps=10):
+    """The Euler row: 8192^2 periodic double shear layer (synth.euler_kh_primitives),
+    gamma = 1.4, cfl = 0.4, `nsteps` adaptive SSP-RK2 steps per call (two fused
+    stage launches per step, the max wave speed of each new state folded into
+    the second), FP32 and FP64 storage and arithmetic."""
+    import synth
+    W = synth.euler_kh_primitives(n, n)
+    out = {"grid": n, "steps_per_call": nsteps, "gamma": 1.4, "cfl": 0.4,
+           "workload": "double shear layer, rho 1..2, u +-0.5, p 2.5, seeded v modes"}
+    st = torch.cuda.current_stream()
+    cells = n * n
+    for dt_, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        w = torch.from_numpy(W).to(tdt).cuda()
+        u = torch.empty_like(w)
+        px.euler_conserved(w, u)
+        del w
+        o = torch.empty_like(u)
+        dts = torch.zeros(nsteps, dtype=torch.float64, device="cuda")
+
+        def call():
+            px.euler_step(u, o, 1.0 / n, 1.0 / n, nsteps, dt=dts)
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            a.record(st)
+            call()
+            b.record(st)
+        torch.cuda.synchronize()
+        t = statistics.median(a.elapsed_time(b) / 1000.0 for a, b in evs)
+        es = 4 if dt_ == "f32" else 8
+        gbs = EULER_ELEMS_PER_STEP * es * cells * nsteps / t / 1e9
+        out[dt_] = {"kernel": EULER_KERNEL[dt_], "ms_per_call": 1000 * t,
+                    "ms_per_step": 1000 * t / nsteps, "Gcell_s": cells * nsteps / t / 1e9,
+                    "algo_GB_s": gbs, "hbm_frac": gbs / hbm_peak,
+                    "launches_per_call": 2 * nsteps + 1,
+                    "t_reached": float(dts.sum()), "finite": bool(torch.isfinite(o).all())}
+        del u, o
+        torch.cuda.empty_cache()
+    return out
+
+
 def load_trained_network(px):
     """The learned-guess network trained by paper_2307_07931_b300.learned, if its
     weights ship with the package (data/learned_guess_params.npy)."""
@@ -705,6 +755,7 @@ def run_gpu(args, world, rank, local):
     batched = bench_batched(px, torch, K, W) if not args.quick else None
     ttt = bench_time_to_tol(px, torch) if not args.quick else None
     c3 = bench_c3(px, torch, budget_s=args.c3_budget) if not args.quick else None
+    euler = bench_euler(px, torch, hbm_peak, min(K, 5), min(W, 3))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -759,6 +810,7 @@ def run_gpu(args, world, rank, local):
             line["time_to_1e-8"] = ttt
         if c3 is not None:
             line["refine_8192"] = c3
+        line["euler"] = euler
         if cpu is not None:
             line["cpu_baseline"] = cpu
         # compact digest of the extra blocks, last in the line so that a

@@ -32,16 +32,30 @@ constexpr int kETX = 32, kETY = 16, kEHalo = 2;
 constexpr int kEWX = kETX + 2 * kEHalo, kEWY = kETY + 2 * kEHalo;  // 36 x 20
 constexpr int kEThreads = 256;
 
+constexpr int kEWP = kEWX + 1;  // row pitch 37: the x-face threads of a warp (4 rows x 8
+                                // segments 4 cells apart) hit 32 different banks
 template <typename T>
 struct ESmem {
-  T w[4][kEWY][kEWX];        // primitives rho, u, v, p of the tile and its halo
+  T raw[4][kEWY * kEWX];     // conserved values of the next tile + halo (cp.async prefetch)
+  T w[4][kEWY][kEWP];        // primitives rho, u, v, p of the tile and its halo
   T fx[4][kETY][kETX + 1];   // x-face fluxes: fx[.][j][k] at face k - 1/2 of row j
   T fy[4][kETY + 1][kETX];   // y-face fluxes: fy[.][j][i] at face j - 1/2 of column i
 };
 
-template <typename T> __device__ __forceinline__ T tsqrt(T v);
-template <> __device__ __forceinline__ float tsqrt<float>(float v) { return sqrtf(v); }
-template <> __device__ __forceinline__ double tsqrt<double>(double v) { return sqrt(v); }
+// Reciprocal and sound speed sqrt(g p / rho) (g p passed as gp). FP64 takes
+// the IEEE operations; FP32 takes the hardware approximations (relative error
+// about 2^-22, far below the storage's own rounding of the fluxes):
+// c = gp rsqrt(gp rho), no division and no square root.
+template <typename T> __device__ __forceinline__ T recip(T v);
+template <> __device__ __forceinline__ float recip<float>(float v) { return __fdividef(1.0f, v); }
+template <> __device__ __forceinline__ double recip<double>(double v) { return 1.0 / v; }
+template <typename T> __device__ __forceinline__ T sound(T gp, T rho);
+template <> __device__ __forceinline__ float sound<float>(float gp, float rho) {
+  return gp * rsqrtf(gp * rho);
+}
+template <> __device__ __forceinline__ double sound<double>(double gp, double rho) {
+  return sqrt(gp / rho);
+}
 
 template <typename T>
 __device__ __forceinline__ T minmod(T a, T b) {
@@ -65,24 +79,22 @@ struct EParams {
   int tiles_x, ntiles;
 };
 
-// Rusanov flux through one face from the four cells a, b | c, d along the face
-// normal (b | c straddle the face). Component order rho, u, v, p; `nx_dir`
-// selects the normal (u for x faces, v for y faces).
+// Rusanov flux through one face from the cells b | c that straddle it and
+// their limited slopes sb, sc along the face normal. Component order rho, u,
+// v, p; kXFace selects the normal velocity (u for x faces, v for y faces).
 template <typename T, bool kXFace>
-__device__ __forceinline__ void face_flux(const T (&a)[4], const T (&b)[4], const T (&c)[4],
-                                          const T (&d)[4], T gamma, T igm1, T (&f)[4]) {
+__device__ __forceinline__ void face_flux(const T (&b)[4], const T (&sb)[4], const T (&c)[4],
+                                          const T (&sc)[4], T gamma, T igm1, T (&f)[4]) {
   T L[4], R[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const T sb = minmod(b[q] - a[q], c[q] - b[q]);
-    const T sc = minmod(c[q] - b[q], d[q] - c[q]);
-    L[q] = b[q] + T(0.5) * sb;
-    R[q] = c[q] - T(0.5) * sc;
+    L[q] = b[q] + T(0.5) * sb[q];
+    R[q] = c[q] - T(0.5) * sc[q];
   }
   const T unL = kXFace ? L[1] : L[2], unR = kXFace ? R[1] : R[2];
   const T EL = L[3] * igm1 + T(0.5) * L[0] * (L[1] * L[1] + L[2] * L[2]);
   const T ER = R[3] * igm1 + T(0.5) * R[0] * (R[1] * R[1] + R[2] * R[2]);
-  const T cL = tsqrt(gamma * L[3] / L[0]), cR = tsqrt(gamma * R[3] / R[0]);
+  const T cL = sound(gamma * L[3], L[0]), cR = sound(gamma * R[3], R[0]);
   const T am = fmax(fabs(unL) + cL, fabs(unR) + cR);
   const T mL = L[0] * unL, mR = R[0] * unR;  // mass fluxes
   const T FL1 = mL * L[1] + (kXFace ? L[3] : T(0)), FR1 = mR * R[1] + (kXFace ? R[3] : T(0));
@@ -94,13 +106,74 @@ __device__ __forceinline__ void face_flux(const T (&a)[4], const T (&b)[4], cons
   f[3] = T(0.5) * (FL3 + FR3) - T(0.5) * am * (ER - EL);
 }
 
+// Fluxes of a run of consecutive faces along one line of the shared tile:
+// faces f0 .. f0 + nf - 1, face f lying between the cells at line positions
+// f + 1 and f + 2 (position p of the line is element base + p * step). The
+// cell window slides along the line, so each cell is read once and its slope
+// computed once for the run. Flux of face f goes to out + f * ostep.
+template <typename T, bool kXFace>
+__device__ __forceinline__ void face_run(const T* base, int step, int plane, int f0, int nf,
+                                         T* out, int ostep, int oplane, T gamma, T igm1) {
+  T w0[4], w1[4], w2[4], s1[4], s2[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    w0[m] = base[m * plane + f0 * step];
+    w1[m] = base[m * plane + (f0 + 1) * step];
+    w2[m] = base[m * plane + (f0 + 2) * step];
+    s1[m] = minmod(w1[m] - w0[m], w2[m] - w1[m]);
+  }
+  for (int k = 0; k < nf; ++k) {
+    const int f = f0 + k;
+    T w3[4], fl[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      w3[m] = base[m * plane + (f + 3) * step];
+      s2[m] = minmod(w2[m] - w1[m], w3[m] - w2[m]);
+    }
+    face_flux<T, kXFace>(w1, s1, w2, s2, gamma, igm1, fl);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      out[m * oplane + f * ostep] = fl[m];
+      w1[m] = w2[m];
+      w2[m] = w3[m];
+      s1[m] = s2[m];
+    }
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ double wave_speed(T r, T mx, T my, T e, T gamma, T gm1, T idx, T idy) {
-  const T ir = T(1) / r;
+  const T ir = recip(r);
   const T u = mx * ir, v = my * ir;
   const T p = gm1 * (e - T(0.5) * r * (u * u + v * v));
-  const T c = tsqrt(gamma * p / r);
+  const T c = sound(gamma * p, r);
   return (double)((fabs(u) + c) * idx + (fabs(v) + c) * idy);
+}
+
+template <int kBytes>
+__device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gsrc), "n"(kBytes)
+               : "memory");
+}
+
+// Issue the copies of one tile and its two-cell periodic halo (four planes)
+// into S.raw, one commit group.
+template <typename T>
+__device__ __forceinline__ void prefetch_tile(ESmem<T>& S, const T* src, int tile, int tiles_x,
+                                              int nx, int ny, int64_t ld, int64_t cs,
+                                              bool near_x, bool near_y) {
+  const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+  const int x0 = tx * kETX, y0 = ty * kETY;
+  for (int q = threadIdx.x; q < kEWX * kEWY; q += kEThreads) {
+    const int ly = q / kEWX, lx = q - ly * kEWX;
+    const int gx = near_x ? wrap1(x0 + lx - kEHalo, nx) : wrapn(x0 + lx - kEHalo, nx);
+    const int gy = near_y ? wrap1(y0 + ly - kEHalo, ny) : wrapn(y0 + ly - kEHalo, ny);
+    const int64_t o = (int64_t)gy * ld + gx;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cp_async_elem<sizeof(T)>(&S.raw[m][q], src + m * cs + o);
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
 __device__ __forceinline__ uint64_t dbits(double v) {
@@ -126,19 +199,20 @@ euler_stage_k(EParams<T> P) {
   const bool near_x = P.nx >= kEWX, near_y = P.ny >= kEWY;
   uint64_t wm = 0;
 
+  if ((int)blockIdx.x < P.ntiles)
+    prefetch_tile(S, src, blockIdx.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x, near_y);
   for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
     const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
     const int x0 = tx * kETX, y0 = ty * kETY;
-    __syncthreads();  // the previous tile's fluxes are consumed
-    // ---- load the tile + halo, convert to primitives
+    // this tile's copies have landed (each thread waits for its own, the
+    // barrier for everyone's); the previous tile's fluxes are consumed
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    // ---- primitives of the tile + halo
     for (int q = tid; q < kEWX * kEWY; q += kEThreads) {
       const int ly = q / kEWX, lx = q - ly * kEWX;
-      const int gx = near_x ? wrap1(x0 + lx - kEHalo, P.nx) : wrapn(x0 + lx - kEHalo, P.nx);
-      const int gy = near_y ? wrap1(y0 + ly - kEHalo, P.ny) : wrapn(y0 + ly - kEHalo, P.ny);
-      const int64_t o = (int64_t)gy * P.ld + gx;
-      const T r = __ldg(src + o), mx = __ldg(src + P.cs + o), my = __ldg(src + 2 * P.cs + o),
-              e = __ldg(src + 3 * P.cs + o);
-      const T ir = T(1) / r;
+      const T r = S.raw[0][q], mx = S.raw[1][q], my = S.raw[2][q], e = S.raw[3][q];
+      const T ir = recip(r);
       const T u = mx * ir, v = my * ir;
       S.w[0][ly][lx] = r;
       S.w[1][ly][lx] = u;
@@ -146,37 +220,23 @@ euler_stage_k(EParams<T> P) {
       S.w[3][ly][lx] = P.gm1 * (e - T(0.5) * r * (u * u + v * v));
     }
     __syncthreads();
-    // ---- face fluxes: x faces (kETX + 1) x kETY, then y faces kETX x (kETY + 1)
-    constexpr int kNX = (kETX + 1) * kETY, kNY = kETX * (kETY + 1);
-    for (int q = tid; q < kNX + kNY; q += kEThreads) {
-      T a[4], b[4], c[4], d[4], f[4];
-      if (q < kNX) {
-        const int j = q / (kETX + 1), k = q - j * (kETX + 1);  // face k - 1/2 of row j
-        const int yy = j + kEHalo, xb = k + kEHalo - 1;           // cell left of the face
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          a[m] = S.w[m][yy][xb - 1];
-          b[m] = S.w[m][yy][xb];
-          c[m] = S.w[m][yy][xb + 1];
-          d[m] = S.w[m][yy][xb + 2];
-        }
-        face_flux<T, true>(a, b, c, d, P.gamma, P.igm1, f);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) S.fx[m][j][k] = f[m];
+    // the raw buffer is free: start the next tile's copies under this tile's fluxes
+    if (tile + (int)gridDim.x < P.ntiles)
+      prefetch_tile(S, src, tile + (int)gridDim.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x,
+                    near_y);
+    // ---- face fluxes. Warps 0-3: x faces, one run of 4 faces (5 for the last
+    // segment of a row) per thread, rows 4w + lane / 8, segment lane % 8.
+    // Warps 4-7: y faces, column lane, segment w - 4 of 4 faces (5 last).
+    {
+      const int warp = tid >> 5, lane = tid & 31;
+      if (warp < 4) {
+        const int j = 4 * warp + (lane >> 3), sg = lane & 7;
+        face_run<T, true>(&S.w[0][j + kEHalo][0], 1, kEWY * kEWP, 4 * sg, sg == 7 ? 5 : 4,
+                          &S.fx[0][j][0], 1, kETY * (kETX + 1), P.gamma, P.igm1);
       } else {
-        const int r = q - kNX;
-        const int j = r / kETX, i = r - j * kETX;                // face j - 1/2 of column i
-        const int xx = i + kEHalo, yb = j + kEHalo - 1;          // cell below the face
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          a[m] = S.w[m][yb - 1][xx];
-          b[m] = S.w[m][yb][xx];
-          c[m] = S.w[m][yb + 1][xx];
-          d[m] = S.w[m][yb + 2][xx];
-        }
-        face_flux<T, false>(a, b, c, d, P.gamma, P.igm1, f);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) S.fy[m][j][i] = f[m];
+        const int i = lane, sg = warp - 4;
+        face_run<T, false>(&S.w[0][0][i + kEHalo], kEWP, kEWY * kEWP, 4 * sg, sg == 3 ? 5 : 4,
+                           &S.fy[0][0][i], kETX, (kETY + 1) * kETX, P.gamma, P.igm1);
       }
     }
     __syncthreads();
