@@ -112,7 +112,9 @@ const char* px_status_string(px_status s);
  *  PX_OPT_FP32_FAMILY           FP32 relaxation kernel for depth >= 2:
  *                               0 automatic by size, 1 one-row shared-memory
  *                               wavefront, 2 two-row shared-memory wavefront,
- *                               3 register wavefront at every size.
+ *                               3 register wavefront at every size, 4 the
+ *                               register wavefront with packed-pair (f32x2)
+ *                               arithmetic at every size.
  *  PX_OPT_RB_SWEEPS_PER_LAUNCH  red-black sweeps per launch of the FP32
  *                               register wavefront: 0 automatic (3), 1..4.
  * px_set_option returns PX_EINVAL for an unknown option or a value out of

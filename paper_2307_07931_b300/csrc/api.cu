@@ -252,7 +252,7 @@ px_status px_set_option(px_ctx* c, int option, int value) {
   c->err.clear();
   switch (option) {
     case PX_OPT_FP32_FAMILY:
-      if (value < 0 || value > 3) return fail(c, PX_EINVAL, "FP32 family %d not in 0..3", value);
+      if (value < 0 || value > 4) return fail(c, PX_EINVAL, "FP32 family %d not in 0..4", value);
       c->opt_fp32_family = value;
       return PX_OK;
     case PX_OPT_RB_SWEEPS_PER_LAUNCH:

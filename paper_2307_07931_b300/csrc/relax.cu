@@ -742,10 +742,14 @@ cudaError_t launch_wave2_t(const FieldDesc& f, const float* src, float* dst, con
   return cudaGetLastError();
 }
 
+// Whether the automatic choice takes the packed-pair (f32x2) form of the
+// register wavefront's Jacobi stages.
+constexpr bool kRegPackedDefault = false;
+
 // FP32 kernel family for depth >= 2, from the context option
 // PX_OPT_FP32_FAMILY carried in the field descriptor: 1 the one-row
 // wavefront, 2 the two-row wavefront, 3 the register wavefront at every size,
-// 0 (the default) the fastest measured (200 sweeps, a report every sweep):
+// 4 the same with packed-pair arithmetic, 0 (the default) the fastest measured (200 sweeps, a report every sweep):
 // the register wavefront at depths 3..8 on fields of 2^23 cells or more
 // (depth 8: 2406 vs 1424 GLUP/s on the two-row wavefront at 16384^2, 1431 vs
 // 912 at 3072^2); below, where the two-row wavefront wins at depth 8 (997 vs
@@ -857,7 +861,7 @@ struct R2Task {
   int y0, lim, lmax;
 };
 
-template <int TB, int P, bool kEdge, bool kRB>
+template <int TB, int P, bool kEdge, bool kRB, bool kPack>
 __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
                                        const float* __restrict__ rho, float* __restrict__ out,
                                        float* ring, int ny, int64_t ld, int gx, bool own,
@@ -895,6 +899,30 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
     const float cl = __shfl_up_sync(0xffffffffu, c[3], 1);
     const float cr = __shfl_down_sync(0xffffffffu, c[0], 1);
     float o0[4], o1[4], q0[4], q1[4];
+    if constexpr (kPack && !kRB) {
+      // The same operations in the same order on packed pairs of cells
+      // (add/fma.rn.f32x2: each half rounds like the scalar instruction, so
+      // the results are bitwise those of the scalar form below). The
+      // horizontal sums stay scalar, which lets them land in aligned pairs
+      // without moves; rho is negated exactly by a product with -1.
+      const float h0[4] = {bl + b[1], b[0] + b[2], b[1] + b[3], b[2] + br};
+      const float h1[4] = {cl + c[1], c[0] + c[2], c[1] + c[3], c[2] + cr};
+      const float2 m4 = make_float2(-4.0f, -4.0f), n1 = make_float2(-1.0f, -1.0f);
+      const float2 ih2 = make_float2(k.ih2, k.ih2), kc = make_float2(k.c, k.c);
+#pragma unroll
+      for (int x = 0; x < 4; x += 2) {
+        const float2 av = make_float2(a[x], a[x + 1]), bv = make_float2(b[x], b[x + 1]);
+        const float2 cv = make_float2(c[x], c[x + 1]), dv = make_float2(d[x], d[x + 1]);
+        const float2 S0 = __fadd2_rn(make_float2(h0[x], h0[x + 1]), __fadd2_rn(av, cv));
+        const float2 S1 = __fadd2_rn(make_float2(h1[x], h1[x + 1]), __fadd2_rn(bv, dv));
+        const float2 s0 = __ffma2_rn(m4, bv, S0), s1 = __ffma2_rn(m4, cv, S1);
+        const float2 Q0 = __ffma2_rn(s0, ih2, __fmul2_rn(make_float2(rh0[x], rh0[x + 1]), n1));
+        const float2 Q1 = __ffma2_rn(s1, ih2, __fmul2_rn(make_float2(rh1[x], rh1[x + 1]), n1));
+        const float2 O0 = __ffma2_rn(kc, Q0, bv), O1 = __ffma2_rn(kc, Q1, cv);
+        q0[x] = Q0.x; q0[x + 1] = Q0.y; q1[x] = Q1.x; q1[x + 1] = Q1.y;
+        o0[x] = O0.x; o0[x + 1] = O0.y; o1[x] = O1.x; o1[x + 1] = O1.y;
+      }
+    } else {
 #pragma unroll
     for (int x = 0; x < 4; ++x) {
       const float w0 = x == 0 ? bl : b[x - 1], e0 = x == 3 ? br : b[x + 1];
@@ -913,6 +941,7 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
         o0[x] = fmaf(k.c, q0[x], b[x]);
         o1[x] = fmaf(k.c, q1[x], c[x]);
       }
+    }
     }
     // Residual of state t-1 at rows r0-t, r0-t+1: exact once the row index
     // is >= t (level t-1 is exact from index t-1 on, and at the bottom every
@@ -1001,7 +1030,7 @@ __device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips,
   return false;
 }
 
-template <int TB, bool kRB>
+template <int TB, bool kRB, bool kPack>
 __global__ void __launch_bounds__(r_warps<TB, kRB>() * 32)
 relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
             int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
@@ -1078,16 +1107,16 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
 #pragma unroll 1
     for (; r0 < kPro; r0 += 4) {
       if (!ready(r0)) goto task_done;
-      rstep2<TB, 0, true, kRB>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, true, kRB, kPack>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) goto task_done;
-      rstep2<TB, 1, true, kRB>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, true, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
     }
 #pragma unroll 1
     for (;; r0 += 4) {
       if (!ready(r0)) break;
-      rstep2<TB, 0, false, kRB>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, false, kRB, kPack>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) break;
-      rstep2<TB, 1, false, kRB>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, false, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
     }
   task_done:
     cp_wait<0>();  // the next task's prologue reuses the ring slots
@@ -1103,17 +1132,17 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
   }
 }
 
-template <int TB, bool kRB = false>
+template <int TB, bool kRB = false, bool kPack = false>
 cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
                           cudaStream_t st) {
   static int occ_by_dev[64] = {};
   int& occ = occ_by_dev[dev_index()];
   if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB>,
+    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB, kPack>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB, kPack>,
                                                       r_warps<TB, kRB>() * 32, r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
@@ -1136,7 +1165,7 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   const int64_t tasks = (int64_t)nstrips * nseg;
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>((tasks + r_warps<TB, kRB>() - 1) / r_warps<TB, kRB>(), resident));
-  relaxR2_f32<TB, kRB><<<blocks, r_warps<TB, kRB>() * 32, r_smem<TB, kRB>(), st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
+  relaxR2_f32<TB, kRB, kPack><<<blocks, r_warps<TB, kRB>() * 32, r_smem<TB, kRB>(), st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
                                                         nstrips, nseg, k, rep, dyn ? sched : nullptr);
   return cudaGetLastError();
 }
@@ -1197,7 +1226,19 @@ cudaError_t launch_relax_t(const FieldDesc& f, const T* src, T* dst, const T* rh
   if constexpr (sizeof(T) == 4) {
     const int fam = f.family;
     // the register wavefront needs many warps' worth of rows: from 2^23 cells
-    if (fam == 3 || (fam == 0 && tb >= 3 && (int64_t)f.nx * f.ny >= ((int64_t)1 << 23))) {
+    if (fam == 3 || fam == 4 || (fam == 0 && tb >= 3 && (int64_t)f.nx * f.ny >= ((int64_t)1 << 23))) {
+      if (fam == 4 || (fam == 0 && kRegPackedDefault)) {
+        switch (tb) {
+          case 2: return launch_reg2_t<2, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 3: return launch_reg2_t<3, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 4: return launch_reg2_t<4, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 5: return launch_reg2_t<5, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 6: return launch_reg2_t<6, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 7: return launch_reg2_t<7, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          case 8: return launch_reg2_t<8, false, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+          default: return cudaErrorInvalidValue;
+        }
+      }
       switch (tb) {
         case 2: return launch_reg2_t<2>(f, src, dst, rho, k, rep, sched, sched_cap, st);
         case 3: return launch_reg2_t<3>(f, src, dst, rho, k, rep, sched, sched_cap, st);

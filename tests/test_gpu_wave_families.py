@@ -7,10 +7,10 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FAMILIES = {"default": 0, "w1": 1, "w2": 2, "r": 3}
+FAMILIES = {"default": 0, "w1": 1, "w2": 2, "r": 3, "rp": 4}
 
 
-@pytest.mark.parametrize("family", ["w1", "w2", "r", "default"])
+@pytest.mark.parametrize("family", ["w1", "w2", "r", "rp", "default"])
 def test_family_bitwise_equals_single_sweep(family):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -44,7 +44,7 @@ def test_option_values_are_checked():
     import paper_2307_07931_b300 as px
     ctx = px.Context(torch.cuda.current_device())
     try:
-        for opt, bad in ((px.PX_OPT_FP32_FAMILY, 4), (px.PX_OPT_FP32_FAMILY, -1),
+        for opt, bad in ((px.PX_OPT_FP32_FAMILY, 5), (px.PX_OPT_FP32_FAMILY, -1),
                          (px.PX_OPT_RB_SWEEPS_PER_LAUNCH, 5), (99, 0)):
             with pytest.raises(px.PxError) as ei:
                 ctx.set_option(opt, bad)
