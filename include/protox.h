@@ -420,8 +420,10 @@ px_status px_cnn_guess(px_cnn* net, const double* rho, double* phi0, int B, int 
 /* Hidden tensors of the last forward pass, for inspection and tests (the
  * paper has no counterpart): which = 0 the activation a_l = gelu(z_l), 1 the
  * pre-activation z_l (kept only by px_cnn_grads and px_cnn_train_step), of
- * hidden layer l = 1..5, as NHWC BF16 bit patterns (B x H x W x 32 values of
- * the last call's shape; count may be smaller). Synchronises the stream. */
+ * hidden layer l = 1..5, as BF16 bit patterns in the library's chunk-planar
+ * order (B, 4, H, W, 8): channel 8 k + c of pixel (y, x) of image b at
+ * (((b * 4 + k) * H + y) * W + x) * 8 + c; B x H x W x 32 values of the last
+ * call's shape (count may be smaller). Synchronises the stream. */
 px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, size_t count,
                             void* stream);
 /* Polls per handshake wait (producer, MMA issuer, epilogue) of the
@@ -432,6 +434,13 @@ px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, s
  * The network stays usable: later calls recompute everything they return.
  * (Failure detection; the paper has no counterpart.) */
 px_status px_cnn_set_wait_limit(px_cnn* net, uint32_t polls);
+/* How the tensor-core convolutions stage each tap's shifted input tile into
+ * shared memory: mode 1 (the default) with one tensor-memory-accelerator box
+ * for tiles that lie inside the image and per-pixel copies for tiles that
+ * wrap around the periodic edge; mode 0 with per-pixel copies only. Both
+ * stage the same bytes, so results are bitwise equal. PX_EINVAL for other
+ * modes. (An implementation choice; the paper has no counterpart.) */
+px_status px_cnn_set_staging(px_cnn* net, int mode);
 
 /* ----------------------------------------------------------------------------
  * 2D Euler equations of gas dynamics by the finite-volume method: the paper's

@@ -116,12 +116,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_cnn_get_hidden.argtypes = [_vp, i, i, ctypes.POINTER(ctypes.c_uint16), ctypes.c_size_t,
                                       _vp]
     lib.px_cnn_set_wait_limit.argtypes = [_vp, ctypes.c_uint32]
+    lib.px_cnn_set_staging.argtypes = [_vp, i]
     lib.px_set_option.argtypes = [_vp, i, i]
     lib.px_get_option.argtypes = [_vp, i, ip]
     eg = ctypes.POINTER(EulerGrid)
     lib.px_euler_step.argtypes = [_vp, eg, _vp, _vp, d, d, i, d, _vp, _vp]
     lib.px_euler_conserved.argtypes = [_vp, eg, _vp, _vp, d, _vp]
-    for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_set_option", "px_get_option",
+    for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_cnn_set_staging",
+                 "px_set_option", "px_get_option",
                  "px_euler_step", "px_euler_conserved"):
         getattr(lib, name).restype = i
     for name in ("px_cnn_get_state", "px_cnn_set_state",
@@ -611,12 +613,18 @@ class Cnn:
         self.ctx.check(load_library().px_cnn_get_hidden(
             self.handle, int(layer), 0 if which == "a" else 1,
             raw.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16)), n, _stream(stream)))
-        return (raw.astype(np.uint32) << 16).view(np.float32).reshape(B, H, W, 32)
+        f = (raw.astype(np.uint32) << 16).view(np.float32).reshape(B, 4, H, W, 8)
+        return f.transpose(0, 2, 3, 1, 4).reshape(B, H, W, 32)
 
     def set_wait_limit(self, polls: int):
         """px_cnn_set_wait_limit: polls per handshake wait of the tensor-core
         kernels (0 = default)."""
         self.ctx.check(load_library().px_cnn_set_wait_limit(self.handle, int(polls)))
+
+    def set_staging(self, mode: int):
+        """px_cnn_set_staging: 1 tensor-memory-accelerator boxes for in-image tap
+        tiles (default), 0 per-pixel copies only."""
+        self.ctx.check(load_library().px_cnn_set_staging(self.handle, int(mode)))
 
     def guess(self, rho, phi0, h: float, stream=None):
         B, H, W = rho.shape

@@ -2,8 +2,13 @@
 // GELU after every layer but the last), BF16 weights and activations with FP32
 // accumulation, trained and run by the kernels in this file.
 //
-// Layout: activations NHWC BF16 with 32 channels (64 bytes per pixel); the
-// network input x and output y are single-channel FP32 images. Convolutions
+// Layout: BF16 activations of 32 channels stored chunk-planar: per image, four
+// planes of 8 channels (16 bytes per pixel), element (b, chunk, y, x, c) at
+// (((b * 4 + chunk) * H + y) * W + x) * 8 + c. A row of 64 pixels of one
+// plane is 1 KB contiguous, which is exactly one core-matrix row block of the
+// tensor-core operand, so a tap tile is one rectangular box for the tensor
+// memory accelerator. The network input x and output y are single-channel
+// FP32 images. Convolutions
 // are periodic cross-correlations: z[p][o] = b[o] + sum_{dy,dx,c} W[o][c][dy][dx]
 // x[p + (dy - 1, dx - 1)][c].
 //
@@ -22,6 +27,7 @@
 // multiply-adds per pixel and run on the CUDA cores.
 #include "px_internal.cuh"
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -62,11 +68,16 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 
-__device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p) {
-  const uint4* q = reinterpret_cast<const uint4*>(p);
+// Element offset of channel chunk `chunk` (8 channels) of pixel (b, y, x).
+__host__ __device__ __forceinline__ int64_t act_off(int b, int y, int x, int chunk, int H, int W) {
+  return ((((int64_t)b * 4 + chunk) * H + y) * W + x) * 8;
+}
+
+// The 32 channels of one pixel: four 16-byte loads, `plane` elements apart.
+__device__ __forceinline__ void load_px32(float (&f)[C], const __nv_bfloat16* p, int64_t plane) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    uint4 u = q[k];
+    uint4 u = *reinterpret_cast<const uint4*>(p + k * plane);
     const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -202,22 +213,41 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                ::"r"(bar) : "memory");
 }
 
+// Tensor memory accelerator: one 5D box of the chunk-planar activations,
+// dims (8 channels, W, H, 4 chunks, B), box (8, 64, R, 4, 1), lands in shared
+// memory as [chunk][row][pixel][8 channels], the operand's core-matrix layout;
+// completion is counted in bytes on the stage's `full` barrier.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                              int b, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(0), "r"(b),
+        "r"(bar)
+      : "memory");
+}
+
 // Stage one tap's [R * 64 px][32 ch] input tile in the core-matrix layout
 // (chunk c of 8 channels at c * R * 1024 B, pixel p at p * 16 B), threads pid
-// of np. A warp copies 8 whole pixels: 512 contiguous global bytes into four
-// 128-byte shared rows. The periodic wrap is a conditional add or subtract
-// when the tap offset is smaller than the image, a full modulo otherwise.
+// of np. Consecutive threads copy consecutive pixels of one channel plane
+// (a warp: 512 contiguous global bytes). The periodic wrap is a conditional
+// add or subtract when the tap offset is smaller than the image, a full
+// modulo otherwise.
 template <int R>
 __device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfloat16* act, int b,
                                               int y0, int x0, int oy, int ox, int H, int W,
                                               int pid, int np) {
   const bool near = oy > -H && oy < H && ox > -W && ox < W;
   for (int q = pid; q < R * TW * 4; q += np) {
-    const int chunk = q & 3, pix = q >> 2;
+    const int chunk = q / (R * TW), pix = q - chunk * (R * TW);
     const int r = pix >> 6, c = pix & (TW - 1);
     const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
     const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
-    cp16(dst + chunk * (R * TW * 16) + pix * 16, act + (((int64_t)b * H + gy) * W + gx) * C + chunk * 8);
+    cp16(dst + chunk * (R * TW * 16) + pix * 16, act + act_off(b, gy, gx, chunk, H, W));
   }
 }
 
@@ -229,7 +259,7 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
                                                    __nv_bfloat16* __restrict__ zout,
                                                    __nv_bfloat16* __restrict__ aout) {
   const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
-  const int64_t pb = (((int64_t)b * H + y) * W + x) * C;
+  const int64_t pb = act_off(b, y, x, 0, H, W), plane = (int64_t)H * W * 8;
   __nv_bfloat162 zz[C / 2], aa[C / 2];
   if (kMode == 0) {
 #pragma unroll
@@ -240,21 +270,21 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
       aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
     }
     if (zout) {
-      uint4* zo = reinterpret_cast<uint4*>(zout + pb);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) zo[k] = reinterpret_cast<const uint4*>(zz)[k];
+      for (int k = 0; k < 4; ++k)
+        *reinterpret_cast<uint4*>(zout + pb + k * plane) = reinterpret_cast<const uint4*>(zz)[k];
     }
   } else {
     float zf[C];
-    load_px32(zf, zprev + pb);
+    load_px32(zf, zprev + pb, plane);
 #pragma unroll
     for (int o = 0; o < C; o += 2)
       aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
                                         __uint_as_float(v[o + 1]) * gelu_grad_f(zf[o + 1]));
   }
-  uint4* ao = reinterpret_cast<uint4*>(aout + pb);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) ao[k] = reinterpret_cast<const uint4*>(aa)[k];
+  for (int k = 0; k < 4; ++k)
+    *reinterpret_cast<uint4*>(aout + pb + k * plane) = reinterpret_cast<const uint4*>(aa)[k];
 }
 
 template <int kMode>
@@ -263,7 +293,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
           __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
           int tiles_x, int tiles_y, int ntiles, int dil, unsigned* __restrict__ fault,
-          uint32_t wait_limit) {
+          uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap_in, int use_tma) {
   // no static shared variables: the core matrices must start on 128-byte boundaries
   extern __shared__ __align__(128) unsigned char wsu[];
   unsigned char* ring = wsu;
@@ -317,8 +347,17 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       for (int tap = 0; tap < 9; ++tap, ++g) {
         const int st = g % kWsStages, u = g / kWsStages;
         if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_, wait_limit)) { go = false; break; }
-        load_tap_cm_p<TR>(ring + st * kCmTile, in, b, ty * TR, tx * TW, tap_dy(tap, dil),
-                      tap_dx(tap, dil), H, W, pid, np);
+        const int oy = tap_dy(tap, dil), ox = tap_dx(tap, dil);
+        const int ys = wrapn(ty * TR + oy, H), xs = wrapn(tx * TW + ox, W);
+        if (use_tma && xs + TW <= W && ys + TR <= H) {
+          // the shifted tile lies inside the image: one box, issued by one thread
+          if (pid == 0) {
+            mbar_expect_tx(full0 + 8 * st, (uint32_t)kCmTile);
+            tma_load_tile(smem_u32(ring + st * kCmTile), &tmap_in, xs, ys, b, full0 + 8 * st);
+          }
+        } else {  // it wraps around the periodic edge: per-pixel copies
+          load_tap_cm_p<TR>(ring + st * kCmTile, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
+        }
         cp_commit();
         if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
           cp_wait_group<kWsAhead>();
@@ -576,7 +615,7 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
         zz[j / 2] = __floats2bfloat162_rn(s0, s1);
         aa[j / 2] = __floats2bfloat162_rn(gelu_f(s0), gelu_f(s1));
       }
-      const int64_t po = ((int64_t)row * W + xx) * C + cg * 8;
+      const int64_t po = act_off(img, yy, xx, cg, H, W);
       if (zout) *reinterpret_cast<uint4*>(zout + po) = *reinterpret_cast<const uint4*>(zz);
       *reinterpret_cast<uint4*>(aout + po) = *reinterpret_cast<const uint4*>(aa);
     }
@@ -604,7 +643,7 @@ __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __re
     const __nv_bfloat16* ar[3];
 #pragma unroll
     for (int ty = 0; ty < 3; ++ty)
-      ar[ty] = a + ((int64_t)img * H + wrapn(yy + (ty - 1) * dil, H)) * W * C + cg * 8;
+      ar[ty] = a + act_off(img, wrapn(yy + (ty - 1) * dil, H), 0, cg, H, W);
     for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
       const int xx = t >> 2;
       const int xs[3] = {wrap_col(xx - dil, W, near), xx, wrap_col(xx + dil, W, near)};
@@ -613,7 +652,7 @@ __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __re
       for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) {
-          const uint4 u = __ldg(reinterpret_cast<const uint4*>(ar[ty] + (int64_t)xs[tx] * C));
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(ar[ty] + (int64_t)xs[tx] * 8));
           const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -675,7 +714,7 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
       for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) g[ty * 3 + tx] = __ldg(gr[ty] + xs[tx]);
-      const int64_t po = ((int64_t)row * W + xx) * C + cg * 8;
+      const int64_t po = act_off(img, yy, xx, cg, H, W);
       const uint4 u = __ldg(reinterpret_cast<const uint4*>(z5 + po));
       const __nv_bfloat162* hz = reinterpret_cast<const __nv_bfloat162*>(&u);
       __nv_bfloat162 o[4];
@@ -730,7 +769,7 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
     const float* srow[3];
 #pragma unroll
     for (int ty = 0; ty < 3; ++ty) srow[ty] = s1 + ibase + (int64_t)wrapn(y + (ty - 1) * sd, H) * W;
-    const __nv_bfloat16* grow = g32 + ((int64_t)row * W) * C + cg * 8;
+    const __nv_bfloat16* grow = g32 + act_off(img, y, 0, cg, H, W);
     for (int x = slot; x < W; x += kWsThreads / 4) {
       const int xs[3] = {wrap_col(x - sd, W, near), x, wrap_col(x + sd, W, near)};
       float sv[9];
@@ -738,7 +777,7 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
       for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) sv[ty * 3 + tx] = __ldg(srow[ty] + xs[tx]);
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>(grow + (int64_t)x * C));
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(grow + (int64_t)x * 8));
       const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
       float g[8];
 #pragma unroll
@@ -971,6 +1010,7 @@ struct px_cnn {
   double* lpart_host = nullptr;
   int64_t cap_img = 0;
   uint32_t wait_limit = kSpinLimit;  // polls per handshake wait of the tensor-core kernels
+  int use_tma = 1;                     // stage in-image tap tiles with the tensor memory accelerator
 };
 
 namespace {
@@ -1070,6 +1110,44 @@ px_status check_conv_fault(px_cnn* n, cudaStream_t st) {
   return PX_OK;
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library); null if unavailable.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+    cudaGetLastError();
+    resolved = true;
+  }
+  return fn;
+}
+
+// Tensor map of B chunk-planar activation images of H x W for boxes of R
+// rows x 64 pixels x 32 channels; false (and the per-pixel copy path) if the
+// driver cannot encode it.
+bool act_tensor_map(CUtensorMap* m, const __nv_bfloat16* act, int B, int H, int W, int R) {
+  std::memset(m, 0, sizeof *m);
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || ((uintptr_t)act & 15u)) return false;
+  const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)B};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16,
+                                 (cuuint64_t)W * H * 64};
+  const cuuint32_t box[5] = {8, (cuuint32_t)TW, (cuuint32_t)R, 4, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 px_status set_conv_attrs() {
   static bool done_by_dev[64] = {};
   bool& done = done_by_dev[px::dev_index()];
@@ -1093,10 +1171,13 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
   unsigned* fault = conv_fault_ptr();
   if (!fault) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
   const int cgrid = std::min(tiles, 2 * px::device_sm_count());  // persistent: 2 CTAs per SM
-  for (int l = 1; l <= 4; ++l)
+  for (int l = 1; l <= 4; ++l) {
+    alignas(64) CUtensorMap tm;
+    const int use = n->use_tma && act_tensor_map(&tm, n->a[l - 1], B, H, W, TR);
     conv32_ws<0><<<cgrid, kWsConvThreads, kWsSmem, st>>>(
         n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault, n->wait_limit);
+        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault, n->wait_limit, tm, use);
+  }
   conv_last<<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
@@ -1137,9 +1218,11 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
         conv_fault_ptr(), n->wait_limit);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
+    alignas(64) CUtensorMap tm;
+    const int use = n->use_tma && act_tensor_map(&tm, gcur, B, H, W, TR);
     conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
         gcur, n->wb[l], nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
-        n->dil[l], conv_fault_ptr(), n->wait_limit);
+        n->dil[l], conv_fault_ptr(), n->wait_limit, tm, use);
     std::swap(gcur, gnext);
   }
   wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
@@ -1274,6 +1357,16 @@ px_status px_cnn_get_hidden(px_cnn* n, int layer, int which, uint16_t* host, siz
   cudaError_t e = cudaMemcpyAsync(host, src, count * sizeof(uint16_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "hidden readback");
+}
+
+// How the tensor-core convolutions stage their tap tiles: 1 (the default)
+// with the tensor memory accelerator for tiles inside the image and
+// per-pixel copies for tiles that wrap around the periodic edge, 0 with
+// per-pixel copies only. Both stage the same bytes: results are bitwise equal.
+px_status px_cnn_set_staging(px_cnn* n, int mode) {
+  if (!n || mode < 0 || mode > 1) return PX_EINVAL;
+  n->use_tma = mode;
+  return PX_OK;
 }
 
 // Polls per handshake wait of the tensor-core kernels (0 restores the

@@ -195,6 +195,35 @@ def test_gradients_multitile_match_oracle(px, dil):
     net.close()
 
 
+@pytest.mark.parametrize("dil", [None, DIL, (1, 2, 5, 64, 7, 1)])
+def test_tma_staging_bitwise_equals_copies(px, dil):
+    """Tap tiles staged by the tensor memory accelerator (in-image tiles) and by
+    per-pixel copies (every tile) are the same bytes: the forward output, the
+    hidden tensors and all gradients agree bitwise, at several tiles per CTA
+    (B = 4, 256^2) and with dilations that make boxes cross the edge."""
+    B, H, W = 4, 256, 256
+    rng = np.random.default_rng(41)
+    x = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+    t = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
+    out = {}
+    for mode in (0, 1):
+        net = px.Cnn(seed=43, dilations=dil)
+        net.set_staging(mode)
+        y = torch.empty_like(x)
+        net.forward(x, y)
+        g, loss = net.grads(x, t)
+        hid = [net.hidden(l, w, (B, H, W)) for l in (2, 5) for w in ("a", "z")]
+        torch.cuda.synchronize()
+        out[mode] = (y.cpu().numpy(), g, loss, hid)
+        net.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+    for a, b in zip(out[0][3], out[1][3]):
+        assert np.array_equal(a, b)
+    with pytest.raises(px.PxError):
+        px.Cnn(seed=1).set_staging(2)
+
+
 def test_bounded_wait_times_out_and_recovers(px):
     """With one poll per handshake wait the tensor-core kernels give up (no
     phase completes that fast everywhere), drain their issued MMAs, free
