@@ -17,6 +17,7 @@ namespace {
 struct ClassCfg {
   int mode = px::MODE_BANDED;
   int ry = 8;
+  int tb = 1;                // sweeps per cluster barrier (MODE_BANDED_T)
   double rate_per_sm = 0.0;  // measured cell updates / s per SM (0 = not measured)
   bool tuned = false;
 };
@@ -45,8 +46,8 @@ std::string gpu_name(int dev) {
   return p.name;
 }
 
-// Tune cache: one JSON object, {"gpu": "...", "classes": {"f32:96x96": {"mode": 0,
-// "ry": 8, "rate_per_sm": 1.2e10}, ...}}. Written and read only by this file.
+// Tune cache: one JSON object, {"gpu": "...", "classes": {"f32:96x96@c2": {"mode": 0,
+// "ry": 8, "tb": 1, "rate_per_sm": 1.2e10}, ...}}. Written and read only by this file.
 void load_cache(const char* path, const std::string& gpu, std::map<std::string, ClassCfg>& out) {
   if (!path) return;
   FILE* f = fopen(path, "r");
@@ -63,13 +64,16 @@ void load_cache(const char* path, const std::string& gpu, std::map<std::string, 
     const size_t q = s.find('"', pos + 1);
     if (q == std::string::npos) break;
     const std::string key = s.substr(pos + 1, q - pos - 1);
-    int mode = 0, ry = 0;
+    int mode = 0, ry = 0, tb = 0;
     double rate = 0;
-    if (sscanf(s.c_str() + q + 1, ": {\"mode\": %d, \"ry\": %d, \"rate_per_sm\": %lf}", &mode,
-               &ry, &rate) == 3 && key.find(':') != std::string::npos) {
+    if (sscanf(s.c_str() + q + 1, ": {\"mode\": %d, \"ry\": %d, \"tb\": %d, \"rate_per_sm\": %lf}",
+               &mode, &ry, &tb, &rate) == 4 && key.find(':') != std::string::npos &&
+        mode >= px::MODE_WHOLE && mode <= px::MODE_BANDED_T && tb >= 1 && tb <= 8 &&
+        (mode != px::MODE_BANDED_T || px::banded_t_ok(key[1] == '3' ? PX_F32 : PX_F64, tb))) {
       ClassCfg c;
       c.mode = mode;
       c.ry = ry;
+      c.tb = tb;
       c.rate_per_sm = rate;
       c.tuned = true;
       out[key] = c;
@@ -87,8 +91,9 @@ void save_cache(const char* path, const std::string& gpu, const std::map<std::st
   bool first = true;
   for (const auto& kv : m) {
     if (!kv.second.tuned) continue;
-    fprintf(f, "%s\n  \"%s\": {\"mode\": %d, \"ry\": %d, \"rate_per_sm\": %.6e}", first ? "" : ",",
-            kv.first.c_str(), kv.second.mode, kv.second.ry, kv.second.rate_per_sm);
+    fprintf(f, "%s\n  \"%s\": {\"mode\": %d, \"ry\": %d, \"tb\": %d, \"rate_per_sm\": %.6e}",
+            first ? "" : ",", kv.first.c_str(), kv.second.mode, kv.second.ry, kv.second.tb,
+            kv.second.rate_per_sm);
     first = false;
   }
   fprintf(f, "\n}}\n");
@@ -119,70 +124,91 @@ struct px_batch {
 
 namespace {
 
-// Measures one class on one representative instance: WHOLE (one CTA) and
-// BANDED (one cluster) with rows-per-task 4, 8, 16; keeps the fastest rate
-// per SM. Buffers are zero fields allocated for the measurement.
+// Measures one class: every candidate (WHOLE in one CTA; BANDED with rows per
+// task 4, 8, 16; for FP32 BANDED_T with 4 or 8 sweeps per barrier) runs on
+// `copies` zero instances at once, one per cluster (or CTA for WHOLE), so the
+// rate includes the memory traffic of a full device: a single instance alone
+// stays in L2 and would make streaming modes look faster than they run in
+// the batch. Keeps the fastest rate per SM.
 px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double omega, int C,
-                     ClassCfg* out) {
+                     int clusters, ClassCfg* out) {
   const int64_t ld = nx;
   const size_t es = dtype == PX_F64 ? 8 : 4;
-  const size_t bytes = (size_t)ld * ny * es;
-  void *phi = nullptr, *rho = nullptr, *scr = nullptr, *idx = nullptr, *ins = nullptr;
+  const size_t fb = ((size_t)ld * ny * es + 255) / 256 * 256;
+  // concurrent copies: every cluster, within 4 GiB of fields
+  const int copies = (int)std::max<int64_t>(1, std::min<int64_t>(clusters, ((int64_t)4 << 30) / (int64_t)(4 * fb)));
+  void *mem = nullptr, *idx = nullptr, *ins = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   px_status st = PX_OK;
-  std::vector<std::pair<int, int>> cands;  // (mode, ry)
-  if (fits_whole(nx, ny, dtype)) cands.push_back({px::MODE_WHOLE, 0});
-  for (int ry : {4, 8, 16}) cands.push_back({px::MODE_BANDED, ry});
+  struct Cand { int mode, ry, tb; };
+  std::vector<Cand> cands;
+  if (fits_whole(nx, ny, dtype)) cands.push_back({px::MODE_WHOLE, 0, 1});
+  for (int ry : {4, 8, 16}) cands.push_back({px::MODE_BANDED, ry, 1});
+  if (dtype == PX_F32)
+    for (int tb : {4, 8}) cands.push_back({px::MODE_BANDED_T, 8, tb});
   double best = -1;
-  cudaError_t e = cudaMalloc(&phi, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&rho, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&scr, bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&idx, 64 * sizeof(int) + 4 * C * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&ins, sizeof(px::BInst));
-  if (e == cudaSuccess) e = cudaMemset(phi, 0, bytes);
-  if (e == cudaSuccess) e = cudaMemset(rho, 0, bytes);
+  cudaError_t e = cudaMalloc(&mem, 4 * fb * copies);  // per copy: phi, rho, scratch, -c rho
+  if (e == cudaSuccess) e = cudaMemset(mem, 0, 4 * fb * copies);
+  const int nidx = 2 * (copies * C + 2) + 2 * copies + 8;
+  if (e == cudaSuccess) e = cudaMalloc(&idx, (size_t)nidx * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&ins, copies * sizeof(px::BInst));
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   for (size_t k = 0; e == cudaSuccess && k < cands.size(); ++k) {
-    px::BInst I{};
-    I.phi = phi; I.rho = rho; I.scratch = scr; I.nx = nx; I.ny = ny; I.ld = ld;
-    I.dtype = dtype; I.mode = cands[k].first; I.ry = cands[k].second;
+    const bool whole = cands[k].mode == px::MODE_WHOLE;
+    // WHOLE: copies instances over the CTAs of ceil(copies / C) clusters
+    const int ncl = whole ? (copies + C - 1) / C : copies;
+    std::vector<px::BInst> I(copies);
     const double h = 1.0 / nx;
-    I.c = omega * h * h / 4.0; I.ih2 = 1.0 / (h * h); I.resid = nullptr;
-    // one cluster: BANDED -> cluster list {0}; WHOLE -> CTA 0 list {0}
+    for (int j = 0; j < copies; ++j) {
+      char* base = (char*)mem + (size_t)j * 4 * fb;
+      I[j] = px::BInst{};
+      I[j].phi = base; I[j].rho = base + fb; I[j].scratch = base + 2 * fb;
+      I[j].nx = nx; I[j].ny = ny; I[j].ld = ld; I[j].dtype = dtype;
+      I[j].mode = cands[k].mode; I[j].ry = cands[k].ry; I[j].tb = cands[k].tb;
+      I[j].c = omega * h * h / 4.0; I[j].ih2 = 1.0 / (h * h); I[j].resid = nullptr;
+      I[j].a1 = 1.0 - omega; I[j].w4 = omega / 4.0;
+      I[j].rhos = (I[j].mode == px::MODE_BANDED && dtype == PX_F64) ? base + 3 * fb : nullptr;
+    }
+    // cl_off | cl_items | cta_off | cta_items
     std::vector<int> ix;
-    const bool band = I.mode == px::MODE_BANDED;
-    ix.push_back(0); ix.push_back(band ? 1 : 0);          // cl_off
-    ix.push_back(0);                                      // cl_items
-    for (int r = 0; r <= C; ++r) ix.push_back(band ? 0 : (r == 0 ? 0 : 1));  // cta_off
-    ix.push_back(0);                                      // cta_items
+    for (int q = 0; q <= ncl; ++q) ix.push_back(whole ? 0 : q);
+    const size_t cl_items_at = ix.size();
+    for (int q = 0; q < (whole ? 0 : copies); ++q) ix.push_back(q);
+    const size_t cta_off_at = ix.size();
+    for (int r = 0; r <= ncl * C; ++r) ix.push_back(whole ? std::min(r, copies) : 0);
+    const size_t cta_items_at = ix.size();
+    for (int q = 0; q < (whole ? copies : 0); ++q) ix.push_back(q);
+    ix.push_back(0);
     e = cudaMemcpy(idx, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ins, &I, sizeof I, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(ins, I.data(), copies * sizeof(px::BInst), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) break;
     px::BParams p{};
     p.inst = (px::BInst*)ins;
     p.cl_off = (int*)idx;
-    p.cl_items = (int*)idx + 2;
-    p.cta_off = (int*)idx + 3;
-    p.cta_items = (int*)idx + 4 + C;
+    p.cl_items = (int*)idx + cl_items_at;
+    p.cta_off = (int*)idx + cta_off_at;
+    p.cta_items = (int*)idx + cta_items_at;
     p.nsweeps = sweeps;
     p.every = 0;
     p.csize = C;
-    const size_t smem = band ? 0 : px::whole_bytes(nx, ny, dtype);
-    e = px::batch_launch(p, 1, smem, 0);  // warm-up
+    const size_t smem = whole ? px::whole_bytes(nx, ny, dtype)
+                              : (cands[k].mode == px::MODE_BANDED_T ? px::banded_t_smem(dtype, cands[k].tb) : 0);
+    e = px::batch_launch(p, ncl, smem, 0);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
-    if (e == cudaSuccess) e = px::batch_launch(p, 1, smem, 0);
+    if (e == cudaSuccess) e = px::batch_launch(p, ncl, smem, 0);
     if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
     if (e != cudaSuccess) break;
-    const double sms = band ? C : 1;
-    const double rate = (double)nx * ny * sweeps / (ms * 1e-3) / sms;
+    const double sms = whole ? copies : (double)copies * C;
+    const double rate = (double)nx * ny * sweeps * copies / (ms * 1e-3) / sms;
     if (rate > best) {
       best = rate;
-      out->mode = I.mode;
-      out->ry = band ? I.ry : 8;
+      out->mode = cands[k].mode;
+      out->ry = whole ? 8 : cands[k].ry;
+      out->tb = cands[k].tb;
       out->rate_per_sm = rate;
       out->tuned = true;
     }
@@ -193,7 +219,7 @@ px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double om
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  cudaFree(phi); cudaFree(rho); cudaFree(scr); cudaFree(idx); cudaFree(ins);
+  cudaFree(mem); cudaFree(idx); cudaFree(ins);
   return st;
 }
 
@@ -302,7 +328,11 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
       int nx = 0, ny = 0, cs = 0;
       sscanf(kv.first.c_str() + 4, "%dx%d@c%d", &nx, &ny, &cs);
       ClassCfg t;
-      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, cs, &t);
+      int ncl_cs = 1;
+      for (auto& cand : cands)
+        if (cand.first == cs) ncl_cs = cand.second;
+      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, cs,
+                               ncl_cs, &t);
       if (s != PX_OK) { destroy_batch(b); return s; }
       kv.second = t;
       cached[kv.first] = t;
@@ -327,6 +357,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
       const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
       if (k.mode == px::MODE_WHOLE)
         used = std::max(used, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
+      if (k.mode == px::MODE_BANDED_T) used = std::max(used, px::banded_t_smem(grids[i].dtype, k.tb));
     }
     S.smem = (used + 1023) / 1024 * 1024;
     S.ncl = ncl_full;
@@ -341,7 +372,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
       const px_grid& g = grids[i];
       const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny, C)];
       const double work = (double)g.nx * g.ny * nsweeps / std::max(k.rate_per_sm, 1.0);
-      if (k.mode == px::MODE_BANDED) banded.push_back({work / C, i});
+      if (k.mode != px::MODE_WHOLE) banded.push_back({work / C, i});
       else whole.push_back({work, i});
     }
     std::sort(banded.begin(), banded.end(), [](auto& x, auto& y) { return x.first > y.first; });
@@ -376,7 +407,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   std::vector<std::vector<int>>& cta_items = S.cta_items;
 
   size_t scratch_bytes = 0;
-  std::vector<size_t> scr_off(n, 0);
+  std::vector<size_t> scr_off(n, 0), rhs_off(n, SIZE_MAX);
   b->inst.resize(n);
   for (int i = 0; i < n; ++i) {
     const px_grid& g = grids[i];
@@ -384,11 +415,19 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     px::BInst& I = b->inst[i];
     I = px::BInst{};
     I.nx = g.nx; I.ny = g.ny; I.ld = g.ld; I.dtype = g.dtype; I.mode = k.mode; I.ry = k.ry;
+    I.tb = k.tb;
     I.c = omega * g.h * g.h / 4.0;
     I.ih2 = 1.0 / (g.h * g.h);
-    if (k.mode == px::MODE_BANDED) {
+    I.a1 = 1.0 - omega;
+    I.w4 = omega / 4.0;
+    if (k.mode != px::MODE_WHOLE) {
+      const size_t fb = ((size_t)g.ld * g.ny * (g.dtype == PX_F64 ? 8 : 4) + 255) / 256 * 256;
       scr_off[i] = scratch_bytes;
-      scratch_bytes += ((size_t)g.ld * g.ny * (g.dtype == PX_F64 ? 8 : 4) + 255) / 256 * 256;
+      scratch_bytes += fb;
+      if (g.dtype == PX_F64 && k.mode == px::MODE_BANDED) {  // -c rho for unreported sweeps
+        rhs_off[i] = scratch_bytes;
+        scratch_bytes += fb;
+      }
     }
   }
   std::vector<int> ix;
@@ -413,8 +452,10 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     destroy_batch(b);
     return px::ctx_fail(c, PX_ENOMEM, "batch plan buffers");
   }
-  for (int i = 0; i < n; ++i)
-    if (b->inst[i].mode == px::MODE_BANDED) b->inst[i].scratch = (char*)b->scratch + scr_off[i];
+  for (int i = 0; i < n; ++i) {
+    if (b->inst[i].mode != px::MODE_WHOLE) b->inst[i].scratch = (char*)b->scratch + scr_off[i];
+    if (rhs_off[i] != SIZE_MAX) b->inst[i].rhos = (char*)b->scratch + rhs_off[i];
+  }
   b->params.inst = b->inst_dev;
   b->params.cl_off = b->idx_dev;
   b->params.cl_items = b->idx_dev + cl_items_at;
@@ -458,8 +499,11 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
         kv.first.compare(kv.first.size() - suffix.size(), suffix.size(), suffix) != 0)
       continue;
     os << (first ? "" : ", ") << "\"" << kv.first << "\": {\"count\": " << count[kv.first]
-       << ", \"mode\": \"" << (kv.second.mode == px::MODE_WHOLE ? "whole" : "banded")
-       << "\", \"ry\": " << kv.second.ry << ", \"rate_per_sm\": " << kv.second.rate_per_sm
+       << ", \"mode\": \""
+       << (kv.second.mode == px::MODE_WHOLE ? "whole"
+                                            : kv.second.mode == px::MODE_BANDED ? "banded" : "banded_t")
+       << "\", \"ry\": " << kv.second.ry << ", \"tb\": " << kv.second.tb
+       << ", \"rate_per_sm\": " << kv.second.rate_per_sm
        << ", \"tuned\": " << (kv.second.tuned ? "true" : "false") << "}";
     first = false;
   }

@@ -228,16 +228,18 @@ px_status ctx_fail(px_ctx* c, px_status st, const char* msg);
 px_status ctx_check_grid(px_ctx* c, const px_grid* g, FieldDesc* f);
 
 // Batched persistent kernel (batch.cu).
-enum { MODE_WHOLE = 0, MODE_BANDED = 1 };
+enum { MODE_WHOLE = 0, MODE_BANDED = 1, MODE_BANDED_T = 2 };
 
 struct BInst {
   void* phi;
   const void* rho;
   void* scratch;  // BANDED ping-pong partner
+  void* rhos;     // BANDED FP64: the scaled right-hand side -c rho (same layout), or null
   int nx, ny;
   int64_t ld;
-  int dtype, mode, ry, pad;
+  int dtype, mode, ry, tb;  // tb: sweeps per cluster barrier of MODE_BANDED_T
   double c, ih2;
+  double a1, w4;  // 1 - omega and omega / 4: the update without the residual
   double* resid;  // this instance's reports, or null
 };
 
@@ -256,5 +258,9 @@ cudaError_t batch_max_clusters(int* n, size_t smem, int csize);
 cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStream_t st);
 int batch_max_cluster_size();
 size_t batch_whole_smem();
+// Shared bytes of the tiles of a MODE_BANDED_T instance of dtype at depth tb.
+size_t banded_t_smem(int dtype, int tb);
+// Whether MODE_BANDED_T supports dtype at depth tb (FP32, 4 or 8 sweeps).
+bool banded_t_ok(int dtype, int tb);
 
 }  // namespace px

@@ -195,3 +195,48 @@ def test_plan_picks_cluster_size_by_makespan(px):
     torch.cuda.synchronize()
     check(specs, phis, host, resid, 6, 3)
     b.close()
+
+
+def _forced_cache(path, specs, mode, tb, ry=8):
+    """A tune cache that pins every class (all cluster sizes) to one mode."""
+    classes = {}
+    for (nx, ny, dt) in specs:
+        for cs in (2, 4, 8):
+            m = mode if (mode != 2 or dt == "f32") else 1
+            classes[f"{dt}:{nx}x{ny}@c{cs}"] = {"mode": m, "ry": ry, "tb": tb if m == 2 else 1,
+                                                 "rate_per_sm": 1e9}
+    with open(path, "w") as f:
+        json.dump({"gpu": torch.cuda.get_device_name(0), "classes": classes}, f)
+
+
+@pytest.mark.parametrize("tb,nsweeps,every", [(4, 7, 2), (4, 12, 3), (8, 13, 1), (8, 9, 0)])
+def test_temporally_blocked_banded_mode(px, tmp_path, tb, nsweeps, every):
+    """FP32 instances in the temporally blocked mode (tb sweeps per cluster
+    barrier, tiles with a tb-cell periodic halo in shared memory) give bitwise
+    the states and reports of the per-sweep banded mode, and match the oracle;
+    shapes cover several tiles, ragged tiles, bands thinner than the halo and
+    odd block counts (the copy back)."""
+    specs = [(256, 256, "f32"), (160, 96, "f32"), (128, 20, "f32"), (36, 300, "f32"),
+             (512, 128, "f32"), (96, 96, "f64"), (132, 70, "f32")]
+    grids = [px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+             for nx, ny, dt in specs]
+    results = {}
+    for mode in (1, 2):
+        cache = str(tmp_path / f"t{mode}.json")
+        _forced_cache(cache, specs, mode, tb)
+        b = px.Batch(grids, nsweeps, OMEGA, every, tune_cache=cache, tune=False)
+        d = b.describe()
+        want = "banded_t" if mode == 2 else "banded"
+        assert all(v["mode"] == want for k, v in d["classes"].items() if k.startswith("f32")), d
+        phis, rhos, host = make_instances(specs, 17)
+        nrep = (nsweeps + every - 1) // every if every else 0
+        resid = torch.zeros(max(1, len(specs) * nrep), dtype=torch.float64, device="cuda")
+        b.run(phis, rhos, resid if every else None)
+        torch.cuda.synchronize()
+        if every:
+            check(specs, phis, host, resid, nsweeps, every)
+        results[mode] = ([p.cpu() for p in phis], resid.cpu())
+        b.close()
+    for a, c in zip(results[1][0], results[2][0]):
+        assert torch.equal(a, c)
+    assert torch.equal(results[1][1], results[2][1])
