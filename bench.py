@@ -581,6 +581,21 @@ def bench_time_to_tol(px, torch, rtol: float = 1e-8):
     return out
 
 
+def append_log(path: str, line: dict, torch) -> None:
+    """One JSONL record per run: the bench line plus the run's context (time,
+    host, GPU, seeds of the synthetic workloads, host cores)."""
+    import platform
+    import synth
+    rec = {"time": time.strftime("%Y-%m-%dT%H:%M:%S%z"), "host": platform.node(),
+           "gpu": torch.cuda.get_device_name(0), "torch": torch.__version__,
+           "seeds": {"large_field": synth.workload_seed(1), "refine_8192": synth.workload_seed(2),
+                     "batched": synth.workload_seed(3), "relax3d": synth.workload_seed(5),
+                     "euler": synth.workload_seed(6)},
+           "host_cores": os.cpu_count(), "line": line}
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
+
+
 def digest(line: dict) -> dict:
     """Rounded headline figures of every block of the bench line."""
     r3 = lambda v: None if v is None else float(f"{v:.3g}")
@@ -817,6 +832,8 @@ def run_gpu(args, world, rank, local):
         # reader of the line's tail sees every headline figure
         line["digest"] = digest(line)
         print(json.dumps(line), flush=True)
+        if args.log:
+            append_log(args.log, line, torch)
 
 
 def main():
@@ -830,6 +847,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="fewer depth variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--log", default=None, help="append a JSONL record of the run to this file")
     ap.add_argument("--c3-budget", type=float, default=20.0,
                     help="wall budget (s) of the 8192^2 refinement run to 1e-10")
     ap.add_argument("--traffic", type=float, default=None,

@@ -105,6 +105,18 @@ const char* px_last_error(const px_ctx* ctx);
 /* Static name of a status code. */
 const char* px_status_string(px_status s);
 
+/* Checked build (the library compiled with -DPX_CHECKED into
+ * libprotox_checked.so; the paper has no counterpart): the relaxation and
+ * Euler kernels check every global index they compute against the field's
+ * extent before the access; a violation is counted in a device word, the
+ * first one recorded as (site << 48 | index), and the access is skipped.
+ * px_is_checked_build() is 1 in that build, 0 otherwise.
+ * px_checked_faults synchronises ctx's device, returns the count and the
+ * first violation (first may be NULL) and clears both; in the normal build it
+ * returns PX_EUNSUPPORTED with *count = 0. */
+int px_is_checked_build(void);
+px_status px_checked_faults(px_ctx* ctx, uint64_t* count, uint64_t* first);
+
 /* Per-context kernel selection (the paper has no counterpart: these pick
  * among kernels that compute the same sweeps, for A/B timing and for tests
  * that compare the kernel families bitwise). Defaults (0) are the fastest

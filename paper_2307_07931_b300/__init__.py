@@ -18,7 +18,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
+
 LIB_PATH = os.path.join(HERE, "libprotox.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libprotox_checked.so")  # -DPX_CHECKED variant
 
 PX_OK, PX_EINVAL, PX_ECUDA, PX_ENOMEM, PX_ENOCONV, PX_ETIMEOUT, PX_EMEAN, PX_ENAN, \
     PX_EUNSUPPORTED = range(9)
@@ -118,12 +120,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_cnn_set_wait_limit.argtypes = [_vp, ctypes.c_uint32]
     lib.px_cnn_set_staging.argtypes = [_vp, i]
     lib.px_set_option.argtypes = [_vp, i, i]
+    lib.px_is_checked_build.restype = i
+    lib.px_checked_faults.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.px_get_option.argtypes = [_vp, i, ip]
     eg = ctypes.POINTER(EulerGrid)
     lib.px_euler_step.argtypes = [_vp, eg, _vp, _vp, d, d, i, d, _vp, _vp]
     lib.px_euler_conserved.argtypes = [_vp, eg, _vp, _vp, d, _vp]
     for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_cnn_set_staging",
-                 "px_set_option", "px_get_option",
+                 "px_set_option", "px_get_option", "px_checked_faults",
                  "px_euler_step", "px_euler_conserved"):
         getattr(lib, name).restype = i
     for name in ("px_cnn_get_state", "px_cnn_set_state",
@@ -167,6 +171,13 @@ class Context:
     def set_option(self, option: int, value: int):
         """px_set_option: per-context kernel selection (PX_OPT_*)."""
         self.check(load_library().px_set_option(self.handle, int(option), int(value)))
+
+    def checked_faults(self):
+        """(count, first) of the checked build's bounds violations since the last
+        call (px_checked_faults; PxError PX_EUNSUPPORTED in the normal build)."""
+        cnt, first = ctypes.c_uint64(), ctypes.c_uint64()
+        self.check(load_library().px_checked_faults(self.handle, ctypes.byref(cnt), ctypes.byref(first)))
+        return cnt.value, first.value
 
     def get_option(self, option: int) -> int:
         v = ctypes.c_int()

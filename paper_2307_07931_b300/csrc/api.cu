@@ -17,6 +17,12 @@
 #include <vector>
 
 
+#ifdef PX_CHECKED
+namespace px {
+__device__ unsigned long long g_px_checked[2];  // violations, first (site << 48 | index)
+}
+#endif
+
 namespace {
 
 thread_local std::string g_create_err;
@@ -247,6 +253,35 @@ const char* px_last_error(const px_ctx* c) {
   return c ? c->err.c_str() : g_create_err.c_str();
 }
 
+int px_is_checked_build(void) {
+#ifdef PX_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+px_status px_checked_faults(px_ctx* c, uint64_t* count, uint64_t* first) {
+  if (!c || !count) return PX_EINVAL;
+  c->err.clear();
+#ifdef PX_CHECKED
+  DeviceScope ds(c->device);
+  unsigned long long h[2] = {0, 0};
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(h, px::g_px_checked, sizeof h);
+  const unsigned long long z[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(px::g_px_checked, z, sizeof z);
+  if (e != cudaSuccess) return cuda_fail(c, e, "checked-build fault word");
+  *count = h[0];
+  if (first) *first = h[1];
+  return PX_OK;
+#else
+  *count = 0;
+  if (first) *first = 0;
+  return fail(c, PX_EUNSUPPORTED, "bounds checks are compiled only into the checked build");
+#endif
+}
+
 px_status px_set_option(px_ctx* c, int option, int value) {
   if (!c) return PX_EINVAL;
   c->err.clear();
@@ -275,6 +310,7 @@ px_status px_get_option(const px_ctx* c, int option, int* value) {
 
 px_status px_apply_stencil(px_ctx* c, const px_grid* g, const void* phi, void* lphi,
                            void* stream) {
+  PX_NVTX_RANGE("px_apply_stencil");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::FieldDesc f;
@@ -291,6 +327,7 @@ px_status px_apply_stencil(px_ctx* c, const px_grid* g, const void* phi, void* l
 px_status px_relax_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_out,
                      const void* rho, double omega, int nsweeps, int tblock,
                      double* resid_dev, int report_every, void* stream) {
+  PX_NVTX_RANGE("px_relax_n");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::FieldDesc f;
@@ -367,6 +404,7 @@ static int rb_sweeps(const px_ctx* c) { return c->opt_rb_sweeps > 0 ? c->opt_rb_
 px_status px_rbsor_n(px_ctx* c, const px_grid* g, const void* phi_in, void* phi_out,
                      const void* rho, double omega, int nsweeps, double* resid_dev,
                      int report_every, void* stream) {
+  PX_NVTX_RANGE("px_rbsor_n");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::FieldDesc f;
@@ -480,6 +518,7 @@ cudaError_t rb_sweeps_ab(px_ctx* c, const px::FieldDesc& f, void* a, void* b, vo
 px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, int ncycles,
                       int nu1, int nu2, double omega, int coarse_sweeps, int max_levels,
                       double* resid_dev, void* stream) {
+  PX_NVTX_RANGE("px_mg_solve");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::FieldDesc f;
@@ -606,6 +645,7 @@ px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, i
 px_status px_relax3_n(px_ctx* c, const px_grid3* g, const void* phi_in, void* phi_out,
                       const void* rho, double omega, int nsweeps, double* resid_dev,
                       int report_every, void* stream) {
+  PX_NVTX_RANGE("px_relax3_n");
   if (!c) return PX_EINVAL;
   c->err.clear();
   if (!g) return fail(c, PX_EINVAL, "grid is NULL");
@@ -698,6 +738,7 @@ px_status px_relax_plan(px_ctx* c, const px_grid* g, const void* phi_in,
 
 px_status px_residual_norm_async(px_ctx* c, const px_grid* g, const void* phi,
                                  const void* rho, double* out_dev, void* stream) {
+  PX_NVTX_RANGE("px_residual_norm_async");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::FieldDesc f;
@@ -712,6 +753,7 @@ px_status px_residual_norm_async(px_ctx* c, const px_grid* g, const void* phi,
 
 px_status px_residual_norm(px_ctx* c, const px_grid* g, const void* phi, const void* rho,
                            double* out_host, double* rho_norm_host, void* stream) {
+  PX_NVTX_RANGE("px_residual_norm");
   if (!c) return PX_EINVAL;
   if (!out_host) return fail(c, PX_EINVAL, "out_host is NULL");
   px_status s = px_residual_norm_async(c, g, phi, rho, c->red, stream);
@@ -767,6 +809,7 @@ extern "C" {
 px_status px_euler_step(px_ctx* c, const px_euler_grid* g, const void* u_in, void* u_out,
                         double gamma, double cfl, int nsteps, double dt_fixed, double* dt_dev,
                         void* stream) {
+  PX_NVTX_RANGE("px_euler_step");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::EulerDesc d;
@@ -824,6 +867,7 @@ px_status px_euler_step(px_ctx* c, const px_euler_grid* g, const void* u_in, voi
 
 px_status px_euler_conserved(px_ctx* c, const px_euler_grid* g, const void* w, void* u,
                              double gamma, void* stream) {
+  PX_NVTX_RANGE("px_euler_conserved");
   if (!c) return PX_EINVAL;
   c->err.clear();
   px::EulerDesc d;
@@ -860,6 +904,7 @@ px_status sync_norms(px_ctx* c, const px::FieldDesc& f, const void* phi, const v
 
 extern "C" px_status px_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho,
                               const px_solve_opts* o, px_solve_info* info, void* stream) {
+  PX_NVTX_RANGE("px_solve");
   if (!c) return PX_EINVAL;
   c->err.clear();
   const auto t0 = std::chrono::steady_clock::now();

@@ -241,6 +241,7 @@ extern "C" {
 
 px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, double omega,
                         int report_every, const char* tune_cache, int tune, px_batch** out) {
+  PX_NVTX_RANGE("px_batch_plan");
   if (!c) return PX_EINVAL;
   c->err.clear();
   if (!out) return px::ctx_fail(c, PX_EINVAL, "out is NULL");
@@ -515,6 +516,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
 
 px_status px_batch_run(px_batch* b, void* const* phis, const void* const* rhos,
                        double* resid_dev, void* stream) {
+  PX_NVTX_RANGE("px_batch_run");
   if (!b) return PX_EINVAL;
   px_ctx* c = b->ctx;
   c->err.clear();

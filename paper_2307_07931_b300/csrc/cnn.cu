@@ -1409,6 +1409,7 @@ px_status px_cnn_set_state(px_cnn* n, const float* host, size_t count, int64_t s
 }
 
 px_status px_cnn_forward(px_cnn* n, const float* x, float* y, int B, int H, int W, void* stream) {
+  PX_NVTX_RANGE("px_cnn_forward");
   if (!n || !x || !y) return PX_EINVAL;
   n->ctx->err.clear();
   px_status s = check_shape(n, B, H, W);
@@ -1421,6 +1422,7 @@ px_status px_cnn_forward(px_cnn* n, const float* x, float* y, int B, int H, int 
 
 px_status px_cnn_grads(px_cnn* n, const float* x, const float* t, int B, int H, int W,
                        float* grads_host, double* loss_host, void* stream) {
+  PX_NVTX_RANGE("px_cnn_grads");
   if (!n || !x || !t) return PX_EINVAL;
   n->ctx->err.clear();
   px_status s = check_shape(n, B, H, W);
@@ -1447,6 +1449,7 @@ px_status px_cnn_grads(px_cnn* n, const float* x, const float* t, int B, int H, 
 
 px_status px_cnn_train_step(px_cnn* n, const float* x, const float* t, int B, int H, int W,
                             float lr, double* loss_host, void* stream) {
+  PX_NVTX_RANGE("px_cnn_train_step");
   if (!n || !x || !t || !(lr >= 0.0f)) return PX_EINVAL;
   n->ctx->err.clear();
   px_status s = check_shape(n, B, H, W);
@@ -1473,6 +1476,7 @@ px_status px_cnn_train_step(px_cnn* n, const float* x, const float* t, int B, in
 
 px_status px_cnn_prepare(px_cnn* n, const double* rho, const double* phi, float* x, float* t,
                          int B, int H, int W, double h, double* scales_host, void* stream) {
+  PX_NVTX_RANGE("px_cnn_prepare");
   if (!n || !rho || !x || (phi && !t) || !(h > 0)) return PX_EINVAL;
   n->ctx->err.clear();
   DevScope ds(n->ctx->device);
@@ -1490,6 +1494,7 @@ px_status px_cnn_prepare(px_cnn* n, const double* rho, const double* phi, float*
 
 px_status px_cnn_guess(px_cnn* n, const double* rho, double* phi0, int B, int H, int W, double h,
                        void* stream) {
+  PX_NVTX_RANGE("px_cnn_guess");
   if (!n || !rho || !phi0 || !(h > 0)) return PX_EINVAL;
   n->ctx->err.clear();
   px_status s = check_shape(n, B, H, W);

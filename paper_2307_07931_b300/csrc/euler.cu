@@ -170,6 +170,7 @@ __device__ __forceinline__ void prefetch_tile(ESmem<T>& S, const T* src, int til
     const int gx = near_x ? wrap1(x0 + lx - kEHalo, nx) : wrapn(x0 + lx - kEHalo, nx);
     const int gy = near_y ? wrap1(y0 + ly - kEHalo, ny) : wrapn(y0 + ly - kEHalo, ny);
     const int64_t o = (int64_t)gy * ld + gx;
+    if (!PX_IN_RANGE(21, gx, 0, nx) || !PX_IN_RANGE(22, gy, 0, ny)) continue;
 #pragma unroll
     for (int m = 0; m < 4; ++m) cp_async_elem<sizeof(T)>(&S.raw[m][q], src + m * cs + o);
   }
@@ -245,6 +246,7 @@ euler_stage_k(EParams<T> P) {
       const int j = q / kETX, i = q - j * kETX;
       const int gx = x0 + i, gy = y0 + j;
       if (gx >= P.nx || gy >= P.ny) continue;
+      if (!PX_IN_RANGE(23, gx, 0, P.nx) || !PX_IN_RANGE(24, gy, 0, P.ny)) continue;
       const int64_t o = (int64_t)gy * P.ld + gx;
       T nv[4];
 #pragma unroll

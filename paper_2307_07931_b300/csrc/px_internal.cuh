@@ -4,9 +4,38 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace px {
 
+// NVTX range around a library call (header-only NVTX: no effect and no
+// library dependency unless a profiler attaches), named after the call.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define PX_NVTX_RANGE(name) ::px::NvtxRange px_nvtx_range_(name)
+
 constexpr int kWarp = 32;
+
+// Bounds checks of the checked build (compiled with -DPX_CHECKED; the
+// sanitizer's stand-in): an index outside [lo, hi) is counted in a device
+// word, the first one recorded (site << 48 | index), and the access skipped.
+// In the normal build the check is the constant true and costs nothing.
+#ifdef PX_CHECKED
+extern __device__ unsigned long long g_px_checked[2];
+__device__ __forceinline__ bool in_range(int site, int64_t v, int64_t lo, int64_t hi) {
+  if (v >= lo && v < hi) return true;
+  if (atomicAdd(&g_px_checked[0], 1ull) == 0ull)
+    g_px_checked[1] = ((unsigned long long)site << 48) | ((unsigned long long)v & 0xffffffffffffull);
+  return false;
+}
+#define PX_IN_RANGE(site, v, lo, hi) ::px::in_range((site), (int64_t)(v), (int64_t)(lo), (int64_t)(hi))
+#else
+#define PX_IN_RANGE(site, v, lo, hi) true
+#endif
 
 // Periodic index for i in [-n, 2n).
 __device__ __forceinline__ int wrap1(int i, int n) {

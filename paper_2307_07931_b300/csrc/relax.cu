@@ -119,10 +119,11 @@ relax1_stream(const T* __restrict__ phi, T* __restrict__ out, const T* __restric
     const int j0 = seg * ry, j1 = min(j0 + ry, ny);
 
     auto load_row = [&](int j, RowReg<T, V>& rr) {
-      const T* rp = phi + (int64_t)wrap1(j, ny) * ld;
-      ldv<T, V>(rr.v, rp + xc);
-      if (need_l) rr.el = rp[xl];
-      if (need_r) rr.er = rp[xr];
+      const int jw = wrap1(j, ny);
+      const T* rp = phi + (int64_t)jw * ld;
+      if (PX_IN_RANGE(1, jw, 0, ny) && PX_IN_RANGE(2, xc, 0, nx - V + 1)) ldv<T, V>(rr.v, rp + xc);
+      if (need_l && PX_IN_RANGE(3, xl, 0, nx)) rr.el = rp[xl];
+      if (need_r && PX_IN_RANGE(4, xr, 0, nx)) rr.er = rp[xr];
     };
     RowReg<T, V> up, cur, dn, pf;
     T rh0[V], rh1[V];
@@ -154,7 +155,7 @@ relax1_stream(const T* __restrict__ phi, T* __restrict__ out, const T* __restric
         o[i] = fma(k.c, r, cur.v[i]);
         if (kRep && valid) mx = umax(mx, absbits(r));
       }
-      if (valid) {
+      if (valid && PX_IN_RANGE(5, j, 0, ny) && PX_IN_RANGE(6, x, 0, nx - V + 1)) {
         T* op = out + (int64_t)j * ld + x;
         if constexpr (V == 1) {
           op[0] = o[0];
@@ -864,7 +865,7 @@ struct R2Task {
 template <int TB, int P, bool kEdge, bool kRB, bool kPack>
 __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
                                        const float* __restrict__ rho, float* __restrict__ out,
-                                       float* ring, int ny, int64_t ld, int gx, bool own,
+                                       float* ring, int nx, int ny, int64_t ld, int gx, bool own,
                                        const R2Task& T, Coef<float> k, const bool (&due)[TB]) {
   constexpr int W = 128;                      // strip floats per ring row
   float* const pr = ring;                     // phi ring, this lane's columns
@@ -875,10 +876,13 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
     S.rl = S.rl + 1 == ny ? 0 : S.rl + 1;
     const int64_t g1 = (int64_t)S.rl * ld + gx;
     S.rl = S.rl + 1 == ny ? 0 : S.rl + 1;
-    cp16(pr + (la & (kRPhiRing - 1)) * W, phi + g0);
-    cp16(pr + ((la + 1) & (kRPhiRing - 1)) * W, phi + g1);
-    cp16(rr_ + (la & (kRRhoRing - 1)) * W, rho + g0);
-    cp16(rr_ + ((la + 1) & (kRRhoRing - 1)) * W, rho + g1);
+    if (PX_IN_RANGE(11, g0, 0, (int64_t)(ny - 1) * ld + nx - 3) &&
+        PX_IN_RANGE(12, g1, 0, (int64_t)(ny - 1) * ld + nx - 3)) {
+      cp16(pr + (la & (kRPhiRing - 1)) * W, phi + g0);
+      cp16(pr + ((la + 1) & (kRPhiRing - 1)) * W, phi + g1);
+      cp16(rr_ + (la & (kRRhoRing - 1)) * W, rho + g0);
+      cp16(rr_ + ((la + 1) & (kRRhoRing - 1)) * W, rho + g1);
+    }
   }
   cp_commit();
   cp_wait<kR2Ahead>();
@@ -966,9 +970,9 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
     } else if (own) {
       // level-TB row index j is global row y0 + j - TB
       const int yo = T.y0 + r0 - 2 * TB;
-      if (yo >= T.y0 && yo < T.lim)
+      if (yo >= T.y0 && yo < T.lim && PX_IN_RANGE(13, yo, 0, ny) && PX_IN_RANGE(14, gx, 0, nx - 3))
         *reinterpret_cast<float4*>(out + (int64_t)yo * ld + gx) = make_float4(o0[0], o0[1], o0[2], o0[3]);
-      if (yo + 1 >= T.y0 && yo + 1 < T.lim)
+      if (yo + 1 >= T.y0 && yo + 1 < T.lim && PX_IN_RANGE(15, yo + 1, 0, ny))
         *reinterpret_cast<float4*>(out + (int64_t)(yo + 1) * ld + gx) =
             make_float4(o1[0], o1[1], o1[2], o1[3]);
     }
@@ -1107,16 +1111,16 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
 #pragma unroll 1
     for (; r0 < kPro; r0 += 4) {
       if (!ready(r0)) goto task_done;
-      rstep2<TB, 0, true, kRB, kPack>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, true, kRB, kPack>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) goto task_done;
-      rstep2<TB, 1, true, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, true, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
     }
 #pragma unroll 1
     for (;; r0 += 4) {
       if (!ready(r0)) break;
-      rstep2<TB, 0, false, kRB, kPack>(S, r0, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, false, kRB, kPack>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) break;
-      rstep2<TB, 1, false, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, false, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
     }
   task_done:
     cp_wait<0>();  // the next task's prologue reuses the ring slots

@@ -109,6 +109,7 @@ extern "C" px_status px_relax_n_static(const px_grid* g, const void* phi_in, voi
                                        const void* rho, double omega, int nsweeps,
                                        int tblock, double* resid_dev, int report_every,
                                        void* stream) {
+  PX_NVTX_RANGE("px_relax_n_static");
   px::unbound_clear();
   px::FieldDesc f;
   px_status s = px::unbound_check_grid(g, &f);
