@@ -381,3 +381,35 @@ def test_full_size_sampled(px, dtype):
         c = slice(m, size - m)
         assert np.max(np.abs(got[c, c] - ref[c, c])) <= tol * scale, (j0, i0)
     del o, rho64
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_full_size_every_report_and_state(px, dtype):
+    """The same 16384^2 workload and launch configuration (automatic depth:
+    the FP32 register wavefront at depth 8 with run-time row balancing, or
+    the FP64 streaming kernel), eight sweeps with a report every sweep,
+    against the serial FP64 oracle run on the whole field: every report
+    (states 0..7, not only state 0) and every cell of the final state."""
+    n = 16384
+    h = 1.0 / n
+    rho64 = synth.large_field_rho(n)
+    rho_t = dev(rho64, dtype)
+    rho = host(rho_t)
+    del rho64
+    phi = torch.zeros_like(rho_t)
+    out = torch.empty_like(rho_t)
+    nsw = 8
+    resid = torch.zeros(nsw, dtype=torch.float64, device="cuda")
+    px.relax_n(phi, out, rho_t, h, OMEGA, nsw, 0, resid, 1)
+    torch.cuda.synchronize()
+    got_rep = resid.cpu().numpy()
+    del phi, rho_t
+    ref, ref_rep = oracle.relax_n(np.zeros_like(rho), rho, h, OMEGA, nsw, 1)
+    got = out.cpu().numpy().astype(np.float64)
+    del out
+    tol = (2e-6 if dtype == torch.float32 else 1e-12) * nsw
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= tol * scale
+    sc = 8 * scale / h**2 + np.max(np.abs(rho))
+    assert np.all(np.abs(got_rep - ref_rep) <= tol * sc), (got_rep, ref_rep)
+    assert got_rep[0] == np.max(np.abs(rho))
