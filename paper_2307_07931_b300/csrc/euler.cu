@@ -107,36 +107,41 @@ __device__ __forceinline__ void face_flux(const T (&b)[4], const T (&sb)[4], con
 }
 
 // Fluxes of a run of consecutive faces along one line of the shared tile:
-// faces f0 .. f0 + nf - 1, face f lying between the cells at line positions
-// f + 1 and f + 2 (position p of the line is element base + p * step). The
-// cell window slides along the line, so each cell is read once and its slope
-// computed once for the run. Flux of face f goes to out + f * ostep.
-template <typename T, bool kXFace>
-__device__ __forceinline__ void face_run(const T* base, int step, int plane, int f0, int nf,
-                                         T* out, int ostep, int oplane, T gamma, T igm1) {
-  T w0[4], w1[4], w2[4], s1[4], s2[4];
+// faces f0 .. f0 + nf - 1 (nf = 4 or 5), face f lying between the cells at
+// line positions f + 1 and f + 2 (position p of the line is element
+// base + p * step). The cell window slides along the line, so each cell is
+// read once and its slope computed once for the run; the loop is unrolled
+// (the window's shift is register renaming, the offsets immediates) and the
+// fifth face is predicated. Flux of face f goes to out + f * ostep.
+template <typename T, bool kXFace, int kStep, int kPlane, int kOStep, int kOPlane>
+__device__ __forceinline__ void face_run(const T* base, int f0, int nf, T* out, T gamma, T igm1) {
+  const T* b0 = base + f0 * kStep;
+  T* o0 = out + f0 * kOStep;
+  T w0[4], w1[4], w2[4], s1[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    w0[m] = base[m * plane + f0 * step];
-    w1[m] = base[m * plane + (f0 + 1) * step];
-    w2[m] = base[m * plane + (f0 + 2) * step];
+    w0[m] = b0[m * kPlane];
+    w1[m] = b0[m * kPlane + kStep];
+    w2[m] = b0[m * kPlane + 2 * kStep];
     s1[m] = minmod(w1[m] - w0[m], w2[m] - w1[m]);
   }
-  for (int k = 0; k < nf; ++k) {
-    const int f = f0 + k;
-    T w3[4], fl[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      w3[m] = base[m * plane + (f + 3) * step];
-      s2[m] = minmod(w2[m] - w1[m], w3[m] - w2[m]);
-    }
-    face_flux<T, kXFace>(w1, s1, w2, s2, gamma, igm1, fl);
+  for (int k = 0; k < 5; ++k) {
+    if (k < nf) {
+      T w3[4], s2[4], fl[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      out[m * oplane + f * ostep] = fl[m];
-      w1[m] = w2[m];
-      w2[m] = w3[m];
-      s1[m] = s2[m];
+      for (int m = 0; m < 4; ++m) {
+        w3[m] = b0[m * kPlane + (k + 3) * kStep];
+        s2[m] = minmod(w2[m] - w1[m], w3[m] - w2[m]);
+      }
+      face_flux<T, kXFace>(w1, s1, w2, s2, gamma, igm1, fl);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        o0[m * kOPlane + k * kOStep] = fl[m];
+        w1[m] = w2[m];
+        w2[m] = w3[m];
+        s1[m] = s2[m];
+      }
     }
   }
 }
@@ -232,12 +237,12 @@ euler_stage_k(EParams<T> P) {
       const int warp = tid >> 5, lane = tid & 31;
       if (warp < 4) {
         const int j = 4 * warp + (lane >> 3), sg = lane & 7;
-        face_run<T, true>(&S.w[0][j + kEHalo][0], 1, kEWY * kEWP, 4 * sg, sg == 7 ? 5 : 4,
-                          &S.fx[0][j][0], 1, kETY * (kETX + 1), P.gamma, P.igm1);
+        face_run<T, true, 1, kEWY * kEWP, 1, kETY * (kETX + 1)>(
+            &S.w[0][j + kEHalo][0], 4 * sg, sg == 7 ? 5 : 4, &S.fx[0][j][0], P.gamma, P.igm1);
       } else {
         const int i = lane, sg = warp - 4;
-        face_run<T, false>(&S.w[0][0][i + kEHalo], kEWP, kEWY * kEWP, 4 * sg, sg == 3 ? 5 : 4,
-                           &S.fy[0][0][i], kETX, (kETY + 1) * kETX, P.gamma, P.igm1);
+        face_run<T, false, kEWP, kEWY * kEWP, kETX, (kETY + 1) * kETX>(
+            &S.w[0][0][i + kEHalo], 4 * sg, sg == 3 ? 5 : 4, &S.fy[0][0][i], P.gamma, P.igm1);
       }
     }
     __syncthreads();

@@ -248,7 +248,8 @@ def main():
         logf.flush()
 
     px.load_library()
-    res = {"config": {k: v for k, v in vars(a).items() if k != "out"}, "grid": N, "omega": OMEGA}
+    res = {"config": {k: v for k, v in vars(a).items() if k not in ("out", "ckpt")}, "grid": N,
+           "omega": OMEGA}
     t0 = time.perf_counter()
     rho_tr = make_fields_gpu(torch, TRAIN_SEED, a.train)
     rho_ev = make_fields_gpu(torch, EVAL_SEED, a.eval)
