@@ -23,7 +23,10 @@
 // Grid-stride over tiles, one resident wave of CTAs.
 #include "px_internal.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstring>
 
 namespace px {
 namespace {
@@ -34,9 +37,17 @@ constexpr int kEThreads = 256;
 
 constexpr int kEWP = kEWX + 1;  // row pitch 37: the x-face threads of a warp (4 rows x 8
                                 // segments 4 cells apart) hit 32 different banks
+// Raw rows of the next tile: the halo's first column sits at kRawOff so that
+// the row starts on a 16-byte boundary of the field when the tile is copied
+// as one tensor-memory-accelerator box (x0 is a multiple of 32).
+template <typename T> struct RawGeom {
+  static constexpr int kOff = sizeof(T) == 4 ? 2 : 0;  // x0 - 2 - kOff is 16-byte aligned
+  static constexpr int kW = kEWX + 2 * kOff;          // 40 (FP32) or 36 (FP64) columns
+};
+
 template <typename T>
 struct ESmem {
-  T raw[4][kEWY * kEWX];     // conserved values of the next tile + halo (cp.async prefetch)
+  T raw[4][kEWY][RawGeom<T>::kW];  // conserved values of the next tile + halo
   T w[4][kEWY][kEWP];        // primitives rho, u, v, p of the tile and its halo
   T fx[4][kETY][kETX + 1];   // x-face fluxes: fx[.][j][k] at face k - 1/2 of row j
   T fy[4][kETY + 1][kETX];   // y-face fluxes: fy[.][j][i] at face j - 1/2 of column i
@@ -77,6 +88,8 @@ struct EParams {
   double* wave_next;   // stage 1 zeroes it, stage 2 folds the new state's max into it
   double* dt_out;      // this step's dt (stage 1 writes it) or null
   int tiles_x, ntiles;
+  int use_tma;         // tmap describes the stage's source planes
+  CUtensorMap tmap;    // (x, y, plane) boxes of kW x 20 x 4
 };
 
 // Rusanov flux through one face from the cells b | c that straddle it and
@@ -163,13 +176,34 @@ __device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
 }
 
 // Issue the copies of one tile and its two-cell periodic halo (four planes)
-// into S.raw, one commit group.
+// into S.raw. A tile whose halo lies inside the field is one box of the
+// tensor memory accelerator (kW x 20 x 4 planes), issued by thread 0 on the
+// CTA's barrier `bar` (expect-tx bytes); returns true. Otherwise every cell
+// is a cp.async of its own (the periodic images), one commit group; false.
 template <typename T>
-__device__ __forceinline__ void prefetch_tile(ESmem<T>& S, const T* src, int tile, int tiles_x,
+__device__ __forceinline__ bool prefetch_tile(ESmem<T>& S, const T* src, int tile, int tiles_x,
                                               int nx, int ny, int64_t ld, int64_t cs,
-                                              bool near_x, bool near_y) {
+                                              bool near_x, bool near_y, const CUtensorMap* tmap,
+                                              bool use_tma, uint32_t bar) {
+  using RG = RawGeom<T>;
   const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
   const int x0 = tx * kETX, y0 = ty * kETY;
+  const int xs = x0 - kEHalo - RG::kOff, ys = y0 - kEHalo;
+  if (use_tma && xs >= 0 && xs + RG::kW <= nx && ys >= 0 && ys + kEWY <= ny) {
+    if (threadIdx.x == 0) {
+      // the buffer's earlier (generic) reads are ordered before the async copy
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   ::"r"(bar), "r"((uint32_t)(4 * kEWY * RG::kW * sizeof(T))) : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3, %4}], [%5];"
+          ::"r"((uint32_t)__cvta_generic_to_shared(&S.raw[0][0][0])),
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(xs), "r"(ys), "r"(0), "r"(bar)
+          : "memory");
+    }
+    return true;
+  }
   for (int q = threadIdx.x; q < kEWX * kEWY; q += kEThreads) {
     const int ly = q / kEWX, lx = q - ly * kEWX;
     const int gx = near_x ? wrap1(x0 + lx - kEHalo, nx) : wrapn(x0 + lx - kEHalo, nx);
@@ -177,9 +211,24 @@ __device__ __forceinline__ void prefetch_tile(ESmem<T>& S, const T* src, int til
     const int64_t o = (int64_t)gy * ld + gx;
     if (!PX_IN_RANGE(21, gx, 0, nx) || !PX_IN_RANGE(22, gy, 0, ny)) continue;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) cp_async_elem<sizeof(T)>(&S.raw[m][q], src + m * cs + o);
+    for (int m = 0; m < 4; ++m)
+      cp_async_elem<sizeof(T)>(&S.raw[m][ly][lx + RG::kOff], src + m * cs + o);
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
+  return false;
+}
+
+// Bounded wait for a tile box's bytes (phase `parity` of `bar`); false if the
+// limit ran out (the results are then meaningless and the next step's wave
+// speed is set to NaN, which makes its dt and state NaN).
+__device__ __forceinline__ bool wait_box(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
 }
 
 __device__ __forceinline__ uint64_t dbits(double v) {
@@ -188,11 +237,20 @@ __device__ __forceinline__ uint64_t dbits(double v) {
 
 template <typename T, int kStage>
 __global__ void __launch_bounds__(kEThreads)
-euler_stage_k(EParams<T> P) {
-  extern __shared__ __align__(16) unsigned char esm_raw[];
+euler_stage_k(const __grid_constant__ EParams<T> P) {
+  extern __shared__ __align__(128) unsigned char esm_raw[];
   ESmem<T>& S = *reinterpret_cast<ESmem<T>*>(esm_raw);
   __shared__ uint64_t wmax_s[kEThreads / 32];
+  __shared__ __align__(8) uint64_t box_bar;
   const int tid = threadIdx.x;
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&box_bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t box_parity = 0;
+  bool box_pending = false, box_fault = false;
   // this step's dt
   double dtd = P.dt_fixed;
   if (!(dtd > 0.0)) dtd = P.cfl / *P.wave_cur;
@@ -206,30 +264,38 @@ euler_stage_k(EParams<T> P) {
   uint64_t wm = 0;
 
   if ((int)blockIdx.x < P.ntiles)
-    prefetch_tile(S, src, blockIdx.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x, near_y);
+    box_pending = prefetch_tile(S, src, blockIdx.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x,
+                                near_y, &P.tmap, P.use_tma, bar);
   for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
     const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
     const int x0 = tx * kETX, y0 = ty * kETY;
     // this tile's copies have landed (each thread waits for its own, the
     // barrier for everyone's); the previous tile's fluxes are consumed
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (box_pending) {
+      if (!wait_box(bar, box_parity)) box_fault = true;
+      box_parity ^= 1u;
+    } else {
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
     __syncthreads();
     // ---- primitives of the tile + halo
     for (int q = tid; q < kEWX * kEWY; q += kEThreads) {
-      const int ly = q / kEWX, lx = q - ly * kEWX;
-      const T r = S.raw[0][q], mx = S.raw[1][q], my = S.raw[2][q], e = S.raw[3][q];
+      const int ly = q / kEWX, lx = q - ly * kEWX + RawGeom<T>::kOff;
+      const T r = S.raw[0][ly][lx], mx = S.raw[1][ly][lx], my = S.raw[2][ly][lx],
+              e = S.raw[3][ly][lx];
       const T ir = recip(r);
       const T u = mx * ir, v = my * ir;
-      S.w[0][ly][lx] = r;
-      S.w[1][ly][lx] = u;
-      S.w[2][ly][lx] = v;
-      S.w[3][ly][lx] = P.gm1 * (e - T(0.5) * r * (u * u + v * v));
+      const int wx = lx - RawGeom<T>::kOff;
+      S.w[0][ly][wx] = r;
+      S.w[1][ly][wx] = u;
+      S.w[2][ly][wx] = v;
+      S.w[3][ly][wx] = P.gm1 * (e - T(0.5) * r * (u * u + v * v));
     }
     __syncthreads();
     // the raw buffer is free: start the next tile's copies under this tile's fluxes
     if (tile + (int)gridDim.x < P.ntiles)
-      prefetch_tile(S, src, tile + (int)gridDim.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x,
-                    near_y);
+      box_pending = prefetch_tile(S, src, tile + (int)gridDim.x, P.tiles_x, P.nx, P.ny, P.ld,
+                                  P.cs, near_x, near_y, &P.tmap, P.use_tma, bar);
     // ---- face fluxes. Warps 0-3: x faces, one run of 4 faces (5 for the last
     // segment of a row) per thread, rows 4w + lane / 8, segment lane % 8.
     // Warps 4-7: y faces, column lane, segment w - 4 of 4 faces (5 last).
@@ -270,6 +336,7 @@ euler_stage_k(EParams<T> P) {
         wm = umax(wm, dbits(wave_speed(nv[0], nv[1], nv[2], nv[3], P.gamma, P.gm1, P.idx, P.idy)));
     }
   }
+  if (box_fault && P.wave_next) atomic_max_bits(P.wave_next, 0x7ff8000000000000ull);  // NaN
   if (kStage == 2 && P.wave_next) {
     wm = warp_max(wm);
     if ((tid & 31) == 0) wmax_s[tid >> 5] = wm;
@@ -338,6 +405,48 @@ cudaError_t euler_setup_t() {
   return e;
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+// cuTensorMapEncodeTiled through the runtime's driver entry point; null if
+// unavailable (the per-cell copies are used then).
+EncodeTiledFn euler_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    cudaGetLastError();
+    resolved = true;
+  }
+  return fn;
+}
+
+// Tensor map of the four planes of a state for tile boxes (kW x 20 x 4); false
+// if the layout does not allow one (pitches not multiples of 16 bytes, a field
+// narrower than the box, a misaligned base) or the driver cannot encode it.
+template <typename T>
+bool euler_tensor_map(CUtensorMap* m, const EulerDesc& g, const T* base) {
+  std::memset(m, 0, sizeof *m);
+  const EncodeTiledFn enc = euler_encoder();
+  const int64_t es = sizeof(T);
+  if (!enc || ((uintptr_t)base & 15u) || (g.ld * es) % 16 || (g.cs * es) % 16 ||
+      g.nx < RawGeom<T>::kW || g.ny < kEWY)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)(g.ld * es), (cuuint64_t)(g.cs * es)};
+  const cuuint32_t box[3] = {(cuuint32_t)RawGeom<T>::kW, (cuuint32_t)kEWY, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+             3, const_cast<T*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T>
 cudaError_t euler_step_t(const EulerDesc& g, const T* u0, T* out, T* s1, double gamma, double cfl,
                          double dt_fixed, double* wave_cur, double* wave_next, double* dt_out,
@@ -378,12 +487,14 @@ cudaError_t euler_step_t(const EulerDesc& g, const T* u0, T* out, T* s1, double 
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)occ * device_sm_count());
   // stage 1: u0 -> s1
   P.out = s1;
+  P.use_tma = euler_tensor_map<T>(&P.tmap, g, u0) ? 1 : 0;
   euler_stage_k<T, 1><<<grid, kEThreads, sizeof(ESmem<T>), st>>>(P);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // stage 2: (u0, s1) -> out, max wave speed of out -> wave_next
   P.out = out;
   P.dt_out = nullptr;
+  P.use_tma = euler_tensor_map<T>(&P.tmap, g, s1) ? 1 : 0;
   euler_stage_k<T, 2><<<grid, kEThreads, sizeof(ESmem<T>), st>>>(P);
   return cudaGetLastError();
 }

@@ -62,7 +62,8 @@ def rel_err(got, ref):
     return max(float(np.max(np.abs(got[m] - ref[m])) / np.max(np.abs(ref[m]))) for m in range(4))
 
 
-SHAPES = [(64, 48), (130, 70), (33, 17), (8, 8), (1, 5), (200, 3), (36, 20), (35, 19), (97, 161)]
+SHAPES = [(64, 48), (130, 70), (33, 17), (8, 8), (1, 5), (200, 3), (36, 20), (35, 19), (97, 161),
+          (256, 96)]
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
@@ -163,6 +164,28 @@ def test_pitched_layout_bitwise(px):
     px.euler_step(U0, packed, 1 / 75, 1 / 37, 3)
     torch.cuda.synchronize()
     assert torch.equal(p_out, packed)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_box_and_per_cell_staging_bitwise(px, dtype):
+    """Tiles whose halo lies inside the field arrive as one tensor-memory-
+    accelerator box when the row and plane pitches are multiples of 16 bytes;
+    a row pitch of nx + 1 elements forces the per-cell copies everywhere. The
+    staged values are the same, so the states and time steps are bitwise equal."""
+    rng = np.random.default_rng(10)
+    nx, ny = 256, 200
+    U0 = torch.from_numpy(blocky_state(rng, ny, nx)).to(dtype).cuda()
+    a = torch.empty_like(U0)
+    da = torch.zeros(3, dtype=torch.float64, device="cuda")
+    px.euler_step(U0, a, 1 / nx, 1 / ny, 3, dt=da)
+    big = torch.zeros(4, ny, nx + 1, dtype=dtype, device="cuda")
+    p_in = big[:, :, :nx]
+    p_in.copy_(U0)
+    p_out = torch.zeros(4, ny, nx + 1, dtype=dtype, device="cuda")[:, :, :nx]
+    db = torch.zeros(3, dtype=torch.float64, device="cuda")
+    px.euler_step(p_in, p_out, 1 / nx, 1 / ny, 3, dt=db)
+    torch.cuda.synchronize()
+    assert torch.equal(a, p_out) and torch.equal(da, db)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
