@@ -51,7 +51,13 @@ struct ESmem {
   T w[4][kEWY][kEWP];        // primitives rho, u, v, p of the tile and its halo
   T fx[4][kETY][kETX + 1];   // x-face fluxes: fx[.][j][k] at face k - 1/2 of row j
   T fy[4][kETY + 1][kETX];   // y-face fluxes: fy[.][j][i] at face j - 1/2 of column i
+  uint64_t wmax[kEThreads / 32];  // per-warp wave-speed maxima (stage 2)
+  uint64_t bar;                   // completion barrier of the box copy
 };
+// raw must start on a 128-byte boundary for the box copy; the kernel declares
+// no static shared variables, so it sits at the dynamic block's start.
+static_assert(sizeof(ESmem<float>::raw) % 128 == 0 && sizeof(ESmem<double>::raw) % 128 == 0,
+              "raw is followed by the other arrays");
 
 // Reciprocal and sound speed sqrt(g p / rho) (g p passed as gp). FP64 takes
 // the IEEE operations; FP32 takes the hardware approximations (relative error
@@ -238,12 +244,16 @@ __device__ __forceinline__ uint64_t dbits(double v) {
 template <typename T, int kStage>
 __global__ void __launch_bounds__(kEThreads)
 euler_stage_k(const __grid_constant__ EParams<T> P) {
+  // no static shared variables: S.raw, the box copy's destination, must start
+  // on a 128-byte boundary, and the tensor map on a 64-byte one; if either
+  // does not, every tile takes the per-cell copies
   extern __shared__ __align__(128) unsigned char esm_raw[];
   ESmem<T>& S = *reinterpret_cast<ESmem<T>*>(esm_raw);
-  __shared__ uint64_t wmax_s[kEThreads / 32];
-  __shared__ __align__(8) uint64_t box_bar;
   const int tid = threadIdx.x;
-  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&box_bar);
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&S.bar);
+  const bool use_tma = P.use_tma &&
+                       ((uint32_t)__cvta_generic_to_shared(&S.raw[0][0][0]) & 127u) == 0 &&
+                       (reinterpret_cast<uintptr_t>(&P.tmap) & 63u) == 0;
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -265,7 +275,7 @@ euler_stage_k(const __grid_constant__ EParams<T> P) {
 
   if ((int)blockIdx.x < P.ntiles)
     box_pending = prefetch_tile(S, src, blockIdx.x, P.tiles_x, P.nx, P.ny, P.ld, P.cs, near_x,
-                                near_y, &P.tmap, P.use_tma, bar);
+                                near_y, &P.tmap, use_tma, bar);
   for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
     const int ty = tile / P.tiles_x, tx = tile - ty * P.tiles_x;
     const int x0 = tx * kETX, y0 = ty * kETY;
@@ -295,7 +305,7 @@ euler_stage_k(const __grid_constant__ EParams<T> P) {
     // the raw buffer is free: start the next tile's copies under this tile's fluxes
     if (tile + (int)gridDim.x < P.ntiles)
       box_pending = prefetch_tile(S, src, tile + (int)gridDim.x, P.tiles_x, P.nx, P.ny, P.ld,
-                                  P.cs, near_x, near_y, &P.tmap, P.use_tma, bar);
+                                  P.cs, near_x, near_y, &P.tmap, use_tma, bar);
     // ---- face fluxes. Warps 0-3: x faces, one run of 4 faces (5 for the last
     // segment of a row) per thread, rows 4w + lane / 8, segment lane % 8.
     // Warps 4-7: y faces, column lane, segment w - 4 of 4 faces (5 last).
@@ -339,12 +349,12 @@ euler_stage_k(const __grid_constant__ EParams<T> P) {
   if (box_fault && P.wave_next) atomic_max_bits(P.wave_next, 0x7ff8000000000000ull);  // NaN
   if (kStage == 2 && P.wave_next) {
     wm = warp_max(wm);
-    if ((tid & 31) == 0) wmax_s[tid >> 5] = wm;
+    if ((tid & 31) == 0) S.wmax[tid >> 5] = wm;
     __syncthreads();
     if (tid == 0) {
       uint64_t m = 0;
 #pragma unroll
-      for (int w = 0; w < kEThreads / 32; ++w) m = umax(m, wmax_s[w]);
+      for (int w = 0; w < kEThreads / 32; ++w) m = umax(m, S.wmax[w]);
       atomic_max_bits(P.wave_next, m);
     }
   }
