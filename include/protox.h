@@ -433,7 +433,8 @@ px_status px_cnn_guess(px_cnn* net, const double* rho, double* phi0, int B, int 
  * paper has no counterpart): which = 0 the activation a_l = gelu(z_l), 1 the
  * pre-activation z_l (kept only by px_cnn_grads and px_cnn_train_step), of
  * hidden layer l = 1..5, as BF16 bit patterns in the library's chunk-planar
- * order (B, 4, H, W, 8): channel 8 k + c of pixel (y, x) of image b at
+ * order (B, 4, H, W, 8), natural pixel order (a relabelled tensor is gathered
+ * back through the network's gradient scratch): channel 8 k + c of pixel (y, x) of image b at
  * (((b * 4 + k) * H + y) * W + x) * 8 + c; B x H x W x 32 values of the last
  * call's shape (count may be smaller). Synchronises the stream. */
 px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, size_t count,
@@ -453,6 +454,19 @@ px_status px_cnn_set_wait_limit(px_cnn* net, uint32_t polls);
  * stage the same bytes, so results are bitwise equal. PX_EINVAL for other
  * modes. (An implementation choice; the paper has no counterpart.) */
 px_status px_cnn_set_staging(px_cnn* net, int mode);
+/* How the dilated 32 -> 32 layers address their taps. on = 1 (the default):
+ * where a layer's dilation d is invertible modulo H and W (d odd and the
+ * sides powers of two, for instance), its input is stored relabelled (natural
+ * pixel p at position p d^-1 modulo the sides), which makes the taps p +
+ * (dy, dx) d unit offsets q + (dy, dx) over positions; the layer then stages
+ * one (4 + 2)-row patch per column offset instead of nine tap tiles. Every
+ * producer stores its output in the positions its consumer wants; the output
+ * y, the loss, the gradients and px_cnn_get_hidden stay in natural order.
+ * on = 0: natural order everywhere, nine offset tap tiles per output tile.
+ * The two forms sum the same products in different orders (results agree to
+ * FP32 rounding). PX_EINVAL for other values. (An implementation choice; the
+ * paper has no counterpart.) */
+px_status px_cnn_set_relabel(px_cnn* net, int on);
 
 /* ----------------------------------------------------------------------------
  * 2D Euler equations of gas dynamics by the finite-volume method: the paper's

@@ -119,6 +119,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                       _vp]
     lib.px_cnn_set_wait_limit.argtypes = [_vp, ctypes.c_uint32]
     lib.px_cnn_set_staging.argtypes = [_vp, i]
+    lib.px_cnn_set_relabel.argtypes = [_vp, i]
     lib.px_set_option.argtypes = [_vp, i, i]
     lib.px_is_checked_build.restype = i
     lib.px_checked_faults.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
@@ -127,6 +128,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.px_euler_step.argtypes = [_vp, eg, _vp, _vp, d, d, i, d, _vp, _vp]
     lib.px_euler_conserved.argtypes = [_vp, eg, _vp, _vp, d, _vp]
     for name in ("px_cnn_get_hidden", "px_cnn_set_wait_limit", "px_cnn_set_staging",
+                 "px_cnn_set_relabel",
                  "px_set_option", "px_get_option", "px_checked_faults",
                  "px_euler_step", "px_euler_conserved"):
         getattr(lib, name).restype = i
@@ -636,6 +638,11 @@ class Cnn:
         """px_cnn_set_staging: 1 tensor-memory-accelerator boxes for in-image tap
         tiles (default), 0 per-pixel copies only."""
         self.ctx.check(load_library().px_cnn_set_staging(self.handle, int(mode)))
+
+    def set_relabel(self, on: bool):
+        """px_cnn_set_relabel: 1 dilated layers over relabelled activations
+        (unit-offset taps, the default), 0 natural order with offset tap tiles."""
+        self.ctx.check(load_library().px_cnn_set_relabel(self.handle, int(on)))
 
     def guess(self, rho, phi0, h: float, stream=None):
         B, H, W = rho.shape

@@ -167,6 +167,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
 // shared abort flag is set; on an abort the CTA raises *fault, lets its MMAs
 // drain (bounded) and frees its tensor memory.
 constexpr int kWsStages = 4;
+// Unit-offset layers (dilation 1, or a dilated layer whose input is stored
+// relabelled, below): one stage is the (TR + 2)-row patch of one column
+// offset dx, [chunk][row][pixel][8 ch] with the chunk stride kUChunk; it
+// serves the three taps of that dx, whose A operands start 1 KB (one
+// 64-pixel row) apart. Three stages per tile instead of nine tap tiles.
+constexpr int kURows = TR + 2;
+constexpr uint32_t kUChunk = kURows * TW * 16;         // 6 KB
+constexpr size_t kUTile = (size_t)4 * kUChunk;         // 24 KB
+constexpr int kUStages = 3;
+constexpr size_t kRingBytes = kUStages * kUTile > kWsStages * kCmTile ? kUStages * kUTile
+                                                                      : kWsStages * kCmTile;
 // A producer declares step g complete kWsAhead steps later (kWsAhead <
 // kWsStages, or it would wait on its own undeclared step). One step measured
 // fastest: with more copies in flight the tap tiles contend in L2 (whole
@@ -176,7 +187,7 @@ constexpr int kWsEpiWarps = 4, kWsProdWarps = 4;
 constexpr int kWsConvThreads = (kWsEpiWarps + kWsProdWarps + 1) * 32;  // 288
 constexpr uint32_t kWsTmemCols = 128;                                 // 2 sets x (2 x 32)
 constexpr int kWsBars = 2 * kWsStages + 4 + 1;  // full, empty, tfull[2], tempty[2], weights
-constexpr size_t kWsSmem = kWsStages * kCmTile + kWBytes + kWsBars * 8 + 16;
+constexpr size_t kWsSmem = kRingBytes + kWBytes + kWsBars * 8 + 16;  // 90 KB: two CTAs per SM
 
 // Handshake wait: up to `limit` polls of the barrier's phase, giving up early
 // once another thread of the CTA has set the abort flag; on running out it
@@ -251,15 +262,23 @@ __device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfl
   }
 }
 
+// Position of the output pixel computed at input position (y, x): the
+// coordinates times (ry, rx), modulo the image (identity when both are 1).
+__device__ __forceinline__ int relabel(int v, int r, int n) {
+  return r == 1 ? v : (int)(((int64_t)v * r) % n);
+}
+
 template <int kMode>
 __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int pix, int b, int y0,
-                                                   int x0, int H, int W,
+                                                   int x0, int H, int W, int ry, int rx,
                                                    const float* __restrict__ bias,
                                                    const __nv_bfloat16* __restrict__ zprev,
                                                    __nv_bfloat16* __restrict__ zout,
                                                    __nv_bfloat16* __restrict__ aout) {
   const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
-  const int64_t pb = act_off(b, y, x, 0, H, W), plane = (int64_t)H * W * 8;
+  // pb: the output's position; zprev shares the input's positions
+  const int64_t pb = act_off(b, relabel(y, ry, H), relabel(x, rx, W), 0, H, W),
+                plane = (int64_t)H * W * 8;
   __nv_bfloat162 zz[C / 2], aa[C / 2];
   if (kMode == 0) {
 #pragma unroll
@@ -276,7 +295,7 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
     }
   } else {
     float zf[C];
-    load_px32(zf, zprev + pb, plane);
+    load_px32(zf, zprev + act_off(b, y, x, 0, H, W), plane);
 #pragma unroll
     for (int o = 0; o < C; o += 2)
       aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
@@ -287,17 +306,24 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
     *reinterpret_cast<uint4*>(aout + pb + k * plane) = reinterpret_cast<const uint4*>(aa)[k];
 }
 
-template <int kMode>
+// kUnit: the unit-offset staging (three dx patches per tile; `dil` is then
+// ignored); otherwise nine tap tiles at offsets of `dil`. (ry, rx): output
+// position = input position times (ry, rx) modulo the image.
+template <int kMode, bool kUnit>
 __global__ void __launch_bounds__(kWsConvThreads, 2)
 conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ wk,
           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ zprev,
           __nv_bfloat16* __restrict__ zout, __nv_bfloat16* __restrict__ aout, int H, int W,
-          int tiles_x, int tiles_y, int ntiles, int dil, unsigned* __restrict__ fault,
-          uint32_t wait_limit, const __grid_constant__ CUtensorMap tmap_in, int use_tma) {
+          int tiles_x, int tiles_y, int ntiles, int dil, int ry, int rx,
+          unsigned* __restrict__ fault, uint32_t wait_limit,
+          const __grid_constant__ CUtensorMap tmap_in, int use_tma) {
+  constexpr int kSteps = kUnit ? 3 : 9;               // stages per tile
+  constexpr int kStages = kUnit ? kUStages : kWsStages;
+  constexpr uint32_t kStage = kUnit ? (uint32_t)kUTile : (uint32_t)kCmTile;
   // no static shared variables: the core matrices must start on 128-byte boundaries
   extern __shared__ __align__(128) unsigned char wsu[];
   unsigned char* ring = wsu;
-  unsigned char* wsm = wsu + kWsStages * kCmTile;
+  unsigned char* wsm = wsu + kRingBytes;
   uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + kWBytes);
   const uint32_t full0 = smem_u32(bar), empty0 = smem_u32(bar + kWsStages);
   const uint32_t tfull0 = smem_u32(bar + 2 * kWsStages), tempty0 = smem_u32(bar + 2 * kWsStages + 2);
@@ -344,32 +370,35 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
     for (int i = 0; i < my_tiles && go; ++i) {
       const int tile = (int)blockIdx.x + i * (int)gridDim.x;
       const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
-      for (int tap = 0; tap < 9; ++tap, ++g) {
-        const int st = g % kWsStages, u = g / kWsStages;
+      for (int step = 0; step < kSteps; ++step, ++g) {
+        const int st = g % kStages, u = g / kStages;
         if (u >= 1 && !mbar_wait_ab(empty0 + 8 * st, (u - 1) & 1, abort_, wait_limit)) { go = false; break; }
-        const int oy = tap_dy(tap, dil), ox = tap_dx(tap, dil);
+        // unit: the patch of rows y0 - 1 .. y0 + TR at column offset step - 1;
+        // otherwise tap `step`'s tile at offset (dy, dx) d
+        const int oy = kUnit ? -1 : tap_dy(step, dil), ox = kUnit ? step - 1 : tap_dx(step, dil);
+        constexpr int kR = kUnit ? kURows : TR;
         const int ys = wrapn(ty * TR + oy, H), xs = wrapn(tx * TW + ox, W);
-        if (use_tma && xs + TW <= W && ys + TR <= H) {
+        if (use_tma && xs + TW <= W && ys + kR <= H) {
           // the shifted tile lies inside the image: one box, issued by one thread
           if (pid == 0) {
-            mbar_expect_tx(full0 + 8 * st, (uint32_t)kCmTile);
-            tma_load_tile(smem_u32(ring + st * kCmTile), &tmap_in, xs, ys, b, full0 + 8 * st);
+            mbar_expect_tx(full0 + 8 * st, kStage);
+            tma_load_tile(smem_u32(ring + st * kStage), &tmap_in, xs, ys, b, full0 + 8 * st);
           }
         } else {  // it wraps around the periodic edge: per-pixel copies
-          load_tap_cm_p<TR>(ring + st * kCmTile, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
+          load_tap_cm_p<kR>(ring + st * kStage, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
         }
         cp_commit();
         if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
           cp_wait_group<kWsAhead>();
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(full0 + 8 * ((g - kWsAhead) % kWsStages));
+          mbar_arrive(full0 + 8 * ((g - kWsAhead) % kStages));
         }
       }
     }
     cp_wait_group<0>();
     if (go) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (int k = g > kWsAhead ? g - kWsAhead : 0; k < g; ++k) mbar_arrive(full0 + 8 * (k % kWsStages));
+      for (int k = g > kWsAhead ? g - kWsAhead : 0; k < g; ++k) mbar_arrive(full0 + 8 * (k % kStages));
     }
   } else if (warp == kWsEpiWarps + kWsProdWarps) {
     // ---- MMA issue
@@ -380,23 +409,41 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
       for (int i = 0; i < my_tiles && go; ++i) {
         const int a = i & 1;
         if (i >= 2 && !mbar_wait_ab(tempty0 + 8 * a, ((i >> 1) - 1) & 1, abort_, wait_limit)) { go = false; break; }
-        for (int tap = 0; tap < 9; ++tap, ++g) {
-          const int st = g % kWsStages;
-          if (!mbar_wait_ab(full0 + 8 * st, (g / kWsStages) & 1, abort_, wait_limit)) { go = false; break; }
+        for (int step = 0; step < kSteps; ++step, ++g) {
+          const int st = g % kStages;
+          if (!mbar_wait_ab(full0 + 8 * st, (g / kStages) & 1, abort_, wait_limit)) { go = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t abase = tbase + st * (uint32_t)kCmTile;
+          const uint32_t abase = tbase + st * kStage;
+          if constexpr (kUnit) {
+            // taps (dy, step) for dy = 0..2: output rows 2h, 2h + 1 read patch
+            // rows 2h + dy, 2h + dy + 1
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
+            for (int dy = 0; dy < 3; ++dy) {
+              const int tap = dy * 3 + step;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
-              umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (tap > 0 || cc > 0) ? 1u : 0u);
+              for (int cc = 0; cc < 2; ++cc) {
+                const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  const uint64_t ad = umma_desc(abase + cc * 2 * kUChunk + (2 * h + dy) * (TW * 16), kUChunk, 128);
+                  umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (step > 0 || dy > 0 || cc > 0) ? 1u : 0u);
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+              const uint64_t bd = umma_desc(wbase + (uint32_t)(step * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
+                umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (step > 0 || cc > 0) ? 1u : 0u);
+              }
             }
           }
           umma_commit(empty0 + 8 * st);
           last_bar = empty0 + 8 * st;
-          last_par = (g / kWsStages) & 1;
+          last_par = (g / kStages) & 1;
         }
         if (!go) break;
         umma_commit(tfull0 + 8 * a);
@@ -419,7 +466,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         uint32_t v[32];
         tmem_ld32(v, tmem + a * 2 * C + h * C + ((uint32_t)(warp * 32) << 16));
         conv_epilogue_half<kMode>(v, h * kUmmaM + warp * 32 + lane, b, ty * TR, tx * TW, H, W,
-                                  bias, zprev, zout, aout);
+                                  ry, rx, bias, zprev, zout, aout);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(tempty0 + 8 * a);
@@ -578,9 +625,12 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
 // are found once per row and the columns wrap with a conditional add when
 // the dilation is below the width.
 
+// (ny, nx): the outputs are stored relabelled: output position (yy, xx) holds
+// the natural pixel (yy ny mod H, xx nx mod W) (1, 1: natural order).
 __global__ void conv_first(const float* __restrict__ x, const float* __restrict__ w1,
                            const float* __restrict__ b1, __nv_bfloat16* __restrict__ zout,
-                           __nv_bfloat16* __restrict__ aout, int B, int H, int W, int dil) {
+                           __nv_bfloat16* __restrict__ aout, int B, int H, int W, int dil,
+                           int ny, int nx) {
   const int cg = threadIdx.x & 3;  // blockDim is a multiple of 4: fixed per thread
   float wr[8][9], br[8];
 #pragma unroll
@@ -591,13 +641,13 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
   }
   const bool near = dil < W;
   for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
-    const int img = row / H, yy = row - img * H;
+    const int img = row / H, yy = row - img * H, yn = relabel(yy, ny, H);
     const float* xr[3];
 #pragma unroll
-    for (int ty = 0; ty < 3; ++ty) xr[ty] = x + ((int64_t)img * H + wrapn(yy + (ty - 1) * dil, H)) * W;
+    for (int ty = 0; ty < 3; ++ty) xr[ty] = x + ((int64_t)img * H + wrapn(yn + (ty - 1) * dil, H)) * W;
     for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
-      const int xx = t >> 2;
-      const int xs[3] = {wrap_col(xx - dil, W, near), xx, wrap_col(xx + dil, W, near)};
+      const int xx = t >> 2, xn = relabel(xx, nx, W);
+      const int xs[3] = {wrap_col(xn - dil, W, near), xn, wrap_col(xn + dil, W, near)};
       float v[9];
 #pragma unroll
       for (int ty = 0; ty < 3; ++ty)
@@ -690,9 +740,11 @@ __global__ void mse_grad(const float* __restrict__ y, const float* __restrict__ 
 }
 
 // Backward of the last layer: dz5[q][c] = gelu'(z5[q][c]) * sum_tap W6[c][tap] dy[q - tap].
+// (ny, nx): dz5 is stored relabelled, position (yy, xx) holding the natural
+// pixel (yy ny mod H, xx nx mod W); z5 and dy are in natural order.
 __global__ void back_last(const float* __restrict__ dy, const float* __restrict__ w6,
                           const __nv_bfloat16* __restrict__ z5, __nv_bfloat16* __restrict__ dz5,
-                          int B, int H, int W, int dil) {
+                          int B, int H, int W, int dil, int ny, int nx) {
   // four threads per pixel, 8 channels each (coalesced 16-byte z5 loads and dz5 stores)
   const int cg = threadIdx.x & 3;
   float wr[8][9];
@@ -702,20 +754,20 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
     for (int tap = 0; tap < 9; ++tap) wr[j][tap] = __ldg(w6 + (cg * 8 + j) * 9 + tap);
   const bool near = dil < W;
   for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
-    const int img = row / H, yy = row - img * H;
+    const int img = row / H, yy = row - img * H, yn = relabel(yy, ny, H);
     const float* gr[3];  // dy at (q - off(tap)): tap row ty reads row y - (ty - 1) d
 #pragma unroll
-    for (int ty = 0; ty < 3; ++ty) gr[ty] = dy + ((int64_t)img * H + wrapn(yy - (ty - 1) * dil, H)) * W;
+    for (int ty = 0; ty < 3; ++ty) gr[ty] = dy + ((int64_t)img * H + wrapn(yn - (ty - 1) * dil, H)) * W;
     for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
-      const int xx = t >> 2;
-      const int xs[3] = {wrap_col(xx + dil, W, near), xx, wrap_col(xx - dil, W, near)};
+      const int xx = t >> 2, xn = relabel(xx, nx, W);
+      const int xs[3] = {wrap_col(xn + dil, W, near), xn, wrap_col(xn - dil, W, near)};
       float g[9];
 #pragma unroll
       for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) g[ty * 3 + tx] = __ldg(gr[ty] + xs[tx]);
       const int64_t po = act_off(img, yy, xx, cg, H, W);
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>(z5 + po));
+      const uint4 u = __ldg(reinterpret_cast<const uint4*>(z5 + act_off(img, yn, xn, cg, H, W)));
       const __nv_bfloat162* hz = reinterpret_cast<const __nv_bfloat162*>(&u);
       __nv_bfloat162 o[4];
 #pragma unroll
@@ -936,6 +988,22 @@ __global__ void finish_images(const float* __restrict__ y, const double* __restr
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) phi0[off + i] = s * ((double)y[off + i] - mean);
 }
 
+// Natural-order copy of a relabelled activation tensor: pixel (y, x) of dst
+// from position (y my mod H, x mx mod W) of src; one 16-byte chunk per thread.
+__global__ void unrelabel(const __nv_bfloat16* __restrict__ src, __nv_bfloat16* __restrict__ dst,
+                          int B, int H, int W, int my, int mx) {
+  const int64_t n = (int64_t)B * 4 * H * W;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W);
+    const int64_t r = i / W;
+    const int y = (int)(r % H);
+    const int64_t bc = r / H;  // b * 4 + chunk
+    const int64_t q = (bc * H + relabel(y, my, H)) * W + relabel(x, mx, W);
+    reinterpret_cast<uint4*>(dst)[i] = reinterpret_cast<const uint4*>(src)[q];
+  }
+}
+
 }  // namespace cnn
 }  // namespace px
 
@@ -1011,6 +1079,11 @@ struct px_cnn {
   int64_t cap_img = 0;
   uint32_t wait_limit = kSpinLimit;  // polls per handshake wait of the tensor-core kernels
   int use_tma = 1;                     // stage in-image tap tiles with the tensor memory accelerator
+  int relabel = 1;                     // store activations relabelled for unit-offset dilated layers
+  // layout of the last call's hidden tensors: a[l], z[l] stored at natural
+  // position times (my[l], mx[l]) modulo (H, W)
+  int last_b = 0, last_h = 0, last_w = 0;
+  int my[kLayers] = {1, 1, 1, 1, 1, 1}, mx[kLayers] = {1, 1, 1, 1, 1, 1};
 };
 
 namespace {
@@ -1152,12 +1225,76 @@ px_status set_conv_attrs() {
   static bool done_by_dev[64] = {};
   bool& done = done_by_dev[px::dev_index()];
   if (done) return PX_OK;
-  cudaError_t e = cudaFuncSetAttribute(conv32_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+  cudaError_t e = cudaFuncSetAttribute(conv32_ws<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgUmmaSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
   return PX_OK;
+}
+
+// Inverse of d modulo m (0 if gcd(d, m) > 1).
+int inv_mod(int64_t d, int64_t m) {
+  int64_t r0 = m, r1 = ((d % m) + m) % m, t0 = 0, t1 = 1;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1, r2 = r0 - q * r1, t2 = t0 - q * t1;
+    r0 = r1; r1 = r2; t0 = t1; t1 = t2;
+  }
+  if (r0 != 1) return m == 1 ? 1 : 0;
+  return (int)(((t0 % m) + m) % m);
+}
+
+// Relabelling of a dilated layer. With d invertible modulo H and W (d odd and
+// the sides powers of two, for instance), storing the layer's input with
+// natural pixel p at position p d^-1 makes the taps p + (dy, dx) d land at
+// positions q + (dy, dx): the layer is a unit-offset convolution over
+// positions, whose output at position q is the natural pixel q d. Each
+// producer stores its outputs in the positions its consumer wants.
+//   rel[l]        layer l (1..4) runs over its input's relabelled positions
+//   unit[l]       layer l stages unit-offset patches (relabelled or d = 1)
+//   my/mx[l]      a[l], z[l] (l = 0..4) and dZ[l+1] are stored at natural * m
+//   ny/nx[l]      the inverse: natural = position * n
+struct Plan {
+  bool rel[kLayers] = {}, unit[kLayers] = {};
+  int my[kLayers], mx[kLayers], ny[kLayers], nx[kLayers];
+};
+Plan plan_of(const px_cnn* n, int H, int W) {
+  Plan p;
+  for (int l = 0; l < kLayers; ++l) p.my[l] = p.mx[l] = p.ny[l] = p.nx[l] = 1;
+  for (int l = 1; l <= 4; ++l) {
+    p.rel[l] = n->relabel && n->dil[l] > 1 && inv_mod(n->dil[l], H) && inv_mod(n->dil[l], W);
+    p.unit[l] = p.rel[l] || n->dil[l] == 1;
+  }
+  for (int l = 0; l < 4; ++l)
+    if (p.rel[l + 1]) {
+      p.my[l] = inv_mod(n->dil[l + 1], H);
+      p.mx[l] = inv_mod(n->dil[l + 1], W);
+      p.ny[l] = n->dil[l + 1] % H;
+      p.nx[l] = n->dil[l + 1] % W;
+    }
+  return p;
+}
+
+// Multiplier (a * b) mod m of two relabellings.
+int mul_mod(int a, int b, int m) { return (int)(((int64_t)a * b) % m); }
+
+// Launches the 32 -> 32 tensor-core convolution in its staging form.
+template <int kMode>
+void launch_conv32(bool unit, int grid, cudaStream_t st, const __nv_bfloat16* in,
+                   const __nv_bfloat16* wk, const float* bias, const __nv_bfloat16* zprev,
+                   __nv_bfloat16* zout, __nv_bfloat16* aout, int H, int W, int tiles_x,
+                   int tiles_y, int ntiles, int dil, int ry, int rx, unsigned* fault,
+                   uint32_t wait_limit, const CUtensorMap& tm, int use) {
+  if (unit)
+    conv32_ws<kMode, true><<<grid, kWsConvThreads, kWsSmem, st>>>(
+        in, wk, bias, zprev, zout, aout, H, W, tiles_x, tiles_y, ntiles, 1, ry, rx, fault,
+        wait_limit, tm, use);
+  else
+    conv32_ws<kMode, false><<<grid, kWsConvThreads, kWsSmem, st>>>(
+        in, wk, bias, zprev, zout, aout, H, W, tiles_x, tiles_y, ntiles, dil, ry, rx, fault,
+        wait_limit, tm, use);
 }
 
 // Forward pass into n->a / n->z (z only when training) and output y.
@@ -1166,17 +1303,26 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
   const int tiles_x = W / TW, tiles_y = H / TR;
   const int tiles = B * tiles_x * tiles_y;
   const int rows_grid = std::min(B * H, 8 * px::device_sm_count());  // whole rows per CTA
+  const Plan P = plan_of(n, H, W);
+  n->last_b = B;
+  n->last_h = H;
+  n->last_w = W;
+  for (int l = 0; l < kLayers; ++l) { n->my[l] = P.my[l]; n->mx[l] = P.mx[l]; }
   conv_first<<<rows_grid, 256, 0, st>>>(x, n->params + kOff.w[0], n->params + kOff.b[0],
-                                        train ? n->z[0] : nullptr, n->a[0], B, H, W, n->dil[0]);
+                                        train ? n->z[0] : nullptr, n->a[0], B, H, W, n->dil[0],
+                                        P.ny[0], P.nx[0]);
   unsigned* fault = conv_fault_ptr();
   if (!fault) return cnn_cuda(n, cudaErrorInvalidSymbol, "conv fault word");
   const int cgrid = std::min(tiles, 2 * px::device_sm_count());  // persistent: 2 CTAs per SM
   for (int l = 1; l <= 4; ++l) {
     alignas(64) CUtensorMap tm;
-    const int use = n->use_tma && act_tensor_map(&tm, n->a[l - 1], B, H, W, TR);
-    conv32_ws<0><<<cgrid, kWsConvThreads, kWsSmem, st>>>(
-        n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr, train ? n->z[l] : nullptr,
-        n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l], fault, n->wait_limit, tm, use);
+    const int use = n->use_tma && act_tensor_map(&tm, n->a[l - 1], B, H, W, P.unit[l] ? kURows : TR);
+    // output position = natural (input position times d if relabelled) times m[l]
+    const int ny = P.rel[l] ? P.ny[l - 1] : 1, nx = P.rel[l] ? P.nx[l - 1] : 1;
+    launch_conv32<0>(P.unit[l], cgrid, st, n->a[l - 1], n->wf[l], n->params + kOff.b[l], nullptr,
+                     train ? n->z[l] : nullptr, n->a[l], H, W, tiles_x, tiles_y, tiles, n->dil[l],
+                     mul_mod(ny, P.my[l], H), mul_mod(nx, P.mx[l], W), fault, n->wait_limit, tm,
+                     use);
   }
   conv_last<<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
                                               n->params + kOff.b[5], y, B, H, W, n->dil[5]);
@@ -1205,24 +1351,31 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   wgrad_single<1><<<nsc_cap, kWsThreads, 0, st>>>(n->a[4], n->dy,
                                                   n->part, B, H, W, rpc, n->dil[5]);
   reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
-  back_last<<<std::min(B * H, 8 * px::device_sm_count()), 256, 0, st>>>(n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W,
-                                              n->dil[5]);
+  const Plan P = plan_of(n, H, W);
+  // dZ of layer 4 goes in the positions of layer 4's input a[3]
+  back_last<<<std::min(B * H, 8 * px::device_sm_count()), 256, 0, st>>>(
+      n->dy, n->params + kOff.w[5], n->z[4], n->g0, B, H, W, n->dil[5], P.ny[3], P.nx[3]);
   __nv_bfloat16* gcur = n->g0;
   __nv_bfloat16* gnext = n->g1;
   // weight gradients: 2 x 64-pixel tiles, two CTAs per SM
   const int wg_tiles = B * tiles_x * (H / kWgRows);
   const int wg_ctas = std::min(wg_tiles, 2 * px::device_sm_count());
   for (int l = 4; l >= 1; --l) {
+    // a[l - 1] and dZ[l] share their positions: unit offsets when relabelled
     wgrad32_umma<<<wg_ctas, kConvThreads, kWgUmmaSmem, st>>>(
-        n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, n->dil[l],
+        n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, P.rel[l] ? 1 : n->dil[l],
         conv_fault_ptr(), n->wait_limit);
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
     reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     alignas(64) CUtensorMap tm;
-    const int use = n->use_tma && act_tensor_map(&tm, gcur, B, H, W, TR);
-    conv32_ws<1><<<std::min(tiles, 2 * px::device_sm_count()), kWsConvThreads, kWsSmem, st>>>(
-        gcur, n->wb[l], nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
-        n->dil[l], conv_fault_ptr(), n->wait_limit, tm, use);
+    const int use = n->use_tma && act_tensor_map(&tm, gcur, B, H, W, P.unit[l] ? kURows : TR);
+    // dZ[l - 1] goes in the positions of a[l - 2] (natural order for l = 1)
+    const int ny = P.rel[l] ? P.ny[l - 1] : 1, nx = P.rel[l] ? P.nx[l - 1] : 1;
+    const int my = l >= 2 ? P.my[l - 2] : 1, mx = l >= 2 ? P.mx[l - 2] : 1;
+    launch_conv32<1>(P.unit[l], std::min(tiles, 2 * px::device_sm_count()), st, gcur, n->wb[l],
+                     nullptr, n->z[l - 1], nullptr, gnext, H, W, tiles_x, tiles_y, tiles,
+                     n->dil[l], mul_mod(ny, my, H), mul_mod(nx, mx, W), conv_fault_ptr(),
+                     n->wait_limit, tm, use);
     std::swap(gcur, gnext);
   }
   wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
@@ -1354,7 +1507,16 @@ px_status px_cnn_get_hidden(px_cnn* n, int layer, int which, uint16_t* host, siz
   DevScope ds(n->ctx->device);
   const __nv_bfloat16* src = which == 0 ? n->a[layer - 1] : n->z[layer - 1];
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(host, src, count * sizeof(uint16_t), cudaMemcpyDeviceToHost, st);
+  const int l = layer - 1, B = n->last_b, H = n->last_h, W = n->last_w;
+  if (n->my[l] != 1 || n->mx[l] != 1) {
+    // stored relabelled: gather natural order into the gradient scratch
+    unrelabel<<<grid_1d((int64_t)B * 4 * H * W, 256), 256, 0, st>>>(src, n->g1, B, H, W, n->my[l],
+                                                                     n->mx[l]);
+    src = n->g1;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host, src, count * sizeof(uint16_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "hidden readback");
 }
@@ -1366,6 +1528,16 @@ px_status px_cnn_get_hidden(px_cnn* n, int layer, int which, uint16_t* host, siz
 px_status px_cnn_set_staging(px_cnn* n, int mode) {
   if (!n || mode < 0 || mode > 1) return PX_EINVAL;
   n->use_tma = mode;
+  return PX_OK;
+}
+
+// Whether dilated layers run over relabelled activations (1, the default:
+// each activation is stored in the positions that make its consumer's taps
+// unit offsets, where the dilation is invertible modulo the image sides) or
+// over natural-order activations with nine offset tap tiles (0).
+px_status px_cnn_set_relabel(px_cnn* n, int on) {
+  if (!n || on < 0 || on > 1) return PX_EINVAL;
+  n->relabel = on;
   return PX_OK;
 }
 

@@ -69,10 +69,17 @@ DIL = (1, 3, 9, 27, 81, 1)
 FWD_TOL, GRAD_TOL_SMALL, GRAD_TOL_LARGE, LOSS_TOL = 1.25e-2, 1e-2, 2e-3, 2e-3
 
 
+@pytest.mark.parametrize("relabel", [1, 0])
 @pytest.mark.parametrize("B,H,W,dil", [(2, 8, 64, None), (1, 12, 128, None), (1, 256, 256, None),
-                                       (2, 8, 64, DIL), (1, 256, 256, DIL), (1, 32, 192, (1, 2, 5, 7, 3, 2))])
-def test_forward_matches_oracle(px, B, H, W, dil):
+                                       (2, 8, 64, DIL), (1, 256, 256, DIL), (1, 32, 192, (1, 2, 5, 7, 3, 2)),
+                                       (1, 12, 192, (1, 5, 3, 7, 9, 1))])
+def test_forward_matches_oracle(px, B, H, W, dil, relabel):
+    """relabel 1: dilated layers whose dilation is invertible modulo H and W
+    run over relabelled activations (at 32 x 192, d = 2 and 3 are not, d = 5
+    and 7 are, so relabelled and natural-order layers alternate; at 12 x 192
+    only d = 5 and 7 are); relabel 0: natural order everywhere."""
     net = px.Cnn(seed=3, dilations=dil)
+    net.set_relabel(relabel)
     rng = np.random.default_rng(B * 1000 + H)
     x = rng.standard_normal((B, H, W)).astype(np.float32)
     xt = torch.from_numpy(x).cuda()
@@ -86,10 +93,12 @@ def test_forward_matches_oracle(px, B, H, W, dil):
     net.close()
 
 
-@pytest.mark.parametrize("dil", [None, DIL])
-def test_gradients_match_oracle(px, dil):
+@pytest.mark.parametrize("relabel", [1, 0])
+@pytest.mark.parametrize("dil", [None, DIL, (1, 2, 5, 7, 3, 2)])
+def test_gradients_match_oracle(px, dil, relabel):
     B, H, W = 2, 8, 64
     net = px.Cnn(seed=5, dilations=dil)
+    net.set_relabel(relabel)
     rng = np.random.default_rng(7)
     x = rng.standard_normal((B, H, W)).astype(np.float32)
     t = rng.standard_normal((B, H, W)).astype(np.float32)
@@ -171,14 +180,15 @@ def test_forward_multitile_matches_oracle(px, dil):
     net.close()
 
 
-@pytest.mark.parametrize("dil", [None, DIL])
-def test_gradients_multitile_match_oracle(px, dil):
+@pytest.mark.parametrize("dil,relabel", [(None, 1), (DIL, 1), (DIL, 0)])
+def test_gradients_multitile_match_oracle(px, dil, relabel):
     """B = 2 images of 256^2: the weight-gradient kernel accumulates about 3.5
     tiles per CTA in tensor memory and reduces 296 partials; the input-gradient
     convolution runs about 1.7 tiles per CTA. Every layer's dW and db against
     the oracle's analytic backward, the loss against the oracle's MSE."""
     B, H, W = 2, 256, 256
     net = px.Cnn(seed=21, dilations=dil)
+    net.set_relabel(relabel)
     rng = np.random.default_rng(23)
     x = rng.standard_normal((B, H, W)).astype(np.float32)
     t = rng.standard_normal((B, H, W)).astype(np.float32)
@@ -195,12 +205,15 @@ def test_gradients_multitile_match_oracle(px, dil):
     net.close()
 
 
-@pytest.mark.parametrize("dil", [None, DIL, (1, 2, 5, 64, 7, 1)])
-def test_tma_staging_bitwise_equals_copies(px, dil):
-    """Tap tiles staged by the tensor memory accelerator (in-image tiles) and by
-    per-pixel copies (every tile) are the same bytes: the forward output, the
-    hidden tensors and all gradients agree bitwise, at several tiles per CTA
-    (B = 4, 256^2) and with dilations that make boxes cross the edge."""
+@pytest.mark.parametrize("dil,relabel", [(None, 1), (DIL, 1), (DIL, 0), ((1, 2, 5, 64, 7, 1), 1),
+                                         ((1, 2, 5, 64, 7, 1), 0)])
+def test_tma_staging_bitwise_equals_copies(px, dil, relabel):
+    """Tiles and patches staged by the tensor memory accelerator (in-image
+    ones) and by per-pixel copies (every one) are the same bytes: the forward
+    output, the hidden tensors and all gradients agree bitwise, at several
+    tiles per CTA (B = 4, 256^2), for the unit-offset patches (relabelled or
+    d = 1) and the nine offset tap tiles (natural order, or d = 2 and 64,
+    which are not invertible modulo 256), with boxes that cross the edge."""
     B, H, W = 4, 256, 256
     rng = np.random.default_rng(41)
     x = torch.from_numpy(rng.standard_normal((B, H, W)).astype(np.float32)).cuda()
@@ -209,6 +222,7 @@ def test_tma_staging_bitwise_equals_copies(px, dil):
     for mode in (0, 1):
         net = px.Cnn(seed=43, dilations=dil)
         net.set_staging(mode)
+        net.set_relabel(relabel)
         y = torch.empty_like(x)
         net.forward(x, y)
         g, loss = net.grads(x, t)
@@ -222,6 +236,8 @@ def test_tma_staging_bitwise_equals_copies(px, dil):
         assert np.array_equal(a, b)
     with pytest.raises(px.PxError):
         px.Cnn(seed=1).set_staging(2)
+    with pytest.raises(px.PxError):
+        px.Cnn(seed=1).set_relabel(2)
 
 
 def test_bounded_wait_times_out_and_recovers(px):
