@@ -59,12 +59,35 @@ __device__ __forceinline__ void cp_wait_group() {
 
 
 
-__device__ __forceinline__ float gelu_f(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+// GELU(z) = z Phi(z) and GELU'(z) = Phi(z) + z phi(z), with the normal
+// distribution Phi(z) = (1 + erf(z / sqrt 2)) / 2 and density phi(z) =
+// exp(-z^2 / 2) / sqrt(2 pi). erf from Abramowitz and Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26: for x >= 0,
+//   erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2),
+//   t = 1 / (1 + p x),  |error| <= 1.5e-7,
+// so with x = |z| / sqrt 2 one exponential exp(-z^2 / 2) serves both erf and
+// phi. The upper tail Q = 1 - erf(x) gives Phi(z) = 1 - Q / 2 for z >= 0 and
+// Q / 2 for z < 0. The hardware reciprocal and exponential add relative
+// errors near 2^-22; the activations are stored in BF16 (2^-9).
+struct NormalCdf {
+  float Phi, E;  // Phi(z) and exp(-z^2 / 2)
+};
+__device__ __forceinline__ NormalCdf normal_cdf(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  q *= t;
+  const float E = __expf(-0.5f * z * z);
+  const float h = 0.5f * q * E;  // Q / 2
+  return {z >= 0.0f ? 1.0f - h : h, E};
 }
+__device__ __forceinline__ float gelu_f(float z) { return z * normal_cdf(z).Phi; }
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
-         z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  const NormalCdf c = normal_cdf(z);
+  return fmaf(z * 0.39894228040143268f, c.E, c.Phi);
 }
 
 
@@ -101,17 +124,25 @@ __device__ __forceinline__ int tap_dx(int tap, int d) { return (tap % 3 - 1) * d
 // ---------------------------------------------------------------------------
 // 32 -> 32 periodic convolution (dilation d) on the 5th-generation tensor
 // cores: tcgen05.mma (kind::f16, BF16 operands, FP32 accumulators in tensor
-// memory). A 4 x 64 output tile is two M = 128 pixel halves, each with a
-// 128-lane x 32-column FP32 accumulator in TMEM. Operands live in shared
+// memory). A 4 x 64 output tile is two M = 128 pixel halves, the left and the
+// right 4 x 32 pixels, each with a 128-lane x 32-column FP32 accumulator in
+// TMEM (lane 32 i + p: row i, pixel p of the half). Operands live in shared
 // memory in the no-swizzle K-major core-matrix layout (a core matrix is 8 rows
-// x 16 bytes, contiguous): a tap's shifted input tile [256 px][32 ch] has
-// chunk c of 8 channels at c * 4096 B and pixel p at p * 16 B; the weights
-// [32 n][288 k] are pre-packed as [k / 8][n][k % 8] (18 KB). Per tap and
-// K = 16 half the MMA reads A at (tile + 2 cc * 4096 + half * 2048, LBO 4096,
-// SBO 128) and B at (weights + (4 tap + 2 cc) * 512, LBO 512, SBO 128).
+// x 16 bytes, contiguous). A staged tile of R rows is [half][chunk][row][32
+// px][8 ch]: a half-row of one 8-channel chunk is 512 contiguous bytes (the
+// box rows of the tensor memory accelerator: 32 pixels x 16 B, so no 32-byte
+// sector is fetched for 16 useful bytes), row r of a half at r * 512 B, chunk
+// c at c * R * 512 B, half h at h * 4 R * 512 B. The half's 128 pixels are
+// then 16 core matrices 128 B apart whatever the row: the MMA reads A at
+// (tile + h * 4 R * 512 + 2 cc * R * 512 + (first row) * 512, LBO R * 512,
+// SBO 128) and B at (weights + (4 tap + 2 cc) * 512, LBO 512, SBO 128); the
+// weights [32 n][288 k] are pre-packed as [k / 8][n][k % 8] (18 KB).
 constexpr int kUmmaM = 128;                               // pixels per MMA = TMEM lanes
-constexpr uint32_t kCmChunk = TR * TW * 16;               // 4096 B: next 8-channel chunk of a tile
-constexpr size_t kCmTile = (size_t)4 * kCmChunk;          // 16 KB: one tap tile
+constexpr int kHW = TW / 2;                               // 32: pixels of a half-row
+constexpr uint32_t kHRow = kHW * 16;                      // 512 B: one half-row of one chunk
+constexpr uint32_t kCmChunk = TR * kHRow;                 // 2048 B: next chunk of a half tile
+constexpr uint32_t kCmHalf = 4 * kCmChunk;                // 8 KB: one half of a tap tile
+constexpr size_t kCmTile = (size_t)2 * kCmHalf;           // 16 KB: one tap tile
 constexpr uint32_t kCmWChunk = C * 16;                    // 512 B: next 8-k chunk of the weights
 constexpr size_t kWBytes = (size_t)(K9 / 8) * kCmWChunk;  // 18 KB
 constexpr uint32_t kSpinLimit = 1u << 26;
@@ -169,12 +200,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t (&v)[32], uint32_t taddr) {
 constexpr int kWsStages = 4;
 // Unit-offset layers (dilation 1, or a dilated layer whose input is stored
 // relabelled, below): one stage is the (TR + 2)-row patch of one column
-// offset dx, [chunk][row][pixel][8 ch] with the chunk stride kUChunk; it
-// serves the three taps of that dx, whose A operands start 1 KB (one
-// 64-pixel row) apart. Three stages per tile instead of nine tap tiles.
+// offset dx in the same [half][chunk][row][32 px][8 ch] layout; it serves the
+// three taps of that dx, whose A operands start one half-row (512 B) apart.
+// Three stages per tile instead of nine tap tiles.
 constexpr int kURows = TR + 2;
-constexpr uint32_t kUChunk = kURows * TW * 16;         // 6 KB
-constexpr size_t kUTile = (size_t)4 * kUChunk;         // 24 KB
+constexpr uint32_t kUChunk = kURows * kHRow;           // 3 KB
+constexpr uint32_t kUHalf = 4 * kUChunk;               // 12 KB
+constexpr size_t kUTile = (size_t)2 * kUHalf;          // 24 KB
 constexpr int kUStages = 3;
 constexpr size_t kRingBytes = kUStages * kUTile > kWsStages * kCmTile ? kUStages * kUTile
                                                                       : kWsStages * kCmTile;
@@ -187,7 +219,9 @@ constexpr int kWsEpiWarps = 4, kWsProdWarps = 4;
 constexpr int kWsConvThreads = (kWsEpiWarps + kWsProdWarps + 1) * 32;  // 288
 constexpr uint32_t kWsTmemCols = 128;                                 // 2 sets x (2 x 32)
 constexpr int kWsBars = 2 * kWsStages + 4 + 1;  // full, empty, tfull[2], tempty[2], weights
-constexpr size_t kWsSmem = kRingBytes + kWBytes + kWsBars * 8 + 16;  // 90 KB: two CTAs per SM
+// ring | weights | barriers, abort flag, TMEM slot (128 B) | bias (128 B): 90 KB, two CTAs per SM
+static_assert(kWsBars * 8 + 8 <= 128, "barrier block");
+constexpr size_t kWsSmem = kRingBytes + kWBytes + 256;
 
 // Handshake wait: up to `limit` polls of the barrier's phase, giving up early
 // once another thread of the CTA has set the abort flag; on running out it
@@ -224,20 +258,22 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
                ::"r"(bar) : "memory");
 }
 
-// Tensor memory accelerator: one 5D box of the chunk-planar activations,
-// dims (8 channels, W, H, 4 chunks, B), box (8, 64, R, 4, 1), lands in shared
-// memory as [chunk][row][pixel][8 channels], the operand's core-matrix layout;
-// completion is counted in bytes on the stage's `full` barrier.
+// Tensor memory accelerator: one 4D box of the chunk-planar activations,
+// dims (W x 8 elements: a row of one chunk, H, 4 chunks, B), box (256, R, 4,
+// 1) = 32 pixels x R rows x 4 chunks, lands in shared memory as
+// [chunk][row][32 px][8 ch], one half of the operand layout; x is the first
+// pixel times 8 (a multiple of 16 bytes). Completion is counted in bytes on
+// the stage's `full` barrier.
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, int x, int y,
+__device__ __forceinline__ void tma_load_half(uint32_t dst, const CUtensorMap* map, int px, int y,
                                               int b, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(0), "r"(b),
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(px * 8), "r"(y), "r"(0), "r"(b),
         "r"(bar)
       : "memory");
 }
@@ -248,6 +284,22 @@ __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m
 // (a warp: 512 contiguous global bytes). The periodic wrap is a conditional
 // add or subtract when the tap offset is smaller than the image, a full
 // modulo otherwise.
+// The same for one half of a conv operand tile: the R x 32 pixels from
+// (y0 + oy, x0 + ox) into [chunk][row][32 px][8 ch] (chunk stride R * 512 B).
+template <int R>
+__device__ __forceinline__ void load_half_cm_p(unsigned char* dst, const __nv_bfloat16* act, int b,
+                                               int y0, int x0, int oy, int ox, int H, int W,
+                                               int pid, int np) {
+  const bool near = oy > -H && oy < H && ox > -W && ox < W;
+  for (int q = pid; q < R * kHW * 4; q += np) {
+    const int chunk = q / (R * kHW), pix = q - chunk * (R * kHW);
+    const int r = pix >> 5, c = pix & (kHW - 1);
+    const int gy = near ? wrap1(y0 + r + oy, H) : wrapn(y0 + r + oy, H);
+    const int gx = near ? wrap1(x0 + c + ox, W) : wrapn(x0 + c + ox, W);
+    cp16(dst + chunk * (R * kHRow) + pix * 16, act + act_off(b, gy, gx, chunk, H, W));
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfloat16* act, int b,
                                               int y0, int x0, int oy, int ox, int H, int W,
@@ -271,11 +323,12 @@ __device__ __forceinline__ int relabel(int v, int r, int n) {
 template <int kMode>
 __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int pix, int b, int y0,
                                                    int x0, int H, int W, int ry, int rx,
-                                                   const float* __restrict__ bias,
+                                                   const float* sbias,  // shared memory
                                                    const __nv_bfloat16* __restrict__ zprev,
                                                    __nv_bfloat16* __restrict__ zout,
                                                    __nv_bfloat16* __restrict__ aout) {
-  const int y = y0 + (pix >> 6), x = x0 + (pix & (TW - 1));
+  // accumulator lane pix & 127 of half pix >> 7: row (pix >> 5) & 3, pixel pix & 31
+  const int y = y0 + ((pix >> 5) & 3), x = x0 + (pix >> 7) * kHW + (pix & (kHW - 1));
   // pb: the output's position; zprev shares the input's positions
   const int64_t pb = act_off(b, relabel(y, ry, H), relabel(x, rx, W), 0, H, W),
                 plane = (int64_t)H * W * 8;
@@ -283,8 +336,9 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
   if (kMode == 0) {
 #pragma unroll
     for (int o = 0; o < C; o += 2) {
-      const float v0 = __uint_as_float(v[o]) + __ldg(bias + o);
-      const float v1 = __uint_as_float(v[o + 1]) + __ldg(bias + o + 1);
+      const float2 bb = *reinterpret_cast<const float2*>(sbias + o);  // same address: broadcast
+      const float v0 = __uint_as_float(v[o]) + bb.x;
+      const float v1 = __uint_as_float(v[o + 1]) + bb.y;
       zz[o / 2] = __floats2bfloat162_rn(v0, v1);
       aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
     }
@@ -330,6 +384,8 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
   const uint32_t wfull = smem_u32(bar + 2 * kWsStages + 4);
   volatile int* abort_ = reinterpret_cast<volatile int*>(bar + kWsBars);
   volatile uint32_t* tslot = reinterpret_cast<volatile uint32_t*>(abort_ + 1);
+  float* const sbias = reinterpret_cast<float*>(wsm + kWBytes + 128);
+  if (threadIdx.x < C) sbias[threadIdx.x] = bias ? bias[threadIdx.x] : 0.0f;  // read after the barrier below
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
 
@@ -377,16 +433,21 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         // otherwise tap `step`'s tile at offset (dy, dx) d
         const int oy = kUnit ? -1 : tap_dy(step, dil), ox = kUnit ? step - 1 : tap_dx(step, dil);
         constexpr int kR = kUnit ? kURows : TR;
-        const int ys = wrapn(ty * TR + oy, H), xs = wrapn(tx * TW + ox, W);
-        if (use_tma && xs + TW <= W && ys + kR <= H) {
-          // the shifted tile lies inside the image: one box, issued by one thread
-          if (pid == 0) {
-            mbar_expect_tx(full0 + 8 * st, kStage);
-            tma_load_tile(smem_u32(ring + st * kStage), &tmap_in, xs, ys, b, full0 + 8 * st);
-          }
-        } else {  // it wraps around the periodic edge: per-pixel copies
-          load_tap_cm_p<kR>(ring + st * kStage, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
+        constexpr uint32_t kHalfB = kStage / 2;
+        const int ys = wrapn(ty * TR + oy, H);
+        const int xs0 = wrapn(tx * TW + ox, W), xs1 = wrapn(tx * TW + kHW + ox, W);
+        // a half that lies inside the image is one box, issued by one thread;
+        // one that wraps around the periodic edge takes per-pixel copies
+        const bool box0 = use_tma && ys + kR <= H && xs0 + kHW <= W;
+        const bool box1 = use_tma && ys + kR <= H && xs1 + kHW <= W;
+        unsigned char* const dst = ring + st * kStage;
+        if ((box0 || box1) && pid == 0) {
+          mbar_expect_tx(full0 + 8 * st, (box0 ? kHalfB : 0u) + (box1 ? kHalfB : 0u));
+          if (box0) tma_load_half(smem_u32(dst), &tmap_in, xs0, ys, b, full0 + 8 * st);
+          if (box1) tma_load_half(smem_u32(dst + kHalfB), &tmap_in, xs1, ys, b, full0 + 8 * st);
         }
+        if (!box0) load_half_cm_p<kR>(dst, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
+        if (!box1) load_half_cm_p<kR>(dst + kHalfB, in, b, ty * TR, tx * TW + kHW, oy, ox, H, W, pid, np);
         cp_commit();
         if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
           cp_wait_group<kWsAhead>();
@@ -415,8 +476,8 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t abase = tbase + st * kStage;
           if constexpr (kUnit) {
-            // taps (dy, step) for dy = 0..2: output rows 2h, 2h + 1 read patch
-            // rows 2h + dy, 2h + dy + 1
+            // taps (dy, step) for dy = 0..2: output rows 0..3 read patch rows
+            // dy .. dy + 3
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy) {
               const int tap = dy * 3 + step;
@@ -425,7 +486,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
                 const uint64_t bd = umma_desc(wbase + (uint32_t)(tap * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                  const uint64_t ad = umma_desc(abase + cc * 2 * kUChunk + (2 * h + dy) * (TW * 16), kUChunk, 128);
+                  const uint64_t ad = umma_desc(abase + h * kUHalf + cc * 2 * kUChunk + dy * kHRow, kUChunk, 128);
                   umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (step > 0 || dy > 0 || cc > 0) ? 1u : 0u);
                 }
               }
@@ -436,7 +497,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
               const uint64_t bd = umma_desc(wbase + (uint32_t)(step * 4 + cc * 2) * kCmWChunk, kCmWChunk, 128);
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
-                const uint64_t ad = umma_desc(abase + cc * 2 * kCmChunk + h * kUmmaM * 16, kCmChunk, 128);
+                const uint64_t ad = umma_desc(abase + h * kCmHalf + cc * 2 * kCmChunk, kCmChunk, 128);
                 umma_bf16(tmem + a * 2 * C + h * C, ad, bd, (step > 0 || cc > 0) ? 1u : 0u);
               }
             }
@@ -466,7 +527,7 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         uint32_t v[32];
         tmem_ld32(v, tmem + a * 2 * C + h * C + ((uint32_t)(warp * 32) << 16));
         conv_epilogue_half<kMode>(v, h * kUmmaM + warp * 32 + lane, b, ty * TR, tx * TW, H, W,
-                                  ry, rx, bias, zprev, zout, aout);
+                                  ry, rx, sbias, zprev, zout, aout);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(tempty0 + 8 * a);
@@ -1205,18 +1266,18 @@ EncodeTiled encode_tiled() {
 }
 
 // Tensor map of B chunk-planar activation images of H x W for boxes of R
-// rows x 64 pixels x 32 channels; false (and the per-pixel copy path) if the
-// driver cannot encode it.
+// rows x 32 pixels x 32 channels (one half of an operand tile); false (and
+// the per-pixel copy path) if the driver cannot encode it.
 bool act_tensor_map(CUtensorMap* m, const __nv_bfloat16* act, int B, int H, int W, int R) {
   std::memset(m, 0, sizeof *m);
   const EncodeTiled enc = encode_tiled();
   if (!enc || ((uintptr_t)act & 15u)) return false;
-  const cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, 4, (cuuint64_t)B};
-  const cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16,
+  const cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, 4, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16,
                                  (cuuint64_t)W * H * 64};
-  const cuuint32_t box[5] = {8, (cuuint32_t)TW, (cuuint32_t)R, 4, 1};
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(act), dims,
+  const cuuint32_t box[4] = {(cuuint32_t)kHW * 8, (cuuint32_t)R, 4, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(act), dims,
              strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
