@@ -440,7 +440,9 @@ px_status px_cnn_guess(px_cnn* net, const double* rho, double* phi0, int B, int 
 px_status px_cnn_get_hidden(px_cnn* net, int layer, int which, uint16_t* host, size_t count,
                             void* stream);
 /* Polls per handshake wait (producer, MMA issuer, epilogue) of the
- * tensor-core kernels; 0 restores the default 2^26. A wait that runs out
+ * tensor-core kernels; 0 restores the default 2^24. A poll suspends the
+ * waiting thread for at most 1 us (it resumes as soon as the awaited phase
+ * completes), so a wait lasts at most polls x 1 us. A wait that runs out
  * makes its CTA stop, drain the MMAs it already issued (that wait keeps the
  * default limit), free its tensor memory and raise a device fault word; the
  * next call that reads the loss returns PX_ETIMEOUT and clears the word.

@@ -67,21 +67,33 @@ __device__ __forceinline__ void cp_wait_group() {
 //   t = 1 / (1 + p x),  |error| <= 1.5e-7,
 // so with x = |z| / sqrt 2 one exponential exp(-z^2 / 2) serves both erf and
 // phi. The upper tail Q = 1 - erf(x) gives Phi(z) = 1 - Q / 2 for z >= 0 and
-// Q / 2 for z < 0. The hardware reciprocal and exponential add relative
-// errors near 2^-22; the activations are stored in BF16 (2^-9).
+// Q / 2 for z < 0; the coefficients below are a_i / 2, so the polynomial
+// gives Q / 2 directly. The reciprocal (of 1 + p x >= 1) and the exponential
+// (2^y with y = -z^2 log2(e) / 2) are the hardware approximations with
+// subnormal results flushed to zero (relative errors near 2^-22; a flushed
+// exp(-z^2 / 2) < 2^-126 contributes below 1e-37); the activations are
+// stored in BF16 (2^-9).
+__device__ __forceinline__ float rcp_ftz(float v) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float exp2_ftz(float v) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
 struct NormalCdf {
   float Phi, E;  // Phi(z) and exp(-z^2 / 2)
 };
 __device__ __forceinline__ NormalCdf normal_cdf(float z) {
-  const float x = fabsf(z) * 0.70710678118654752f;
-  const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-  float q = fmaf(1.061405429f, t, -1.453152027f);
-  q = fmaf(q, t, 1.421413741f);
-  q = fmaf(q, t, -0.284496736f);
-  q = fmaf(q, t, 0.254829592f);
-  q *= t;
-  const float E = __expf(-0.5f * z * z);
-  const float h = 0.5f * q * E;  // Q / 2
+  const float t = rcp_ftz(fmaf(0.3275911f * 0.70710678118654752f, fabsf(z), 1.0f));
+  float q = fmaf(0.5f * 1.061405429f, t, 0.5f * -1.453152027f);
+  q = fmaf(q, t, 0.5f * 1.421413741f);
+  q = fmaf(q, t, 0.5f * -0.284496736f);
+  q = fmaf(q, t, 0.5f * 0.254829592f);
+  const float E = exp2_ftz((z * (-0.5f * 1.4426950408889634f)) * z);
+  const float h = (q * t) * E;  // Q / 2
   return {z >= 0.0f ? 1.0f - h : h, E};
 }
 __device__ __forceinline__ float gelu_f(float z) { return z * normal_cdf(z).Phi; }
@@ -145,7 +157,7 @@ constexpr uint32_t kCmHalf = 4 * kCmChunk;                // 8 KB: one half of a
 constexpr size_t kCmTile = (size_t)2 * kCmHalf;           // 16 KB: one tap tile
 constexpr uint32_t kCmWChunk = C * 16;                    // 512 B: next 8-k chunk of the weights
 constexpr size_t kWBytes = (size_t)(K9 / 8) * kCmWChunk;  // 18 KB
-constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint32_t kSpinLimit = 1u << 24;  // polls per wait (a healthy wait takes microseconds)
 __device__ unsigned g_conv_fault;  // set by a conv CTA whose bounded wait ran out
 // instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 32, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(C >> 3) << 17) |
@@ -225,13 +237,18 @@ constexpr size_t kWsSmem = kRingBytes + kWBytes + 256;
 
 // Handshake wait: up to `limit` polls of the barrier's phase, giving up early
 // once another thread of the CTA has set the abort flag; on running out it
-// sets the flag itself.
+// sets the flag itself. Each poll may suspend the thread for up to
+// kPollSuspendNs until the phase completes (try_wait's suspend-time hint), so
+// waiting warps sleep instead of taking issue slots from the working ones;
+// a wait lasts at most limit x kPollSuspendNs.
+constexpr uint32_t kPollSuspendNs = 1000;
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, volatile int* abort_,
                                              uint32_t limit) {
   for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 "selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done) : "r"(bar), "r"(parity), "r"(kPollSuspendNs) : "memory");
     if (done) return true;
     if ((it & 63) == 63 && *abort_) return false;
   }
