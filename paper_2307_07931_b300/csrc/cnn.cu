@@ -696,6 +696,190 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
 }
 
 
+// Weight gradient of a unit-offset 32 -> 32 layer (dilation 1, or a dilated
+// layer over relabelled activations, whose input and dz share positions):
+// the same sums as wgrad32_umma with the nine tap tiles replaced by three
+// column-offset patches. A 2 x 64-pixel tile (K = 128 pixels) stages, for
+// dx = 0..2, the 4-row patch of rows y0 - 1 .. y0 + 2 at columns x0 + dx - 1,
+// and the dz tile, in the conv operands' [half][chunk][row][32 px][8 ch]
+// layout (512-byte half-rows, one box of the tensor memory accelerator per
+// half that lies inside the image, per-pixel copies for halves that wrap).
+// MN-major A of the block for dx: M = (chunk c, dy) for dy = 0..3, whose core
+// matrices sit at (4 c + dy) x 512 B: one descriptor (stride byte offset 512)
+// covers all three taps (dy, dx) of the patch; the fourth dy reads one row
+// past the patch (the next buffer in shared memory) and its rows of D are
+// dropped. K-step ks (16 pixels) of output row ks / 4 starts at that row's
+// half-row offset. A fourth block multiplies a tile of ones: db. D of block
+// dx, TMEM lane 32 w + l: channel 8 w + l % 8, tap (l / 8, dx).
+constexpr int kWuRows = 2;                          // output rows per tile (K = 128 pixels)
+constexpr int kWuPRows = kWuRows + 2;               // patch rows
+constexpr uint32_t kWuPChunk = kWuPRows * kHRow;    // 2 KB
+constexpr uint32_t kWuPHalf = 4 * kWuPChunk;        // 8 KB
+constexpr uint32_t kWuPatch = 2 * kWuPHalf;         // 16 KB
+constexpr uint32_t kWuZChunk = kWuRows * kHRow;     // 1 KB
+constexpr uint32_t kWuZHalf = 4 * kWuZChunk;        // 4 KB
+constexpr uint32_t kWuZ = 3 * kWuPatch;             // dz tile offset (after the patches)
+constexpr uint32_t kWuOnes = kWuZ + 2 * kWuZHalf;   // ones tile offset (4 KB)
+constexpr uint32_t kWuBars = kWuOnes + 4096;        // barriers and flags (64 B)
+constexpr size_t kWuSmem = kWuBars + 64;            // 61.5 KB: three CTAs per SM
+// the last patch's dropped fourth dy reads at most up to here
+static_assert(2 * kWuPatch + kWuPHalf + kHRow + 16 * 16 + 15 * kHRow + 2 * 128 <= kWuBars,
+              "the dropped fourth dy stays inside the buffer");
+
+__global__ void __launch_bounds__(kConvThreads, 3)
+wgrad32_unit(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
+             float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
+             unsigned* __restrict__ fault, uint32_t wait_limit,
+             const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_dz,
+             int use_tma) {
+  // no static shared variables: the core matrices must start on 128-byte boundaries
+  extern __shared__ __align__(128) unsigned char wuu[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wuu + kWuBars);  // [0] boxes, [1] MMAs
+  volatile int* s_ok = reinterpret_cast<volatile int*>(bar + 2);
+  volatile uint32_t* tslot = reinterpret_cast<volatile uint32_t*>(bar + 3);
+  volatile int* abort_ = reinterpret_cast<volatile int*>(bar + 4);  // stays 0: one waiter only
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+  const int my_tiles = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  {
+    uint4* ones = reinterpret_cast<uint4*>(wuu + kWuOnes);  // BF16 1.0 = 0x3f80
+    for (int q = tid; q < 4096 / 16; q += blockDim.x)
+      ones[q] = make_uint4(0x3f803f80u, 0x3f803f80u, 0x3f803f80u, 0x3f803f80u);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32((const void*)tslot)), "r"(kWgTmemCols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 1)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *s_ok = (smem_u32(wuu) & 127u) == 0;
+    *abort_ = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t base = smem_u32(wuu);
+  uint32_t box_par = 0, mma_par = 0;
+
+#pragma unroll 1
+  for (int i = 0; i < my_tiles; ++i) {
+    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+    const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
+    const int y0 = ty * kWuRows, x0 = tx * TW;
+    const bool ok = *s_ok != 0;
+    // which halves come as boxes: bit 2 dx + h for the patches, bit 6 + h for dz
+    uint32_t boxes = 0;
+    const int ysp = wrapn(y0 - 1, H);
+    if (use_tma && ok) {
+      for (int dx = 0; dx < 3; ++dx)
+        for (int h = 0; h < 2; ++h) {
+          const int xs = wrapn(x0 + kHW * h + dx - 1, W);
+          if (ysp + kWuPRows <= H && xs + kHW <= W) boxes |= 1u << (2 * dx + h);
+        }
+      boxes |= 3u << 6;  // the dz tile never wraps (y0 + 2 <= H, x0 + 64 <= W)
+    }
+    if (tid == 0 && boxes) {
+      const uint32_t bytes = (uint32_t)__popc(boxes & 63u) * (4 * kWuPRows * kHRow) +
+                             (uint32_t)__popc(boxes >> 6) * (4 * kWuRows * kHRow);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                   ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+      for (int dx = 0; dx < 3; ++dx)
+        for (int h = 0; h < 2; ++h)
+          if (boxes & (1u << (2 * dx + h)))
+            tma_load_half(base + dx * kWuPatch + h * kWuPHalf, &tmap_in,
+                          wrapn(x0 + kHW * h + dx - 1, W), ysp, b, smem_u32(bar));
+      for (int h = 0; h < 2; ++h)
+        tma_load_half(base + kWuZ + h * kWuZHalf, &tmap_dz, x0 + kHW * h, y0, b, smem_u32(bar));
+    }
+    if (ok) {
+      for (int dx = 0; dx < 3; ++dx)
+        for (int h = 0; h < 2; ++h)
+          if (!(boxes & (1u << (2 * dx + h))))
+            load_half_cm_p<kWuPRows>(wuu + dx * kWuPatch + h * kWuPHalf, in, b, y0, x0 + kHW * h,
+                                     -1, dx - 1, H, W, tid, blockDim.x);
+      for (int h = 0; h < 2; ++h)
+        if (!(boxes & (1u << (6 + h))))
+          load_half_cm_p<kWuRows>(wuu + kWuZ + h * kWuZHalf, dz, b, y0, x0 + kHW * h, 0, 0, H, W,
+                                  tid, blockDim.x);
+    }
+    cp_commit();
+    cp_wait_group<0>();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // copies -> tensor core
+    __syncthreads();
+    if (tid == 0 && ok) {
+      bool good = true;
+      if (boxes) {
+        good = mbar_wait_ab(smem_u32(bar), box_par, abort_, wait_limit);
+        box_par ^= 1u;
+      }
+      if (good) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int blk = 0; blk < 4; ++blk) {
+#pragma unroll
+          for (int ks = 0; ks < (kWuRows * TW) / 16; ++ks) {
+            // output row ro, pixels px0 .. px0 + 15: half px0 / 32 of the tile
+            const int ro = ks >> 2, px0 = (ks & 3) * 16;
+            const uint32_t koff = ro * kHRow + (px0 % kHW) * 16, half = px0 / kHW;
+            const uint64_t ad = blk < 3
+                ? umma_desc(base + blk * kWuPatch + half * kWuPHalf + koff, 128, kHRow)
+                : umma_desc(base + kWuOnes, 128, 256);
+            const uint64_t bd = umma_desc(base + kWuZ + half * kWuZHalf + koff, 128, kWuZChunk);
+            asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                         ::"r"(tmem + blk * C), "l"(ad), "l"(bd), "r"(kIdescMN),
+                           "r"((i > 0 || ks > 0) ? 1u : 0u) : "memory");
+          }
+        }
+        umma_commit(smem_u32(bar + 1));
+        // the buffers are restaged only after these MMAs have read them; a
+        // wait that runs out still drains them before the CTA goes on
+        if (!mbar_wait_ab(smem_u32(bar + 1), mma_par, abort_, wait_limit)) {
+          mbar_wait_drain(smem_u32(bar + 1), mma_par);
+          good = false;
+        }
+        mma_par ^= 1u;
+      } else if (boxes) {
+        mbar_wait_drain(smem_u32(bar), box_par ^ 1u);  // boxes still landing: let them finish
+      }
+      if (!good) *s_ok = 0;
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+
+  float* out = part + (size_t)blockIdx.x * (C * K9 + C);
+  const bool ok = *s_ok != 0;
+#pragma unroll 1
+  for (int blk = 0; blk < 4; ++blk) {
+    uint32_t v[32];
+    if (ok && my_tiles > 0) tmem_ld32(v, tmem + blk * C + ((uint32_t)(warp * 32) << 16));
+    else
+#pragma unroll
+      for (int o = 0; o < C; ++o) v[o] = 0u;
+    const int dy = lane >> 3, c = warp * 8 + (lane & 7);
+    if (blk < 3 && dy < 3) {
+      const int tap = dy * 3 + blk;
+#pragma unroll
+      for (int o = 0; o < C; ++o) out[o * K9 + tap * C + c] = __uint_as_float(v[o]);
+    } else if (blk == 3 && tid == 0) {
+#pragma unroll
+      for (int o = 0; o < C; ++o) out[C * K9 + o] = __uint_as_float(v[o]);
+    }
+  }
+  if (!ok && tid == 0) atomicOr(fault, 1u);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols)
+                 : "memory");
+}
+
 // First layer (1 -> 32) forward: z = b + sum_tap W1[o][tap] x[p + tap]; a = gelu(z).
 // Row-structured loops shared by the three single-channel layers: a CTA takes
 // whole image rows (one division per row), its 4 W threads slots cover
@@ -1308,6 +1492,7 @@ px_status set_conv_attrs() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(conv32_ws<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgUmmaSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wgrad32_unit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWuSmem);
   if (e != cudaSuccess) { cudaGetLastError(); return PX_ECUDA; }
   done = true;
   return PX_OK;
@@ -1440,11 +1625,22 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   const int wg_ctas = std::min(wg_tiles, 2 * px::device_sm_count());
   for (int l = 4; l >= 1; --l) {
     // a[l - 1] and dZ[l] share their positions: unit offsets when relabelled
-    wgrad32_umma<<<wg_ctas, kConvThreads, kWgUmmaSmem, st>>>(
-        n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, P.rel[l] ? 1 : n->dil[l],
-        conv_fault_ptr(), n->wait_limit);
+    int nparts = wg_ctas;
+    if (P.unit[l]) {
+      alignas(64) CUtensorMap tmi, tmz;
+      const int use = n->use_tma && act_tensor_map(&tmi, n->a[l - 1], B, H, W, kWuPRows) &&
+                      act_tensor_map(&tmz, gcur, B, H, W, kWuRows);
+      nparts = std::min(wg_tiles, 3 * px::device_sm_count());
+      wgrad32_unit<<<nparts, kConvThreads, kWuSmem, st>>>(
+          n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWuRows, wg_tiles, conv_fault_ptr(),
+          n->wait_limit, tmi, tmz, use);
+    } else {
+      wgrad32_umma<<<wg_ctas, kConvThreads, kWgUmmaSmem, st>>>(
+          n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWgRows, wg_tiles, n->dil[l],
+          conv_fault_ptr(), n->wait_limit);
+    }
     // reorder [o][tap*32 + c] + bias into W[o][c][tap] + b
-    reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, wg_ctas, n->grads + kOff.w[l], n->grads + kOff.b[l]);
+    reduce_w32<<<(C * K9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nparts, n->grads + kOff.w[l], n->grads + kOff.b[l]);
     alignas(64) CUtensorMap tm;
     const int use = n->use_tma && act_tensor_map(&tm, gcur, B, H, W, P.unit[l] ? kURows : TR);
     // dZ[l - 1] goes in the positions of a[l - 2] (natural order for l = 1)
