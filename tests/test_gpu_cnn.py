@@ -19,6 +19,10 @@ input of a layer, z = bf16(fp32 sum) differs from the FP64 oracle's z by at
 most u |z| (the rounding) plus the FP32 accumulation error of 289 terms,
 289 * 2^-24 * sum|w x| <= 2e-5 S (S bounded by max|x| sum|w| per output
 channel; 5e-5 S is allowed for the tensor cores' accumulation order).
+The GPU's GELU is erf from Abramowitz and Stegun 7.1.26 (|error| <= 1.5e-7)
+with the hardware reciprocal and exponential: within 4.2e-7 of the oracle's
+erf-GELU, and within 1e-6 |z| + 0.01 u |GELU(z)| (the slack of the activation
+bound below) at every FP32 z in [-12, 12] (tests/test_cnn_gelu.py).
 Adam runs in FP32 on FP32 master weights: the update matches the oracle's
 FP64 Adam applied to the same gradients to 1e-5 relative.
 
