@@ -70,6 +70,15 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def bf16_peak_tflops():
+    """Dense BF16 tensor throughput: the measured burst figure, else the
+    fallback of one earlier B300 measurement."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p))["bf16_tflops"])
+    return 1800.0
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -504,6 +513,53 @@ def bench_euler(px, torch, hbm_peak, steps, warmup, n=8192, nsteps=10):
     return out
 
 
+CNN_DILATIONS = (1, 3, 9, 27, 81, 1)
+
+
+def cnn_conv_flops(b: int, n: int) -> float:
+    """Tensor-core FLOPs of one forward pass: four 32 -> 32 layers of 3 x 3 x 32
+    multiply-adds per output channel and pixel (2 FLOPs each)."""
+    return 4 * 2.0 * b * n * n * 32 * 9 * 32
+
+
+def bench_cnn(px, torch, bf16_peak, steps, warmup):
+    """The learned-guess network's kernels: one forward pass at 16 x 256^2
+    and one Adam training step (forward, backward, weight gradients, Adam) at
+    batch 64, random weights of the dilated architecture, CUDA events on the
+    launching stream, median over `steps` calls. tc_TFLOP_s counts only the
+    four tensor-core layers' FLOPs over the whole call (the CUDA-core first
+    and last layers, the loss and Adam are inside the time), so it is a lower
+    bound on the conv kernels' own rate."""
+    out = {"dilations": list(CNN_DILATIONS), "grid": 256}
+    net = px.Cnn(seed=1, dilations=CNN_DILATIONS)
+    rng = np.random.default_rng(0)
+    st = torch.cuda.current_stream()
+    for name, b in (("forward", 16), ("train_step", 64)):
+        x = torch.from_numpy(rng.standard_normal((b, 256, 256)).astype(np.float32)).cuda()
+        t = torch.from_numpy(rng.standard_normal((b, 256, 256)).astype(np.float32)).cuda()
+        y = torch.empty_like(x)
+        call = ((lambda: net.forward(x, y)) if name == "forward" else
+                (lambda: net.train_step(x, t, 1e-4, want_loss=False)))
+        for _ in range(warmup):
+            call()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for e0, e1 in evs:
+            e0.record(st)
+            call()
+            e1.record(st)
+        torch.cuda.synchronize()
+        ms = statistics.median(e0.elapsed_time(e1) for e0, e1 in evs)
+        # training: forward + input gradient + weight gradient = 3 x the forward's conv FLOPs
+        fl = cnn_conv_flops(b, 256) * (1 if name == "forward" else 3)
+        tf = fl / (ms * 1e-3) / 1e12
+        out[name] = {"batch": b, "ms": ms, "tc_TFLOP_s": tf, "tc_frac_of_bf16_peak": tf / bf16_peak}
+        del x, t, y
+    torch.cuda.empty_cache()
+    return out
+
+
 def load_trained_network(px):
     """The learned-guess network trained by paper_2307_07931_b300.learned, if its
     weights ship with the package (data/learned_guess_params.npy)."""
@@ -621,6 +677,9 @@ def digest(line: dict) -> dict:
         e = line["euler"]
         d["euler"] = {k: [r3(v["Gcell_s"]), r3(v["hbm_frac"])] for k, v in e.items()
                       if isinstance(v, dict) and "Gcell_s" in v}
+    if "cnn" in line:
+        d["cnn_ms"] = {k: r3(line["cnn"][k]["ms"]) for k in ("forward", "train_step")
+                       if k in line["cnn"]}
     d["e2e"] = r3(line["e2e"]["value"])
     return d
 
@@ -771,6 +830,7 @@ def run_gpu(args, world, rank, local):
     ttt = bench_time_to_tol(px, torch) if not args.quick else None
     c3 = bench_c3(px, torch, budget_s=args.c3_budget) if not args.quick else None
     euler = bench_euler(px, torch, hbm_peak, min(K, 5), min(W, 3))
+    cnn = bench_cnn(px, torch, bf16_peak_tflops(), max(5, min(K, 10)), max(3, min(W, 3)))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -826,6 +886,7 @@ def run_gpu(args, world, rank, local):
         if c3 is not None:
             line["refine_8192"] = c3
         line["euler"] = euler
+        line["cnn"] = cnn
         if cpu is not None:
             line["cpu_baseline"] = cpu
         # compact digest of the extra blocks, last in the line so that a

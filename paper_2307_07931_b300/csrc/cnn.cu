@@ -101,6 +101,33 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   const NormalCdf c = normal_cdf(z);
   return fmaf(z * 0.39894228040143268f, c.E, c.Phi);
 }
+// The same operations on a pair of values with the packed FP32 instructions
+// (add/mul/fma.rn.f32x2 round each half like the scalar instruction, so the
+// results are bitwise those of normal_cdf, gelu_f and gelu_grad_f): one issue
+// slot per two values for the polynomial and the products. The reciprocal,
+// the exponential and the sign select stay per value.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+struct NormalCdf2 {
+  float2 Phi, E;
+};
+__device__ __forceinline__ NormalCdf2 normal_cdf2(float2 z) {
+  const float2 t = make_float2(rcp_ftz(fmaf(0.3275911f * 0.70710678118654752f, fabsf(z.x), 1.0f)),
+                               rcp_ftz(fmaf(0.3275911f * 0.70710678118654752f, fabsf(z.y), 1.0f)));
+  float2 q = __ffma2_rn(f2(0.5f * 1.061405429f), t, f2(0.5f * -1.453152027f));
+  q = __ffma2_rn(q, t, f2(0.5f * 1.421413741f));
+  q = __ffma2_rn(q, t, f2(0.5f * -0.284496736f));
+  q = __ffma2_rn(q, t, f2(0.5f * 0.254829592f));
+  const float2 y = __fmul2_rn(__fmul2_rn(z, f2(-0.5f * 1.4426950408889634f)), z);
+  const float2 E = make_float2(exp2_ftz(y.x), exp2_ftz(y.y));
+  const float2 h = __fmul2_rn(__fmul2_rn(q, t), E);          // Q / 2
+  const float2 u = __ffma2_rn(h, f2(-1.0f), f2(1.0f));       // 1 - h, one rounding
+  return {make_float2(z.x >= 0.0f ? u.x : h.x, z.y >= 0.0f ? u.y : h.y), E};
+}
+__device__ __forceinline__ float2 gelu_f2(float2 z) { return __fmul2_rn(z, normal_cdf2(z).Phi); }
+__device__ __forceinline__ float2 gelu_grad_f2(float2 z) {
+  const NormalCdf2 c = normal_cdf2(z);
+  return __ffma2_rn(__fmul2_rn(z, f2(0.39894228040143268f)), c.E, c.Phi);
+}
 
 
 // Element offset of channel chunk `chunk` (8 channels) of pixel (b, y, x).
@@ -354,10 +381,9 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
 #pragma unroll
     for (int o = 0; o < C; o += 2) {
       const float2 bb = *reinterpret_cast<const float2*>(sbias + o);  // same address: broadcast
-      const float v0 = __uint_as_float(v[o]) + bb.x;
-      const float v1 = __uint_as_float(v[o + 1]) + bb.y;
-      zz[o / 2] = __floats2bfloat162_rn(v0, v1);
-      aa[o / 2] = __floats2bfloat162_rn(gelu_f(v0), gelu_f(v1));
+      const float2 vz = __fadd2_rn(make_float2(__uint_as_float(v[o]), __uint_as_float(v[o + 1])), bb);
+      zz[o / 2] = __float22bfloat162_rn(vz);
+      aa[o / 2] = __float22bfloat162_rn(gelu_f2(vz));
     }
     if (zout) {
 #pragma unroll
@@ -369,8 +395,9 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
     load_px32(zf, zprev + act_off(b, y, x, 0, H, W), plane);
 #pragma unroll
     for (int o = 0; o < C; o += 2)
-      aa[o / 2] = __floats2bfloat162_rn(__uint_as_float(v[o]) * gelu_grad_f(zf[o]),
-                                        __uint_as_float(v[o + 1]) * gelu_grad_f(zf[o + 1]));
+      aa[o / 2] = __float22bfloat162_rn(
+          __fmul2_rn(make_float2(__uint_as_float(v[o]), __uint_as_float(v[o + 1])),
+                     gelu_grad_f2(make_float2(zf[o], zf[o + 1]))));
   }
 #pragma unroll
   for (int k = 0; k < 4; ++k)

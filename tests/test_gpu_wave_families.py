@@ -75,3 +75,80 @@ def test_balanced_register_kernel_bitwise():
             px.relax_n(phi, a, rho, h, 2 / 3, 8, tb, ra, 1)
             torch.cuda.synchronize()
             assert torch.equal(a, b) and torch.equal(ra, rb), (nx, ny, tb)
+
+
+@pytest.mark.parametrize("family", ["r", "rp"])
+def test_register_kernel_report_spacings_bitwise(family):
+    """The register wavefront reports only the stages whose input state is
+    due (a flag per stage); for report spacings 1, 2, 3, 5, 16 and no report,
+    its states and reports are bitwise those of the single-sweep kernel, at
+    every depth 2..8 (8-warp and 12-warp launches) and sizes with several
+    strips and ranges."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_FP32_FAMILY, FAMILIES[family])
+        g = torch.Generator(device="cuda")
+        g.manual_seed(23)
+        for (nx, ny) in [(1000, 1002), (2052, 300), (124, 64)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            o1, ot = torch.empty_like(phi), torch.empty_like(phi)
+            for every in (1, 2, 3, 5, 16, 0):
+                n = 17
+                k = (n + every - 1) // every if every else 1
+                r1 = torch.zeros(k, dtype=torch.float64, device="cuda")
+                rt = torch.full_like(r1, -1.0)
+                px.relax_n(phi, o1, rho, h, 2 / 3, n, 1, r1 if every else None, every, ctx=ctx)
+                for tb in range(2, 9):
+                    rt.fill_(-1.0)
+                    px.relax_n(phi, ot, rho, h, 2 / 3, n, tb, rt if every else None, every,
+                               ctx=ctx)
+                    torch.cuda.synchronize()
+                    assert torch.equal(o1, ot), (family, nx, ny, tb, every)
+                    if every:
+                        assert torch.equal(r1, rt), (family, nx, ny, tb, every)
+    finally:
+        ctx.close()
+
+
+@pytest.mark.parametrize("sweeps", [2, 4])
+def test_red_black_register_report_spacings_bitwise(sweeps):
+    """Red-black register wavefront launches with reports on every sweep,
+    every other or third sweep and none give bitwise the states and reports
+    of the two-pass kernels (pitched copies take those)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_RB_SWEEPS_PER_LAUNCH, sweeps)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        nx, ny = 1000, 1002
+        h = 1.0 / nx
+        rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+        phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+
+        def pitched(a):
+            b = torch.zeros(ny, nx + 1, device="cuda", dtype=torch.float32)[:, :nx]
+            b.copy_(a)
+            return b
+        pp, rp, op = pitched(phi), pitched(rho), pitched(torch.zeros_like(phi))
+        out = torch.empty_like(phi)
+        for every in (1, 2, 3, 0):
+            n = 13
+            k = (n + every - 1) // every if every else 1
+            r1 = torch.zeros(k, dtype=torch.float64, device="cuda")
+            r2 = torch.full_like(r1, -1.0)
+            px.rbsor_n(pp, op, rp, h, 1.3, n, r1 if every else None, every, ctx=ctx)
+            px.rbsor_n(phi, out, rho, h, 1.3, n, r2 if every else None, every, ctx=ctx)
+            torch.cuda.synchronize()
+            assert torch.equal(op, out), every
+            if every:
+                assert torch.equal(r1, r2), every
+    finally:
+        ctx.close()
