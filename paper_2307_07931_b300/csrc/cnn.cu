@@ -249,11 +249,12 @@ constexpr size_t kUTile = (size_t)2 * kUHalf;          // 24 KB
 constexpr int kUStages = 3;
 constexpr size_t kRingBytes = kUStages * kUTile > kWsStages * kCmTile ? kUStages * kUTile
                                                                       : kWsStages * kCmTile;
-// A producer declares step g complete kWsAhead steps later (kWsAhead <
-// kWsStages, or it would wait on its own undeclared step). One step measured
-// fastest: with more copies in flight the tap tiles contend in L2 (whole
-// forward at 16 x 256^2: 0.93 ms at one step ahead, 1.03 ms at three).
-constexpr int kWsAhead = 1;
+// A producer declares a step with per-pixel copies complete one step later
+// (after the next step's copies are issued: its own copies then wait only
+// for the older group), and a step of boxes only at once. One step ahead
+// measured fastest for the copies: with more copies in flight the tap tiles
+// contend in L2 (whole forward at 16 x 256^2: 0.93 ms at one step ahead,
+// 1.03 ms at three, with per-pixel copies throughout).
 constexpr int kWsEpiWarps = 4, kWsProdWarps = 4;
 constexpr int kWsConvThreads = (kWsEpiWarps + kWsProdWarps + 1) * 32;  // 288
 constexpr uint32_t kWsTmemCols = 128;                                 // 2 sets x (2 x 32)
@@ -360,8 +361,13 @@ __device__ __forceinline__ void load_tap_cm_p(unsigned char* dst, const __nv_bfl
 
 // Position of the output pixel computed at input position (y, x): the
 // coordinates times (ry, rx), modulo the image (identity when both are 1).
+// 0 <= v, r < n: the product fits 32 unsigned bits for n <= 65535, where the
+// 32-bit remainder (a few instructions) replaces the 64-bit one (a library
+// routine per call).
 __device__ __forceinline__ int relabel(int v, int r, int n) {
-  return r == 1 ? v : (int)(((int64_t)v * r) % n);
+  if (r == 1) return v;
+  if (n <= 65535) return (int)(((unsigned)v * (unsigned)r) % (unsigned)n);
+  return (int)(((int64_t)v * r) % n);
 }
 
 template <int kMode>
@@ -376,32 +382,38 @@ __device__ __forceinline__ void conv_epilogue_half(const uint32_t (&v)[32], int 
   // pb: the output's position; zprev shares the input's positions
   const int64_t pb = act_off(b, relabel(y, ry, H), relabel(x, rx, W), 0, H, W),
                 plane = (int64_t)H * W * 8;
-  __nv_bfloat162 zz[C / 2], aa[C / 2];
   if (kMode == 0) {
+    // one 8-channel chunk at a time, its two 16-byte stores right after its
+    // values: few values live between the accumulator read and the stores
 #pragma unroll
-    for (int o = 0; o < C; o += 2) {
-      const float2 bb = *reinterpret_cast<const float2*>(sbias + o);  // same address: broadcast
-      const float2 vz = __fadd2_rn(make_float2(__uint_as_float(v[o]), __uint_as_float(v[o + 1])), bb);
-      zz[o / 2] = __float22bfloat162_rn(vz);
-      aa[o / 2] = __float22bfloat162_rn(gelu_f2(vz));
-    }
-    if (zout) {
+    for (int k = 0; k < 4; ++k) {
+      __nv_bfloat162 zz[4], aa[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        *reinterpret_cast<uint4*>(zout + pb + k * plane) = reinterpret_cast<const uint4*>(zz)[k];
+      for (int e = 0; e < 4; ++e) {
+        const int o = 8 * k + 2 * e;
+        const float2 bb = *reinterpret_cast<const float2*>(sbias + o);  // same address: broadcast
+        const float2 vz = __fadd2_rn(make_float2(__uint_as_float(v[o]), __uint_as_float(v[o + 1])), bb);
+        zz[e] = __float22bfloat162_rn(vz);
+        aa[e] = __float22bfloat162_rn(gelu_f2(vz));
+      }
+      if (zout) *reinterpret_cast<uint4*>(zout + pb + k * plane) = *reinterpret_cast<const uint4*>(zz);
+      *reinterpret_cast<uint4*>(aout + pb + k * plane) = *reinterpret_cast<const uint4*>(aa);
     }
   } else {
+    // the input gradient: all four chunks of z in flight first (chunk-wise
+    // loads next to their uses measured 20 % slower)
     float zf[C];
     load_px32(zf, zprev + act_off(b, y, x, 0, H, W), plane);
+    __nv_bfloat162 aa[C / 2];
 #pragma unroll
     for (int o = 0; o < C; o += 2)
       aa[o / 2] = __float22bfloat162_rn(
           __fmul2_rn(make_float2(__uint_as_float(v[o]), __uint_as_float(v[o + 1])),
                      gelu_grad_f2(make_float2(zf[o], zf[o + 1]))));
-  }
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
-    *reinterpret_cast<uint4*>(aout + pb + k * plane) = reinterpret_cast<const uint4*>(aa)[k];
+    for (int k = 0; k < 4; ++k)
+      *reinterpret_cast<uint4*>(aout + pb + k * plane) = reinterpret_cast<const uint4*>(aa)[k];
+  }
 }
 
 // kUnit: the unit-offset staging (three dx patches per tile; `dil` is then
@@ -467,6 +479,8 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
     mbar_arrive(wfull);
     bool go = *abort_ == 0;
     int g = 0;
+    int pend = -1;  // step whose copies this thread has issued but not declared
+    const bool pnear = kUnit || (dil < H && dil < W);
     for (int i = 0; i < my_tiles && go; ++i) {
       const int tile = (int)blockIdx.x + i * (int)gridDim.x;
       const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
@@ -478,8 +492,11 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         const int oy = kUnit ? -1 : tap_dy(step, dil), ox = kUnit ? step - 1 : tap_dx(step, dil);
         constexpr int kR = kUnit ? kURows : TR;
         constexpr uint32_t kHalfB = kStage / 2;
-        const int ys = wrapn(ty * TR + oy, H);
-        const int xs0 = wrapn(tx * TW + ox, W), xs1 = wrapn(tx * TW + kHW + ox, W);
+        // the starts lie within one period of the image when the offsets do
+        // (always for unit offsets): a conditional add instead of a remainder
+        const int ys = pnear ? wrap1(ty * TR + oy, H) : wrapn(ty * TR + oy, H);
+        const int xs0 = pnear ? wrap1(tx * TW + ox, W) : wrapn(tx * TW + ox, W);
+        const int xs1 = pnear ? wrap1(tx * TW + kHW + ox, W) : wrapn(tx * TW + kHW + ox, W);
         // a half that lies inside the image is one box, issued by one thread;
         // one that wraps around the periodic edge takes per-pixel copies
         const bool box0 = use_tma && ys + kR <= H && xs0 + kHW <= W;
@@ -493,17 +510,24 @@ conv32_ws(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict_
         if (!box0) load_half_cm_p<kR>(dst, in, b, ty * TR, tx * TW, oy, ox, H, W, pid, np);
         if (!box1) load_half_cm_p<kR>(dst + kHalfB, in, b, ty * TR, tx * TW + kHW, oy, ox, H, W, pid, np);
         cp_commit();
-        if (g >= kWsAhead) {  // copies of step g - kWsAhead: done, visible to the tensor core
-          cp_wait_group<kWsAhead>();
+        // A step with copies is declared one step later, once they have
+        // landed (the thread's older copy groups: all but the newest); a step
+        // of boxes only is declared at once, its boxes completing the phase
+        // by their byte count.
+        if (pend >= 0) {
+          cp_wait_group<1>();
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(full0 + 8 * ((g - kWsAhead) % kStages));
+          mbar_arrive(full0 + 8 * (pend % kStages));
+          pend = -1;
         }
+        if (box0 && box1) mbar_arrive(full0 + 8 * st);
+        else pend = g;
       }
     }
     cp_wait_group<0>();
-    if (go) {
+    if (go && pend >= 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      for (int k = g > kWsAhead ? g - kWsAhead : 0; k < g; ++k) mbar_arrive(full0 + 8 * (k % kStages));
+      mbar_arrive(full0 + 8 * (pend % kStages));
     }
   } else if (warp == kWsEpiWarps + kWsProdWarps) {
     // ---- MMA issue
