@@ -772,7 +772,8 @@ def run_gpu(args, world, rank, local):
     # place and never write it). Steps are pipelined the way a user streaming
     # problems would run them: two device buffer sets, the upload of step k+1
     # and the download of step k-1 overlap the sweeps of step k (PCIe is full
-    # duplex), and a set is refilled only after its previous download finished.
+    # duplex). A set's rho buffer is refilled once the sweeps that read it have
+    # finished, its output buffer rewritten once its download has finished.
     pin_rho = rho32_host.pin_memory()
     pin_out = torch.empty_like(pin_rho).pin_memory()
     pin_res = torch.empty(SWEEPS, dtype=torch.float64).pin_memory()
@@ -780,28 +781,32 @@ def run_gpu(args, world, rank, local):
     sets = [{"rho": torch.empty_like(rho["f32"]), "out": torch.empty_like(rho["f32"]),
              "res": torch.zeros(SWEEPS, dtype=torch.float64, device="cuda")} for _ in range(2)]
     s_up, s_cmp, s_down = (torch.cuda.Stream() for _ in range(3))
-    freed = [None, None]
+    rho_free = [None, None]  # per set: the sweeps that read its rho are done
+    out_free = [None, None]  # per set: the download of its output is done
 
     def e2e_step(k):
         S = sets[k % 2]
         with torch.cuda.stream(s_up):
-            if freed[k % 2] is not None:
-                s_up.wait_event(freed[k % 2])
+            if rho_free[k % 2] is not None:
+                s_up.wait_event(rho_free[k % 2])
             S["rho"].copy_(pin_rho, non_blocking=True)
             up = torch.cuda.Event()
             up.record(s_up)
         s_cmp.wait_event(up)
+        if out_free[k % 2] is not None:
+            s_cmp.wait_event(out_free[k % 2])
         px.relax_n(zero_phi, S["out"], S["rho"], h, OMEGA, SWEEPS, 0, S["res"], 1,
                    stream=s_cmp.cuda_stream)
         done = torch.cuda.Event()
         done.record(s_cmp)
+        rho_free[k % 2] = done
         s_down.wait_event(done)
         with torch.cuda.stream(s_down):
             pin_out.copy_(S["out"], non_blocking=True)
             pin_res.copy_(S["res"], non_blocking=True)
             fr = torch.cuda.Event()
             fr.record(s_down)
-        freed[k % 2] = fr
+        out_free[k % 2] = fr
 
     def e2e_run(nsteps):
         torch.cuda.synchronize()
