@@ -83,29 +83,12 @@ __device__ __forceinline__ float exp2_ftz(float v) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
   return r;
 }
-struct NormalCdf {
-  float Phi, E;  // Phi(z) and exp(-z^2 / 2)
-};
-__device__ __forceinline__ NormalCdf normal_cdf(float z) {
-  const float t = rcp_ftz(fmaf(0.3275911f * 0.70710678118654752f, fabsf(z), 1.0f));
-  float q = fmaf(0.5f * 1.061405429f, t, 0.5f * -1.453152027f);
-  q = fmaf(q, t, 0.5f * 1.421413741f);
-  q = fmaf(q, t, 0.5f * -0.284496736f);
-  q = fmaf(q, t, 0.5f * 0.254829592f);
-  const float E = exp2_ftz((z * (-0.5f * 1.4426950408889634f)) * z);
-  const float h = (q * t) * E;  // Q / 2
-  return {z >= 0.0f ? 1.0f - h : h, E};
-}
-__device__ __forceinline__ float gelu_f(float z) { return z * normal_cdf(z).Phi; }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  const NormalCdf c = normal_cdf(z);
-  return fmaf(z * 0.39894228040143268f, c.E, c.Phi);
-}
-// The same operations on a pair of values with the packed FP32 instructions
-// (add/mul/fma.rn.f32x2 round each half like the scalar instruction, so the
-// results are bitwise those of normal_cdf, gelu_f and gelu_grad_f): one issue
-// slot per two values for the polynomial and the products. The reciprocal,
-// the exponential and the sign select stay per value.
+// The formula is evaluated on pairs of values with the packed FP32
+// instructions (add/mul/fma.rn.f32x2 round each half like the scalar
+// instruction, so each half takes the scalar sequence of roundings: t, the
+// polynomial in Horner form, E, h = (q t) E, then 1 - h): one issue slot per
+// two values for the polynomial and the products. The reciprocal, the
+// exponential and the sign select stay per value.
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 struct NormalCdf2 {
   float2 Phi, E;
@@ -976,7 +959,7 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
           s1 = fmaf(wr[j + 1][tap], v[tap], s1);
         }
         zz[j / 2] = __floats2bfloat162_rn(s0, s1);
-        aa[j / 2] = __floats2bfloat162_rn(gelu_f(s0), gelu_f(s1));
+        aa[j / 2] = __float22bfloat162_rn(gelu_f2(make_float2(s0, s1)));
       }
       const int64_t po = act_off(img, yy, xx, cg, H, W);
       if (zout) *reinterpret_cast<uint4*>(zout + po) = *reinterpret_cast<const uint4*>(zz);
@@ -990,6 +973,12 @@ __global__ void conv_first(const float* __restrict__ x, const float* __restrict_
 // Four threads per pixel sum 8 channels each (coalesced 16-byte loads: a warp
 // reads 8 whole pixels per tap), then combine their partial sums in a fixed
 // order with two shuffles (W is a multiple of 8, so whole warps iterate).
+// The kernel is bound by the L1 bandwidth of its 16-byte tap loads (9 per
+// thread and pixel). At dilation 1 (kRows = 4) a thread computes four output
+// rows of one column: each of the six input rows' three columns is loaded
+// once and serves every output row it is a tap of, 4.5 loads per pixel
+// instead of 9; each output keeps its own sum in tap order.
+template <int kRows>
 __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __restrict__ w6,
                           const float* __restrict__ b6, float* __restrict__ y, int B, int H, int W,
                           int dil) {
@@ -1001,32 +990,47 @@ __global__ void conv_last(const __nv_bfloat16* __restrict__ a, const float* __re
     for (int tap = 0; tap < 9; ++tap) wr[j][tap] = __ldg(w6 + (cg * 8 + j) * 9 + tap);
   const float bias = __ldg(b6);
   const bool near = dil < W;
-  for (int row = blockIdx.x; row < B * H; row += gridDim.x) {
+  // kRows > 1: dil == 1 and H % kRows == 0 (checked by the launcher)
+  for (int rb = blockIdx.x; rb < B * H / kRows; rb += gridDim.x) {
+    const int row = rb * kRows;  // first output row of the block
     const int img = row / H, yy = row - img * H;
-    const __nv_bfloat16* ar[3];
+    constexpr int kIn = kRows == 1 ? 3 : kRows + 2;  // distinct input rows
+    const __nv_bfloat16* ar[kIn];
 #pragma unroll
-    for (int ty = 0; ty < 3; ++ty)
-      ar[ty] = a + act_off(img, wrapn(yy + (ty - 1) * dil, H), 0, cg, H, W);
+    for (int r = 0; r < kIn; ++r)
+      ar[r] = a + act_off(img, wrapn(yy + (kRows == 1 ? (r - 1) * dil : r - 1), H), 0, cg, H, W);
     for (int t = threadIdx.x; t < 4 * W; t += blockDim.x) {
       const int xx = t >> 2;
       const int xs[3] = {wrap_col(xx - dil, W, near), xx, wrap_col(xx + dil, W, near)};
-      float s = 0.f;
+      float s[kRows];
 #pragma unroll
-      for (int ty = 0; ty < 3; ++ty)
+      for (int j = 0; j < kRows; ++j) s[j] = 0.f;
+#pragma unroll
+      for (int r = 0; r < kIn; ++r)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) {
-          const uint4 u = __ldg(reinterpret_cast<const uint4*>(ar[ty] + (int64_t)xs[tx] * 8));
+          const uint4 u = __ldg(reinterpret_cast<const uint4*>(ar[r] + (int64_t)xs[tx] * 8));
           const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
+          // input row r is tap row ty = r - j of output row j
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 f = __bfloat1622float2(hv[e]);
-            s = fmaf(wr[2 * e][ty * 3 + tx], f.x, s);
-            s = fmaf(wr[2 * e + 1][ty * 3 + tx], f.y, s);
+          for (int j = 0; j < kRows; ++j) {
+            const int ty = r - j;
+            if (ty < 0 || ty > 2) continue;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f = __bfloat1622float2(hv[e]);
+              s[j] = fmaf(wr[2 * e][ty * 3 + tx], f.x, s[j]);
+              s[j] = fmaf(wr[2 * e + 1][ty * 3 + tx], f.y, s[j]);
+            }
           }
         }
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (cg == 0) y[(int64_t)row * W + xx] = bias + s;
+#pragma unroll
+      for (int j = 0; j < kRows; ++j) {
+        float v = s[j];
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (cg == 0) y[(int64_t)(row + j) * W + xx] = bias + v;
+      }
     }
   }
 }
@@ -1092,7 +1096,7 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
           s0 = fmaf(wr[2 * e][tap], g[tap], s0);
           s1 = fmaf(wr[2 * e + 1][tap], g[tap], s1);
         }
-        o[e] = __floats2bfloat162_rn(s0 * gelu_grad_f(z.x), s1 * gelu_grad_f(z.y));
+        o[e] = __float22bfloat162_rn(__fmul2_rn(make_float2(s0, s1), gelu_grad_f2(z)));
       }
       *reinterpret_cast<uint4*>(dz5 + po) = *reinterpret_cast<const uint4*>(o);
     }
@@ -1104,26 +1108,39 @@ __global__ void back_last(const float* __restrict__ dy, const float* __restrict_
 //   mode 1 (last):  dW6[c][tap] = sum_p s1[p] * g32[p + off(tap)][c],  db6    = sum_p s1[p]
 // Mode 1 is computed as sum_q g32[q][c] * s1[q - off(tap)]: both modes are
 // then "32-channel image times a shifted single-channel image", with the
-// shift sign flipped. A CTA of 256 threads owns a range of image rows; thread
-// t takes channels 8 (t & 3) .. +7 and pixel slot t >> 2 (64 slots striding
-// along each row), and keeps 72 independent accumulators. The wrapped
-// neighbour rows are found once per row. The CTA reduces its threads in a
-// fixed order (shuffles within a warp, then warps in index order) and writes
-// one partial per CTA, so the result is deterministic.
+// shift sign flipped. A CTA of 256 threads owns a range of image rows; kQ
+// threads share a pixel, thread t taking channels (32 / kQ) (t % kQ) .. and
+// pixel slot t / kQ (striding along each row), with 9 x 32 / kQ independent
+// accumulators. kQ = 8 (36 accumulators, three CTAs per SM) measured faster
+// for the last layer (220 against 372 us at batch 64), kQ = 4 (72, two CTAs,
+// half the loads of the shifted image per pixel) for the first (201 against
+// 222 us). The wrapped neighbour rows are found once per row. The CTA reduces
+// its threads in a fixed order (shuffles within a warp, then warps in index
+// order) and writes one partial per CTA, so the result is deterministic.
 constexpr int kWsThreads = 256;
+template <int kMode> constexpr int ws_q() { return kMode == 0 ? 4 : 8; }
+template <int kMode> constexpr int ws_ctas_per_sm() { return kMode == 0 ? 2 : 3; }
+// CTAs launched per SM: one resident wave for kQ = 8, two waves for kQ = 4
+// (measured at batch 64; the row ranges are then shorter)
+template <int kMode> constexpr int ws_split_per_sm() { return kMode == 0 ? 4 : 3; }
 template <int kMode>
-__global__ void __launch_bounds__(kWsThreads)
+__global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<kMode>())
 wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1,
              float* __restrict__ part, int B, int H, int W, int rows_per_cta, int dil) {
-  __shared__ float red[kWsThreads / 32][4][C / 4 * 9 + C / 4];
-  const int cg = threadIdx.x & 3, slot = threadIdx.x >> 2;
+  constexpr int kQ = ws_q<kMode>();   // threads per pixel
+  constexpr int kN = C / kQ;          // channels per thread: 8 or 4
+  constexpr int kSlots = kWsThreads / kQ;
+  constexpr int kJ = kN * 9 + kN;     // a thread's products and sums
+  __shared__ float red[kWsThreads / 32][kQ][kJ];
+  const int cq = threadIdx.x & (kQ - 1), slot = threadIdx.x / kQ;
+  const int c0 = cq * kN, chunk = c0 / 8, sub = c0 % 8;  // channels c0 .. c0 + kN - 1
   const int sd = kMode == 0 ? dil : -dil;  // shift of s1 relative to g32
   const bool near = dil < W;
   const int rows = B * H;
   const int r0 = blockIdx.x * rows_per_cta, r1 = min(rows, r0 + rows_per_cta);
-  float acc[8][9], accb[8];
+  float acc[kN][9], accb[kN];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < kN; ++k) {
     accb[k] = 0.f;
 #pragma unroll
     for (int tp = 0; tp < 9; ++tp) acc[k][tp] = 0.f;
@@ -1134,63 +1151,72 @@ wgrad_single(const __nv_bfloat16* __restrict__ g32, const float* __restrict__ s1
     const float* srow[3];
 #pragma unroll
     for (int ty = 0; ty < 3; ++ty) srow[ty] = s1 + ibase + (int64_t)wrapn(y + (ty - 1) * sd, H) * W;
-    const __nv_bfloat16* grow = g32 + act_off(img, y, 0, cg, H, W);
-    for (int x = slot; x < W; x += kWsThreads / 4) {
+    const __nv_bfloat16* grow = g32 + act_off(img, y, 0, chunk, H, W) + sub;
+    for (int x = slot; x < W; x += kSlots) {
       const int xs[3] = {wrap_col(x - sd, W, near), x, wrap_col(x + sd, W, near)};
       float sv[9];
 #pragma unroll
       for (int ty = 0; ty < 3; ++ty)
 #pragma unroll
         for (int tx = 0; tx < 3; ++tx) sv[ty * 3 + tx] = __ldg(srow[ty] + xs[tx]);
-      const uint4 u = __ldg(reinterpret_cast<const uint4*>(grow + (int64_t)x * 8));
-      const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
-      float g[8];
+      float g[kN];
+      if constexpr (kN == 8) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(grow + (int64_t)x * 8));
+        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float2 f = __bfloat1622float2(hv[e]);
-        g[2 * e] = f.x;
-        g[2 * e + 1] = f.y;
+        for (int e = 0; e < 4; ++e) {
+          const float2 f = __bfloat1622float2(hv[e]);
+          g[2 * e] = f.x;
+          g[2 * e + 1] = f.y;
+        }
+      } else {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(grow + (int64_t)x * 8));
+        const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float2 f = __bfloat1622float2(hv[e]);
+          g[2 * e] = f.x;
+          g[2 * e + 1] = f.y;
+        }
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
+      for (int k = 0; k < kN; ++k) {
 #pragma unroll
         for (int tp = 0; tp < 9; ++tp) acc[k][tp] = fmaf(g[k], sv[tp], acc[k][tp]);
         if (kMode == 0) accb[k] += g[k];
       }
-      if (kMode == 1 && cg == 0) accb[0] += sv[4];
+      if (kMode == 1 && cq == 0) accb[0] += sv[4];
     }
   }
-  // lanes l, l ^ 4, l ^ 8, l ^ 16 share a channel group: reduce them
+  // lanes l, l ^ kQ, l ^ 2 kQ, ... share a channel group: reduce them
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < kN; ++k) {
 #pragma unroll
     for (int tp = 0; tp < 9; ++tp) {
       float v = acc[k][tp];
-      v += __shfl_xor_sync(0xffffffffu, v, 4);
-      v += __shfl_xor_sync(0xffffffffu, v, 8);
-      v += __shfl_xor_sync(0xffffffffu, v, 16);
-      if (lane < 4) red[warp][cg][k * 9 + tp] = v;
+#pragma unroll
+      for (int o = kQ; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane < kQ) red[warp][cq][k * 9 + tp] = v;
     }
     float vb = accb[k];
-    vb += __shfl_xor_sync(0xffffffffu, vb, 4);
-    vb += __shfl_xor_sync(0xffffffffu, vb, 8);
-    vb += __shfl_xor_sync(0xffffffffu, vb, 16);
-    if (lane < 4) red[warp][cg][C / 4 * 9 + k] = vb;
+#pragma unroll
+    for (int o = kQ; o < 32; o <<= 1) vb += __shfl_xor_sync(0xffffffffu, vb, o);
+    if (lane < kQ) red[warp][cq][kN * 9 + k] = vb;
   }
   __syncthreads();
   float* out = part + (size_t)blockIdx.x * (C * 9 + C);
-  for (int i = threadIdx.x; i < 4 * (C / 4 * 9 + C / 4); i += blockDim.x) {
-    const int g = i / (C / 4 * 9 + C / 4), j = i - g * (C / 4 * 9 + C / 4);
+  for (int i = threadIdx.x; i < kQ * kJ; i += blockDim.x) {
+    const int q = i / kJ, j = i - q * kJ;
     float v = 0.f;
-    for (int w = 0; w < kWsThreads / 32; ++w) v += red[w][g][j];
-    if (j < C / 4 * 9) {
+    for (int w = 0; w < kWsThreads / 32; ++w) v += red[w][q][j];
+    if (j < kN * 9) {
       const int k = j / 9, tp = j - k * 9;
-      out[(g * 8 + k) * 9 + tp] = v;  // channel g*8 + k, tap tp
+      out[(q * kN + k) * 9 + tp] = v;  // channel q kN + k, tap tp
     } else if (kMode == 0) {
-      out[C * 9 + g * 8 + (j - C / 4 * 9)] = v;
-    } else if (g == 0 && j == C / 4 * 9) {
-      out[C * 9] = v;  // db6: only channel group 0 summed s1
+      out[C * 9 + q * kN + (j - kN * 9)] = v;
+    } else if (q == 0 && j == kN * 9) {
+      out[C * 9] = v;  // db6: only group 0 summed s1
     }
   }
 }
@@ -1638,8 +1664,12 @@ px_status forward(px_cnn* n, const float* x, float* y, int B, int H, int W, bool
                      mul_mod(ny, P.my[l], H), mul_mod(nx, P.mx[l], W), fault, n->wait_limit, tm,
                      use);
   }
-  conv_last<<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
-                                              n->params + kOff.b[5], y, B, H, W, n->dil[5]);
+  if (n->dil[5] == 1 && H % 4 == 0)
+    conv_last<4><<<std::min(B * H / 4, 8 * px::device_sm_count()), 256, 0, st>>>(
+        n->a[4], n->params + kOff.w[5], n->params + kOff.b[5], y, B, H, W, 1);
+  else
+    conv_last<1><<<rows_grid, 256, 0, st>>>(n->a[4], n->params + kOff.w[5],
+                                            n->params + kOff.b[5], y, B, H, W, n->dil[5]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network forward");
 }
@@ -1656,12 +1686,18 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
   mse_grad<<<lblocks, 256, 0, st>>>(n->y, t, n->dy, n->lpart, px);
   *nloss = lblocks;
   // last layer
-  // single-channel weight gradients: whole image rows per CTA, about four CTAs per SM
+  // single-channel weight gradients: whole image rows per CTA
   const int rows = B * H;
-  const int64_t want = std::min<int64_t>((int64_t)px::device_sm_count() * 4,
-                                         (int64_t)(n->part_floats / (C * 9 + C)));
-  const int rpc = (int)((rows + want - 1) / want);
-  const int nsc_cap = (rows + rpc - 1) / rpc;
+  auto single_split = [&](int per_sm, int* rpc_out) {
+    const int64_t want = std::min<int64_t>((int64_t)px::device_sm_count() * per_sm,
+                                           (int64_t)(n->part_floats / (C * 9 + C)));
+    const int r = (int)((rows + want - 1) / want);
+    *rpc_out = r;
+    return (rows + r - 1) / r;
+  };
+  int rpc = 0, rpc0 = 0;
+  const int nsc_cap = single_split(ws_split_per_sm<1>(), &rpc);
+  const int nsc0 = single_split(ws_split_per_sm<0>(), &rpc0);
   wgrad_single<1><<<nsc_cap, kWsThreads, 0, st>>>(n->a[4], n->dy,
                                                   n->part, B, H, W, rpc, n->dil[5]);
   reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + 1, n->grads + kOff.w[5]);
@@ -1703,8 +1739,8 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
                      n->wait_limit, tm, use);
     std::swap(gcur, gnext);
   }
-  wgrad_single<0><<<nsc_cap, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc, n->dil[0]);
-  reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc_cap, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
+  wgrad_single<0><<<nsc0, kWsThreads, 0, st>>>(gcur, x, n->part, B, H, W, rpc0, n->dil[0]);
+  reduce_partials<<<(C * 9 + C + 31) / 32, 32 * kRedSlices, 0, st>>>(n->part, nsc0, C * 9 + C, C * 9 + C, n->grads + kOff.w[0]);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PX_OK : cnn_cuda(n, e, "network backward");
 }
