@@ -403,9 +403,10 @@ def bench_batched(px, torch, steps: int, warmup: int):
     whole = sum(v["count"] for v in d["classes"].values() if v["mode"] == "whole")
     return {"instances": 1024, "sweeps": BATCH_SWEEPS, "cells": cells[0] + cells[1],
             "fp64_cells": cells[0], "fp32_cells": cells[1], "ms": 1000 * t,
-            "GLUP_s": total / t / 1e9, "launches_per_step": 1,
+            "GLUP_s": total / t / 1e9, "launches_per_step": d.get("launches", 1),
             "whole_instances": whole, "banded_instances": 1024 - whole,
             "clusters": d["clusters"], "predicted_ms": d["predicted_ms"],
+            "launches": d.get("launches", 1), "side_by_side": d.get("side_by_side"),
             "plan_and_tune_s": plan_s,
             "fp64_bound_ms": 1000 * cells[0] * (BATCH_SWEEPS) * 6 / 0.555e12,
             "note": "FP64 instances are bound by the FP64 pipe (6 ops/update at 0.555e12/s)"}

@@ -354,7 +354,9 @@ __device__ void run_whole(const BInst& I, const BParams& p, unsigned char* smem,
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_k(BParams p) {
+// At most 64 registers a thread (two CTAs of 512 threads per SM), so that the
+// two launches of a mixed-precision plan can share every SM.
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_k(BParams p) {
   extern __shared__ __align__(16) unsigned char bsm[];
   __shared__ uint64_t red64[kBatchThreads / 32];
   __shared__ uint32_t red32[kBatchThreads / 32];
@@ -436,6 +438,16 @@ cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStrea
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, batch_k, p);
+}
+
+bool batch_coresident(size_t smem) {
+  if (batch_attr() != cudaSuccess) { cudaGetLastError(); return false; }
+  int k = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, batch_k, kBatchThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return k >= 2;
 }
 
 int batch_max_cluster_size() { return kMaxCluster; }

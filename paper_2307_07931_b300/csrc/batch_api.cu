@@ -28,9 +28,28 @@ std::string class_key(int dtype, int nx, int ny, int csize) {
   return b;
 }
 
-bool fits_whole(int nx, int ny, int dtype) {
-  return px::whole_bytes(nx, ny, dtype) <= px::batch_whole_smem();
+bool fits_whole(int nx, int ny, int dtype, size_t cap = 0) {
+  return px::whole_bytes(nx, ny, dtype) <= (cap ? cap : px::batch_whole_smem());
 }
+
+// Shared bytes of a configured class.
+size_t cfg_smem(const ClassCfg& k, int nx, int ny, int dtype) {
+  if (k.mode == px::MODE_WHOLE) return px::whole_bytes(nx, ny, dtype);
+  if (k.mode == px::MODE_BANDED_T) return px::banded_t_smem(dtype, k.tb);
+  return 0;
+}
+
+// Mixed-precision plans: the FP64 and the FP32 instances run as two launches
+// side by side, one CTA of each on every SM, so that the FP64-pipe-bound
+// sweeps and the memory-bound FP32 sweeps overlap on the same SMs. A CTA of
+// such a plan uses at most this much shared memory (two must fit an SM);
+// classes whose fastest mode needs more are tuned again under the cap (key
+// suffix "s").
+constexpr size_t kCoSmem = 100 * 1024;
+// Measured on B300 (1024-instance workload, 300 sweeps): FP64 launch alone
+// 231.5 ms, FP32 launch alone 66.9 ms, side by side 244.0 ms, so the shorter
+// launch adds about a fifth of its own time to the longer one.
+constexpr double kCoOverlap = 0.2;
 
 // Default rates per SM (cell updates / s) when a class was not measured: FP64
 // is bound by the FP64 pipe (about 0.555e12 DFMA/s over 148 SMs, 6 per
@@ -116,7 +135,13 @@ struct px_batch {
   int nclusters = 0;
   size_t smem = 0;
   px::BParams params{};
+  // a mixed-precision plan runs FP32 instances in a second launch beside the
+  // FP64 one (params2, nclusters2, smem2); nclusters2 == 0 otherwise
+  px::BParams params2{};
+  int nclusters2 = 0;
+  size_t smem2 = 0;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::string desc;
@@ -131,7 +156,7 @@ namespace {
 // stays in L2 and would make streaming modes look faster than they run in
 // the batch. Keeps the fastest rate per SM.
 px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double omega, int C,
-                     int clusters, ClassCfg* out) {
+                     int clusters, size_t smem_cap, ClassCfg* out) {
   const int64_t ld = nx;
   const size_t es = dtype == PX_F64 ? 8 : 4;
   const size_t fb = ((size_t)ld * ny * es + 255) / 256 * 256;
@@ -142,10 +167,11 @@ px_status tune_class(px_ctx* c, int dtype, int nx, int ny, int sweeps, double om
   px_status st = PX_OK;
   struct Cand { int mode, ry, tb; };
   std::vector<Cand> cands;
-  if (fits_whole(nx, ny, dtype)) cands.push_back({px::MODE_WHOLE, 0, 1});
+  if (fits_whole(nx, ny, dtype, smem_cap)) cands.push_back({px::MODE_WHOLE, 0, 1});
   for (int ry : {4, 8, 16}) cands.push_back({px::MODE_BANDED, ry, 1});
   if (dtype == PX_F32)
-    for (int tb : {4, 8}) cands.push_back({px::MODE_BANDED_T, 8, tb});
+    for (int tb : {4, 8})
+      if (px::banded_t_smem(dtype, tb) <= smem_cap) cands.push_back({px::MODE_BANDED_T, 8, tb});
   double best = -1;
   cudaError_t e = cudaMalloc(&mem, 4 * fb * copies);  // per copy: phi, rho, scratch, -c rho
   if (e == cudaSuccess) e = cudaMemset(mem, 0, 4 * fb * copies);
@@ -228,6 +254,7 @@ void destroy_batch(px_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->cap_stream2) cudaStreamDestroy(b->cap_stream2);
   if (b->inst_dev) cudaFree(b->inst_dev);
   if (b->inst_pinned) cudaFreeHost(b->inst_pinned);
   if (b->idx_dev) cudaFree(b->idx_dev);
@@ -284,18 +311,24 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   // tuned (or read from the cache) and scheduled; the plan keeps the one with
   // the smallest predicted makespan. The largest BANDED instances matter most
   // here: one of them runs on a single cluster, so small clusters can leave it
-  // as the critical path even when they cover more SMs.
+  // as the critical path even when they cover more SMs. A launch holds one
+  // CTA per SM at most, which leaves the second CTA slot of every SM to the
+  // other launch of a mixed-precision plan.
   std::vector<std::pair<int, int>> cands;  // (cluster size, resident clusters)
   for (int cs = px::batch_max_cluster_size(); cs >= 2; cs /= 2) {
     int m = 0;
     cudaError_t e = px::batch_max_clusters(&m, smem, cs);
     if (e != cudaSuccess) { cudaGetLastError(); continue; }
+    m = std::min(m, px::device_sm_count() / cs);
     if (m >= 1) cands.push_back({cs, m});
   }
   if (cands.empty()) {
     destroy_batch(b);
     return px::ctx_fail(c, PX_ECUDA, "no cluster of the batch kernel fits on this device");
   }
+  bool has64 = false, has32 = false;
+  for (int i = 0; i < n; ++i) (grids[i].dtype == PX_F64 ? has64 : has32) = true;
+  const bool mixed = has64 && has32 && px::batch_coresident(kCoSmem);
 
   // classes and their configuration, per candidate cluster size
   std::map<std::string, ClassCfg> cfg;
@@ -318,27 +351,52 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   std::map<std::string, ClassCfg> cached;
   load_cache(tune_cache, gpu, cached);
   int tuned_now = 0;
-  for (auto& kv : cfg) {
-    auto it = cached.find(kv.first);
+  auto tune_key = [&](const std::string& key, size_t cap, ClassCfg* out) -> px_status {
+    auto it = cached.find(key);
     if (it != cached.end()) {
-      kv.second = it->second;
+      *out = it->second;
+      return PX_OK;
+    }
+    if (!tune) return PX_OK;
+    int dt = key[1] == '6' ? PX_F64 : PX_F32;
+    int nx = 0, ny = 0, cs = 0;
+    sscanf(key.c_str() + 4, "%dx%d@c%d", &nx, &ny, &cs);
+    ClassCfg t;
+    int ncl_cs = 1;
+    for (auto& cand : cands)
+      if (cand.first == cs) ncl_cs = cand.second;
+    px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, cs,
+                             ncl_cs, cap, &t);
+    if (s != PX_OK) return s;
+    *out = t;
+    cached[key] = t;
+    ++tuned_now;
+    return PX_OK;
+  };
+  for (auto& kv : cfg) {
+    px_status s = tune_key(kv.first, px::batch_whole_smem(), &kv.second);
+    if (s != PX_OK) { destroy_batch(b); return s; }
+  }
+  // configurations under the co-resident cap (mixed plans only): the class's
+  // own where it fits, else tuned again without the modes that do not. A
+  // class over the cap with no measured configuration under it (no tuning,
+  // none cached) leaves the plan to a single launch.
+  std::map<std::string, ClassCfg> cocfg;
+  bool co_ok = mixed;
+  for (auto& kv : cfg) {
+    if (!co_ok) break;
+    int dt = kv.first[1] == '6' ? PX_F64 : PX_F32;
+    int nx = 0, ny = 0, cs = 0;
+    sscanf(kv.first.c_str() + 4, "%dx%d@c%d", &nx, &ny, &cs);
+    if (cfg_smem(kv.second, nx, ny, dt) <= kCoSmem) {
+      cocfg[kv.first] = kv.second;
       continue;
     }
-    if (tune) {
-      int dt = kv.first[1] == '6' ? PX_F64 : PX_F32;
-      int nx = 0, ny = 0, cs = 0;
-      sscanf(kv.first.c_str() + 4, "%dx%d@c%d", &nx, &ny, &cs);
-      ClassCfg t;
-      int ncl_cs = 1;
-      for (auto& cand : cands)
-        if (cand.first == cs) ncl_cs = cand.second;
-      px_status s = tune_class(c, dt, nx, ny, std::max(1, std::min(nsweeps, 40)), omega, cs,
-                               ncl_cs, &t);
-      if (s != PX_OK) { destroy_batch(b); return s; }
-      kv.second = t;
-      cached[kv.first] = t;
-      ++tuned_now;
-    }
+    ClassCfg d;
+    px_status s = tune_key(kv.first + "s", kCoSmem, &d);
+    if (s != PX_OK) { destroy_batch(b); return s; }
+    if (!d.tuned) co_ok = false;
+    cocfg[kv.first] = d;
   }
   if (tuned_now) save_cache(tune_cache, gpu, cached);
 
@@ -349,29 +407,30 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     double makespan = 0, total = 0;
     std::vector<std::vector<int>> cl_items, cta_items;
   };
-  auto schedule = [&](int C, int ncl_full) {
+  // instances `sub` on ncl_full clusters of C CTAs, configured by `conf`
+  auto schedule = [&](int C, int ncl_full, const std::vector<int>& sub,
+                      std::map<std::string, ClassCfg>& conf) {
     Sched S;
     S.C = C;
     // WHOLE classes decide the shared memory actually used (less is fine)
     size_t used = 0;
-    for (int i = 0; i < n; ++i) {
-      const ClassCfg& k = cfg[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
-      if (k.mode == px::MODE_WHOLE)
-        used = std::max(used, px::whole_bytes(grids[i].nx, grids[i].ny, grids[i].dtype));
-      if (k.mode == px::MODE_BANDED_T) used = std::max(used, px::banded_t_smem(grids[i].dtype, k.tb));
+    for (int i : sub) {
+      const ClassCfg& k = conf[class_key(grids[i].dtype, grids[i].nx, grids[i].ny, C)];
+      used = std::max(used, cfg_smem(k, grids[i].nx, grids[i].ny, grids[i].dtype));
     }
     S.smem = (used + 1023) / 1024 * 1024;
     S.ncl = ncl_full;
     int m = 0;
     if (px::batch_max_clusters(&m, S.smem, C) == cudaSuccess && m > S.ncl) S.ncl = m;
     cudaGetLastError();
+    S.ncl = std::min(S.ncl, std::max(1, px::device_sm_count() / C));
     std::vector<double> cl_load(S.ncl, 0.0), cta_load((size_t)S.ncl * C, 0.0);
     S.cl_items.assign(S.ncl, {});
     S.cta_items.assign((size_t)S.ncl * C, {});
     std::vector<std::pair<double, int>> banded, whole;
-    for (int i = 0; i < n; ++i) {
+    for (int i : sub) {
       const px_grid& g = grids[i];
-      const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny, C)];
+      const ClassCfg& k = conf[class_key(g.dtype, g.nx, g.ny, C)];
       const double work = (double)g.nx * g.ny * nsweeps / std::max(k.rate_per_sm, 1.0);
       if (k.mode != px::MODE_WHOLE) banded.push_back({work / C, i});
       else whole.push_back({work, i});
@@ -394,25 +453,50 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     for (double v : cta_load) S.total += v;
     return S;
   };
-  std::vector<Sched> scheds;
-  for (auto& cand : cands) scheds.push_back(schedule(cand.first, cand.second));
+  struct Plan {
+    Sched a, b;       // b: the FP32 launch of a mixed plan (b.ncl == 0 otherwise)
+    double predicted = 0;
+  };
+  std::vector<int> all(n), sub64, sub32;
+  for (int i = 0; i < n; ++i) {
+    all[i] = i;
+    (grids[i].dtype == PX_F64 ? sub64 : sub32).push_back(i);
+  }
+  std::vector<Plan> plans;
+  for (auto& cand : cands) {
+    Plan P;
+    P.a = schedule(cand.first, cand.second, all, cfg);
+    P.predicted = P.a.makespan;
+    plans.push_back(std::move(P));
+    if (co_ok) {
+      Plan Q;
+      Q.a = schedule(cand.first, cand.second, sub64, cocfg);
+      Q.b = schedule(cand.first, cand.second, sub32, cocfg);
+      const double hi = std::max(Q.a.makespan, Q.b.makespan), lo = std::min(Q.a.makespan, Q.b.makespan);
+      Q.predicted = hi + kCoOverlap * lo;
+      if (Q.a.smem <= kCoSmem && Q.b.smem <= kCoSmem) plans.push_back(std::move(Q));
+    }
+  }
   size_t pick = 0;
-  for (size_t k = 1; k < scheds.size(); ++k)
-    if (scheds[k].makespan < scheds[pick].makespan * (1 - 1e-9)) pick = k;
-  Sched& S = scheds[pick];
+  for (size_t k = 1; k < plans.size(); ++k)
+    if (plans[k].predicted < plans[pick].predicted * (1 - 1e-9)) pick = k;
+  Plan& PL = plans[pick];
+  const bool co = PL.b.ncl > 0;
+  std::map<std::string, ClassCfg>& used_cfg = co ? cocfg : cfg;
+  Sched& S = PL.a;
   const int C = S.C, ncl = S.ncl;
   smem = S.smem;
   b->nclusters = ncl;
   b->smem = smem;
-  std::vector<std::vector<int>>& cl_items = S.cl_items;
-  std::vector<std::vector<int>>& cta_items = S.cta_items;
+  b->nclusters2 = co ? PL.b.ncl : 0;
+  b->smem2 = co ? PL.b.smem : 0;
 
   size_t scratch_bytes = 0;
   std::vector<size_t> scr_off(n, 0), rhs_off(n, SIZE_MAX);
   b->inst.resize(n);
   for (int i = 0; i < n; ++i) {
     const px_grid& g = grids[i];
-    const ClassCfg& k = cfg[class_key(g.dtype, g.nx, g.ny, C)];
+    const ClassCfg& k = used_cfg[class_key(g.dtype, g.nx, g.ny, C)];
     px::BInst& I = b->inst[i];
     I = px::BInst{};
     I.nx = g.nx; I.ny = g.ny; I.ld = g.ld; I.dtype = g.dtype; I.mode = k.mode; I.ry = k.ry;
@@ -431,17 +515,26 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
       }
     }
   }
+  // index arrays of one launch: cl_off | cl_items | cta_off | cta_items
   std::vector<int> ix;
-  ix.push_back(0);
-  for (int k = 0; k < ncl; ++k) ix.push_back(ix.back() + (int)cl_items[k].size());
-  const size_t cl_items_at = ix.size();
-  for (int k = 0; k < ncl; ++k) ix.insert(ix.end(), cl_items[k].begin(), cl_items[k].end());
-  const size_t cta_off_at = ix.size();
-  ix.push_back(0);
-  for (int k = 0; k < ncl * C; ++k) ix.push_back(ix.back() + (int)cta_items[k].size());
-  const size_t cta_items_at = ix.size();
-  for (int k = 0; k < ncl * C; ++k) ix.insert(ix.end(), cta_items[k].begin(), cta_items[k].end());
-  ix.push_back(0);  // keep the arrays non-empty
+  struct Offs { size_t cl_off, cl_items, cta_off, cta_items; };
+  auto append = [&](const Sched& T) {
+    Offs o;
+    o.cl_off = ix.size();
+    ix.push_back(0);
+    for (int k = 0; k < T.ncl; ++k) ix.push_back(ix[o.cl_off + k] + (int)T.cl_items[k].size());
+    o.cl_items = ix.size();
+    for (int k = 0; k < T.ncl; ++k) ix.insert(ix.end(), T.cl_items[k].begin(), T.cl_items[k].end());
+    o.cta_off = ix.size();
+    ix.push_back(0);
+    for (int k = 0; k < T.ncl * T.C; ++k) ix.push_back(ix[o.cta_off + k] + (int)T.cta_items[k].size());
+    o.cta_items = ix.size();
+    for (int k = 0; k < T.ncl * T.C; ++k) ix.insert(ix.end(), T.cta_items[k].begin(), T.cta_items[k].end());
+    ix.push_back(0);  // keep the arrays non-empty
+    return o;
+  };
+  const Offs oa = append(S);
+  const Offs ob = co ? append(PL.b) : Offs{};
 
   cudaError_t e = cudaMalloc(&b->idx_dev, ix.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(b->idx_dev, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -457,23 +550,42 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
     if (b->inst[i].mode != px::MODE_WHOLE) b->inst[i].scratch = (char*)b->scratch + scr_off[i];
     if (rhs_off[i] != SIZE_MAX) b->inst[i].rhos = (char*)b->scratch + rhs_off[i];
   }
-  b->params.inst = b->inst_dev;
-  b->params.cl_off = b->idx_dev;
-  b->params.cl_items = b->idx_dev + cl_items_at;
-  b->params.cta_off = b->idx_dev + cta_off_at;
-  b->params.cta_items = b->idx_dev + cta_items_at;
-  b->params.nsweeps = nsweeps;
-  b->params.every = report_every;
-  b->params.csize = C;
+  auto set_params = [&](px::BParams& P, const Offs& o) {
+    P.inst = b->inst_dev;
+    P.cl_off = b->idx_dev + o.cl_off;
+    P.cl_items = b->idx_dev + o.cl_items;
+    P.cta_off = b->idx_dev + o.cta_off;
+    P.cta_items = b->idx_dev + o.cta_items;
+    P.nsweeps = nsweeps;
+    P.every = report_every;
+    P.csize = C;
+  };
+  set_params(b->params, oa);
+  if (co) set_params(b->params2, ob);
 
-  // The launch is captured once into a graph; runs replay it.
+  // The launch (or the two side-by-side launches) is captured once into a
+  // graph; runs replay it.
   e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && co) e = cudaStreamCreateWithFlags(&b->cap_stream2, cudaStreamNonBlocking);
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (e == cudaSuccess && co) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && co) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t el = px::batch_launch(b->params, ncl, smem, b->cap_stream);
+    cudaError_t el = cudaSuccess;
+    if (co) {
+      el = cudaEventRecord(fork, b->cap_stream);
+      if (el == cudaSuccess) el = cudaStreamWaitEvent(b->cap_stream2, fork, 0);
+    }
+    if (el == cudaSuccess) el = px::batch_launch(b->params, ncl, smem, b->cap_stream);
+    if (el == cudaSuccess && co) el = px::batch_launch(b->params2, b->nclusters2, b->smem2, b->cap_stream2);
+    if (el == cudaSuccess && co) el = cudaEventRecord(join, b->cap_stream2);
+    if (el == cudaSuccess && co) el = cudaStreamWaitEvent(b->cap_stream, join, 0);
     e = cudaStreamEndCapture(b->cap_stream, &b->graph);
     if (el != cudaSuccess) e = el;
   }
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -484,18 +596,23 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
 
   // description
   std::ostringstream os;
-  const double makespan = S.makespan, total = S.total;
   os << "{\"clusters\": " << ncl << ", \"cluster_size\": " << C << ", \"smem\": " << smem
-     << ", \"predicted_ms\": " << makespan * 1e3
-     << ", \"balance\": " << (makespan > 0 ? total / (makespan * ncl * C) : 1.0)
-     << ", \"candidates\": [";
-  for (size_t k = 0; k < scheds.size(); ++k)
-    os << (k ? ", " : "") << "{\"cluster_size\": " << scheds[k].C << ", \"clusters\": "
-       << scheds[k].ncl << ", \"predicted_ms\": " << scheds[k].makespan * 1e3 << "}";
+     << ", \"predicted_ms\": " << PL.predicted * 1e3
+     << ", \"balance\": " << (S.makespan > 0 ? S.total / (S.makespan * ncl * C) : 1.0)
+     << ", \"launches\": " << (co ? 2 : 1);
+  if (co)
+    os << ", \"side_by_side\": {\"fp64_ms\": " << S.makespan * 1e3 << ", \"fp32_ms\": "
+       << PL.b.makespan * 1e3 << ", \"fp32_clusters\": " << PL.b.ncl << ", \"fp32_smem\": "
+       << PL.b.smem << ", \"smem_cap\": " << kCoSmem << "}";
+  os << ", \"candidates\": [";
+  for (size_t k = 0; k < plans.size(); ++k)
+    os << (k ? ", " : "") << "{\"cluster_size\": " << plans[k].a.C << ", \"clusters\": "
+       << plans[k].a.ncl << ", \"launches\": " << (plans[k].b.ncl > 0 ? 2 : 1)
+       << ", \"predicted_ms\": " << plans[k].predicted * 1e3 << "}";
   os << "], \"classes\": {";
   const std::string suffix = "@c" + std::to_string(C);
   bool first = true;
-  for (auto& kv : cfg) {
+  for (auto& kv : used_cfg) {
     if (kv.first.size() < suffix.size() ||
         kv.first.compare(kv.first.size() - suffix.size(), suffix.size(), suffix) != 0)
       continue;

@@ -286,6 +286,8 @@ size_t whole_bytes(int nx, int ny, int dtype);
 cudaError_t batch_max_clusters(int* n, size_t smem, int csize);
 cudaError_t batch_launch(const BParams& p, int nclusters, size_t smem, cudaStream_t st);
 int batch_max_cluster_size();
+// Whether two CTAs of the batch kernel with `smem` dynamic shared bytes fit on one SM.
+bool batch_coresident(size_t smem);
 size_t batch_whole_smem();
 // Shared bytes of the tiles of a MODE_BANDED_T instance of dtype at depth tb.
 size_t banded_t_smem(int dtype, int tb);

@@ -185,7 +185,8 @@ def test_plan_picks_cluster_size_by_makespan(px):
     assert len(cands) >= 1
     best = min(c["predicted_ms"] for c in cands)
     assert abs(d["predicted_ms"] - best) <= 1e-9 * max(1.0, best)
-    chosen = [c for c in cands if c["cluster_size"] == d["cluster_size"]][0]
+    chosen = [c for c in cands if c["cluster_size"] == d["cluster_size"]
+              and c["launches"] == d["launches"]][0]
     assert chosen["predicted_ms"] == best
     if any(c["cluster_size"] > 2 for c in cands):
         assert d["cluster_size"] > 2, cands
@@ -240,3 +241,49 @@ def test_temporally_blocked_banded_mode(px, tmp_path, tb, nsweeps, every):
     for a, c in zip(results[1][0], results[2][0]):
         assert torch.equal(a, c)
     assert torch.equal(results[1][1], results[2][1])
+
+
+def test_mixed_plan_side_by_side_launches(px, tmp_path):
+    """A batch of FP64 and FP32 instances runs as two launches side by side
+    (one CTA of each on every SM: the FP64 sweeps are bound by the FP64 pipe,
+    the FP32 ones by memory): classes whose mode needs more shared memory
+    than the cap take their configuration under the cap (cache keys with the
+    suffix "s"), and every instance still matches the oracle, states and
+    reports, over two replays of the graph."""
+    # enough small instances of both precisions that each launch holds
+    # several per CTA (side by side then beats one launch in the planner's
+    # model), plus classes over the cap, banded ones and ragged shapes
+    specs = ([(64, 64, "f64")] * 296 + [(64, 64, "f32")] * 296 +
+             [(32, 32, "f32"), (160, 160, "f32"), (128, 128, "f32"), (96, 96, "f64"),
+              (48, 48, "f64"), (256, 256, "f32"), (256, 128, "f64"), (80, 48, "f32"),
+              (1024, 64, "f32"), (112, 112, "f64")])
+    whole_bytes = lambda nx, ny, dt: 2 * nx * ny * (8 if dt == "f64" else 4)
+    classes = {}
+    for (nx, ny, dt) in set(specs):
+        for cs in (2, 4, 8):
+            k = f"{dt}:{nx}x{ny}@c{cs}"
+            fits = whole_bytes(nx, ny, dt) <= 200 * 1024
+            classes[k] = {"mode": 0 if fits else 1, "ry": 8, "tb": 1, "rate_per_sm": 1e9}
+            classes[k + "s"] = {"mode": 0 if whole_bytes(nx, ny, dt) <= 100 * 1024 else 1,
+                                "ry": 8, "tb": 1, "rate_per_sm": 1e9}
+    cache = str(tmp_path / "co.json")
+    with open(cache, "w") as f:
+        json.dump({"gpu": torch.cuda.get_device_name(0), "classes": classes}, f)
+    nsweeps, every = 9, 2
+    b = px.Batch([px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+                  for nx, ny, dt in specs], nsweeps, OMEGA, every, tune_cache=cache, tune=False)
+    d = b.describe()
+    assert d["launches"] == 2, d
+    sbs = d["side_by_side"]
+    assert d["smem"] <= sbs["smem_cap"] and sbs["fp32_smem"] <= sbs["smem_cap"]
+    modes = {k.split("@")[0]: v["mode"] for k, v in d["classes"].items()}
+    assert modes["f32:160x160"] == "banded" and modes["f64:96x96"] == "banded"
+    assert modes["f32:32x32"] == "whole" and modes["f64:48x48"] == "whole"
+    nrep = (nsweeps + every - 1) // every
+    for rep in range(2):
+        phis, rhos, host = make_instances(specs, 31 + rep)
+        resid = torch.full((len(specs) * nrep,), -1.0, dtype=torch.float64, device="cuda")
+        b.run(phis, rhos, resid)
+        torch.cuda.synchronize()
+        check(specs, phis, host, resid, nsweeps, every)
+    b.close()
