@@ -129,9 +129,14 @@ px_status px_checked_faults(px_ctx* ctx, uint64_t* count, uint64_t* first);
  *                               arithmetic at every size.
  *  PX_OPT_RB_SWEEPS_PER_LAUNCH  red-black sweeps per launch of the FP32
  *                               register wavefront: 0 automatic (3), 1..4.
+ *  PX_OPT_BATCH_LAUNCHES        kernels in the graph of a batch plan made
+ *                               through ctx: 0 automatic (one persistent
+ *                               launch, or for batches mixing FP64 and FP32
+ *                               two side by side when that predicts less),
+ *                               1 always one persistent launch.
  * px_set_option returns PX_EINVAL for an unknown option or a value out of
  * range; it affects calls made through ctx afterwards. */
-enum { PX_OPT_FP32_FAMILY = 1, PX_OPT_RB_SWEEPS_PER_LAUNCH = 2 };
+enum { PX_OPT_FP32_FAMILY = 1, PX_OPT_RB_SWEEPS_PER_LAUNCH = 2, PX_OPT_BATCH_LAUNCHES = 3 };
 px_status px_set_option(px_ctx* ctx, int option, int value);
 px_status px_get_option(const px_ctx* ctx, int option, int* value);
 
@@ -334,18 +339,26 @@ px_status px_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho,
 /* ----------------------------------------------------------------------------
  * Batched relaxation: many independent periodic instances of uneven sizes and
  * mixed dtypes, nsweeps fused sweeps each (the same sweep as px_relax_n), in
- * ONE persistent kernel launch replayed from a CUDA graph. Instances are
- * independent problems, so the batch needs no exchange between them.
+ * persistent kernel launches replayed from one CUDA graph (one graph launch
+ * per run). Instances are independent problems, so the batch needs no
+ * exchange between them.
  *
  * Execution per size class (dtype, nx, ny), chosen by an autotuner:
- *  WHOLE   one CTA keeps the instance in shared memory for all sweeps
- *          (fits when 2 * nx * ny * element size <= 200 KiB);
- *  BANDED  a cluster of 8 CTAs shares the instance, one band of rows each,
- *          sweeping from global memory with a cluster barrier per sweep.
- * The tuner times both modes (and the rows per warp task of BANDED) on one
- * representative instance per class and keeps the fastest rate per SM; the
- * results are cached as JSON keyed by GPU name. The schedule assigns
- * instances longest-first to the least loaded cluster / CTA.
+ *  WHOLE     one CTA keeps the instance in shared memory for all sweeps
+ *            (fits when 2 * nx * ny * element size <= 200 KiB);
+ *  BANDED    a cluster of 2, 4 or 8 CTAs shares the instance, one band of
+ *            rows each, sweeping from global memory with a cluster barrier
+ *            per sweep;
+ *  BANDED_T  (FP32) BANDED with tb = 4 or 8 sweeps per cluster barrier in
+ *            shared-memory tiles with a tb-cell halo.
+ * The tuner times the modes (and the rows per warp task) with one copy per
+ * cluster running at once and keeps the fastest rate per SM; the results are
+ * cached as JSON keyed by GPU name. The schedule assigns instances
+ * longest-first to the least loaded cluster / CTA. The graph holds ONE
+ * persistent launch, or, for a batch mixing FP64 and FP32 instances when
+ * that predicts less, two launched side by side (FP64 instances in one, FP32
+ * in the other, one CTA of each per SM, at most 100 KiB of shared memory a
+ * CTA); PX_OPT_BATCH_LAUNCHES = 1 on the context keeps one launch.
  *
  * px_batch_plan   grids[n]: layouts (unghosted; nx, ld multiples of 4 for FP32,
  *                 2 for FP64; PX_EUNSUPPORTED otherwise). nsweeps, omega,
@@ -361,7 +374,7 @@ px_status px_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho,
  *                 zero-filled by the call. Waits for the plan's previous run,
  *                 then enqueues on `stream` and returns.
  * px_batch_describe  JSON text of the plan (classes, modes, rates, clusters,
- *                 predicted time); valid until px_batch_destroy.
+ *                 launches, predicted time); valid until px_batch_destroy.
  * px_batch_destroy   synchronises the device and frees the plan.
  */
 typedef struct px_batch px_batch;

@@ -295,6 +295,10 @@ px_status px_set_option(px_ctx* c, int option, int value) {
         return fail(c, PX_EINVAL, "red-black sweeps per launch %d not in 0..4", value);
       c->opt_rb_sweeps = value;
       return PX_OK;
+    case PX_OPT_BATCH_LAUNCHES:
+      if (value < 0 || value > 1) return fail(c, PX_EINVAL, "batch launches option %d not in 0..1", value);
+      c->opt_batch_launches = value;
+      return PX_OK;
   }
   return fail(c, PX_EINVAL, "unknown option %d", option);
 }
@@ -304,6 +308,7 @@ px_status px_get_option(const px_ctx* c, int option, int* value) {
   switch (option) {
     case PX_OPT_FP32_FAMILY: *value = c->opt_fp32_family; return PX_OK;
     case PX_OPT_RB_SWEEPS_PER_LAUNCH: *value = c->opt_rb_sweeps; return PX_OK;
+    case PX_OPT_BATCH_LAUNCHES: *value = c->opt_batch_launches; return PX_OK;
   }
   return PX_EINVAL;
 }

@@ -328,7 +328,7 @@ px_status px_batch_plan(px_ctx* c, int n, const px_grid* grids, int nsweeps, dou
   }
   bool has64 = false, has32 = false;
   for (int i = 0; i < n; ++i) (grids[i].dtype == PX_F64 ? has64 : has32) = true;
-  const bool mixed = has64 && has32 && px::batch_coresident(kCoSmem);
+  const bool mixed = has64 && has32 && c->opt_batch_launches == 0 && px::batch_coresident(kCoSmem);
 
   // classes and their configuration, per candidate cluster size
   std::map<std::string, ClassCfg> cfg;

@@ -235,6 +235,7 @@ struct px_ctx {
   double* ewave = nullptr;   // Euler: max wave speeds of the current and next state
   int opt_fp32_family = 0;   // PX_OPT_FP32_FAMILY (0 = automatic)
   int opt_rb_sweeps = 0;     // PX_OPT_RB_SWEEPS_PER_LAUNCH (0 = automatic)
+  int opt_batch_launches = 0;  // PX_OPT_BATCH_LAUNCHES (0 = automatic, 1 = one launch)
   std::string err;
 };
 

@@ -287,3 +287,27 @@ def test_mixed_plan_side_by_side_launches(px, tmp_path):
         torch.cuda.synchronize()
         check(specs, phis, host, resid, nsweeps, every)
     b.close()
+    # PX_OPT_BATCH_LAUNCHES = 1 keeps the same batch in one persistent launch,
+    # with the same states and reports bit for bit (the per-instance sweeps
+    # do not depend on the launch that runs them; configurations under the
+    # cap are pinned for both plans by the cache)
+    ctx = px.Context(torch.cuda.current_device())
+    try:
+        ctx.set_option(px.PX_OPT_BATCH_LAUNCHES, 1)
+        assert ctx.get_option(px.PX_OPT_BATCH_LAUNCHES) == 1
+        b1 = px.Batch([px.Grid(nx, ny, nx, 0, px.PX_F64 if dt == "f64" else px.PX_F32, 1.0 / nx)
+                       for nx, ny, dt in specs], nsweeps, OMEGA, every, tune_cache=cache,
+                      tune=False, ctx=ctx)
+        assert b1.describe()["launches"] == 1
+        phis2, rhos2, _ = make_instances(specs, 32)
+        resid2 = torch.zeros_like(resid)
+        b1.run(phis2, rhos2, resid2)
+        torch.cuda.synchronize()
+        b1.close()
+        # the last two-launch run above used seed 32 as well
+        for i, (nx, ny, dt) in enumerate(specs):
+            if whole_bytes(nx, ny, dt) <= 100 * 1024:  # same mode in both plans
+                assert torch.equal(phis[i], phis2[i]), (i, nx, ny, dt)
+        assert torch.isfinite(resid2).all()
+    finally:
+        ctx.close()
