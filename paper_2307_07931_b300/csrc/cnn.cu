@@ -732,35 +732,68 @@ wgrad32_umma(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
 
 // Weight gradient of a unit-offset 32 -> 32 layer (dilation 1, or a dilated
 // layer over relabelled activations, whose input and dz share positions):
-// the same sums as wgrad32_umma with the nine tap tiles replaced by three
-// column-offset patches. A 2 x 64-pixel tile (K = 128 pixels) stages, for
-// dx = 0..2, the 4-row patch of rows y0 - 1 .. y0 + 2 at columns x0 + dx - 1,
-// and the dz tile, in the conv operands' [half][chunk][row][32 px][8 ch]
-// layout (512-byte half-rows, one box of the tensor memory accelerator per
-// half that lies inside the image, per-pixel copies for halves that wrap).
-// MN-major A of the block for dx: M = (chunk c, dy) for dy = 0..3, whose core
-// matrices sit at (4 c + dy) x 512 B: one descriptor (stride byte offset 512)
-// covers all three taps (dy, dx) of the patch; the fourth dy reads one row
-// past the patch (the next buffer in shared memory) and its rows of D are
-// dropped. K-step ks (16 pixels) of output row ks / 4 starts at that row's
-// half-row offset. A fourth block multiplies a tile of ones: db. D of block
-// dx, TMEM lane 32 w + l: channel 8 w + l % 8, tap (l / 8, dx).
+// the same sums as wgrad32_umma from one staged patch per half. A 2 x 64-pixel
+// tile (K = 128 pixels) stages, per 32-pixel half, the rows y0 - 1 .. y0 + 2
+// at columns x0 + 32 h - 1 .. x0 + 32 h + 32 (one halo pixel per side), as
+// [chunk][row][34 px][8 ch] with 544-byte rows: one box of the tensor memory
+// accelerator (32-bit elements, so that a 34-pixel row is one box row) where
+// the half and its halo lie inside the image, per-pixel copies where they
+// wrap. The dz tile is staged as before ([half][chunk][row][32 px][8 ch]).
+// In this MN-major A operand (M = channels, K = pixels) a core matrix is
+// 8 pixels x 16 bytes, contiguous, and the next 8 pixels follow 128 bytes on,
+// so the column offset dx = 0..2 of a tap is a start address 16 dx bytes on:
+// the three column offsets share the patch. M = (chunk c, dy) for dy = 0..3,
+// core matrices at (4c + dy) x 544 B: one descriptor (stride byte offset 544)
+// covers the three taps (dy, dx) of a column offset; the fourth dy reads one
+// row past the patch (inside the buffer) and its rows of D are dropped. A
+// fourth block multiplies a tile of ones: db. D of block dx, TMEM lane
+// 32 w + l: channel 8 w + l % 8, tap (l / 8, dx).
 constexpr int kWuRows = 2;                          // output rows per tile (K = 128 pixels)
 constexpr int kWuPRows = kWuRows + 2;               // patch rows
-constexpr uint32_t kWuPChunk = kWuPRows * kHRow;    // 2 KB
-constexpr uint32_t kWuPHalf = 4 * kWuPChunk;        // 8 KB
-constexpr uint32_t kWuPatch = 2 * kWuPHalf;         // 16 KB
+constexpr int kWuHW = kHW + 2;                      // 34: a half-row and its two halo pixels
+constexpr uint32_t kWuHRow = kWuHW * 16;            // 544 B
+constexpr uint32_t kWuPChunk = kWuPRows * kWuHRow;  // 2176 B
+constexpr uint32_t kWuPHalf = 4 * kWuPChunk;        // 8704 B (a multiple of 128)
+constexpr uint32_t kWuPatch = 2 * kWuPHalf;         // 17408 B
 constexpr uint32_t kWuZChunk = kWuRows * kHRow;     // 1 KB
 constexpr uint32_t kWuZHalf = 4 * kWuZChunk;        // 4 KB
-constexpr uint32_t kWuZ = 3 * kWuPatch;             // dz tile offset (after the patches)
+constexpr uint32_t kWuZ = kWuPatch;                 // dz tile offset (after the patch)
 constexpr uint32_t kWuOnes = kWuZ + 2 * kWuZHalf;   // ones tile offset (4 KB)
 constexpr uint32_t kWuBars = kWuOnes + 4096;        // barriers and flags (64 B)
-constexpr size_t kWuSmem = kWuBars + 64;            // 61.5 KB: three CTAs per SM
-// the last patch's dropped fourth dy reads at most up to here
-static_assert(2 * kWuPatch + kWuPHalf + kHRow + 16 * 16 + 15 * kHRow + 2 * 128 <= kWuBars,
+constexpr size_t kWuSmem = kWuBars + 64;            // 29.1 KB
+constexpr int kWuCtasPerSm = 4;                     // 4 x 128 TMEM columns per SM
+static_assert(kWuPHalf % 128 == 0 && kWuZ % 128 == 0 && kWuOnes % 128 == 0,
+              "box destinations and core matrices on 128-byte boundaries");
+// the second half's dropped fourth dy reads at most up to here
+static_assert(kWuPHalf + 15 * kWuHRow + 2 * 16 + kWuHRow + 16 * 16 <= kWuBars,
               "the dropped fourth dy stays inside the buffer");
 
-__global__ void __launch_bounds__(kConvThreads, 3)
+// Per-pixel copies of one halo-padded patch half (rows y0 - 1 .., columns
+// x0 - 1 ..), periodic wrap, into [chunk][row][34 px][8 ch].
+__device__ __forceinline__ void load_patch_half(unsigned char* dst, const __nv_bfloat16* act,
+                                                int b, int y0, int x0, int H, int W, int pid,
+                                                int np) {
+  constexpr int kN = kWuPRows * kWuHW * 4;
+  for (int q = pid; q < kN; q += np) {
+    const int chunk = q / (kWuPRows * kWuHW), pix = q - chunk * (kWuPRows * kWuHW);
+    const int r = pix / kWuHW, c = pix - r * kWuHW;
+    const int gy = wrap1(y0 + r - 1, H), gx = wrap1(x0 + c - 1, W);
+    cp16(dst + chunk * kWuPChunk + pix * 16, act + act_off(b, gy, gx, chunk, H, W));
+  }
+}
+
+// One halo-padded patch half as a box: 32-bit elements, x = first pixel x 4.
+__device__ __forceinline__ void tma_load_patch_half(uint32_t dst, const CUtensorMap* map, int px,
+                                                    int y, int b, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(px * 4), "r"(y), "r"(0), "r"(b),
+        "r"(bar)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kConvThreads, kWuCtasPerSm)
 wgrad32_unit(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restrict__ dz,
              float* __restrict__ part, int H, int W, int tiles_x, int tiles_y, int ntiles,
              unsigned* __restrict__ fault, uint32_t wait_limit,
@@ -804,38 +837,34 @@ wgrad32_unit(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
     const int tx = tile % tiles_x, ty = (tile / tiles_x) % tiles_y, b = tile / (tiles_x * tiles_y);
     const int y0 = ty * kWuRows, x0 = tx * TW;
     const bool ok = *s_ok != 0;
-    // which halves come as boxes: bit 2 dx + h for the patches, bit 6 + h for dz
+    // which halves come as boxes: bit h for the patch, bit 2 + h for dz
     uint32_t boxes = 0;
-    const int ysp = wrapn(y0 - 1, H);
     if (use_tma && ok) {
-      for (int dx = 0; dx < 3; ++dx)
-        for (int h = 0; h < 2; ++h) {
-          const int xs = wrapn(x0 + kHW * h + dx - 1, W);
-          if (ysp + kWuPRows <= H && xs + kHW <= W) boxes |= 1u << (2 * dx + h);
-        }
-      boxes |= 3u << 6;  // the dz tile never wraps (y0 + 2 <= H, x0 + 64 <= W)
+      const bool rows_in = y0 >= 1 && y0 - 1 + kWuPRows <= H;
+      for (int h = 0; h < 2; ++h) {
+        const int xs = x0 + kHW * h - 1;
+        if (rows_in && xs >= 0 && xs + kWuHW <= W) boxes |= 1u << h;
+      }
+      boxes |= 3u << 2;  // the dz tile never wraps (y0 + 2 <= H, x0 + 64 <= W)
     }
     if (tid == 0 && boxes) {
-      const uint32_t bytes = (uint32_t)__popc(boxes & 63u) * (4 * kWuPRows * kHRow) +
-                             (uint32_t)__popc(boxes >> 6) * (4 * kWuRows * kHRow);
+      const uint32_t bytes = (uint32_t)__popc(boxes & 3u) * kWuPHalf +
+                             (uint32_t)__popc(boxes >> 2) * kWuZHalf;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                    ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-      for (int dx = 0; dx < 3; ++dx)
-        for (int h = 0; h < 2; ++h)
-          if (boxes & (1u << (2 * dx + h)))
-            tma_load_half(base + dx * kWuPatch + h * kWuPHalf, &tmap_in,
-                          wrapn(x0 + kHW * h + dx - 1, W), ysp, b, smem_u32(bar));
+      for (int h = 0; h < 2; ++h)
+        if (boxes & (1u << h))
+          tma_load_patch_half(base + h * kWuPHalf, &tmap_in, x0 + kHW * h - 1, y0 - 1, b,
+                              smem_u32(bar));
       for (int h = 0; h < 2; ++h)
         tma_load_half(base + kWuZ + h * kWuZHalf, &tmap_dz, x0 + kHW * h, y0, b, smem_u32(bar));
     }
     if (ok) {
-      for (int dx = 0; dx < 3; ++dx)
-        for (int h = 0; h < 2; ++h)
-          if (!(boxes & (1u << (2 * dx + h))))
-            load_half_cm_p<kWuPRows>(wuu + dx * kWuPatch + h * kWuPHalf, in, b, y0, x0 + kHW * h,
-                                     -1, dx - 1, H, W, tid, blockDim.x);
       for (int h = 0; h < 2; ++h)
-        if (!(boxes & (1u << (6 + h))))
+        if (!(boxes & (1u << h)))
+          load_patch_half(wuu + h * kWuPHalf, in, b, y0, x0 + kHW * h, H, W, tid, blockDim.x);
+      for (int h = 0; h < 2; ++h)
+        if (!(boxes & (1u << (2 + h))))
           load_half_cm_p<kWuRows>(wuu + kWuZ + h * kWuZHalf, dz, b, y0, x0 + kHW * h, 0, 0, H, W,
                                   tid, blockDim.x);
     }
@@ -855,12 +884,15 @@ wgrad32_unit(const __nv_bfloat16* __restrict__ in, const __nv_bfloat16* __restri
         for (int blk = 0; blk < 4; ++blk) {
 #pragma unroll
           for (int ks = 0; ks < (kWuRows * TW) / 16; ++ks) {
-            // output row ro, pixels px0 .. px0 + 15: half px0 / 32 of the tile
+            // output row ro, pixels px0 .. px0 + 15: half px0 / 32 of the tile;
+            // in the patch, output pixel p of a half sits at column p + 1, so
+            // column offset dx - 1 reads from column p + dx
             const int ro = ks >> 2, px0 = (ks & 3) * 16;
-            const uint32_t koff = ro * kHRow + (px0 % kHW) * 16, half = px0 / kHW;
+            const uint32_t half = px0 / kHW;
             const uint64_t ad = blk < 3
-                ? umma_desc(base + blk * kWuPatch + half * kWuPHalf + koff, 128, kHRow)
+                ? umma_desc(base + half * kWuPHalf + ro * kWuHRow + ((px0 % kHW) + blk) * 16, 128, kWuHRow)
                 : umma_desc(base + kWuOnes, 128, 256);
+            const uint32_t koff = ro * kHRow + (px0 % kHW) * 16;
             const uint64_t bd = umma_desc(base + kWuZ + half * kWuZHalf + koff, 128, kWuZChunk);
             asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
@@ -1560,6 +1592,23 @@ bool act_tensor_map(CUtensorMap* m, const __nv_bfloat16* act, int B, int H, int 
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same activations seen as 32-bit elements (two channels each), with a
+// box of kWuHW pixels x R rows x 4 chunks: a halo-padded patch half of the
+// weight gradient, 544-byte box rows.
+bool act_tensor_map_halo(CUtensorMap* m, const __nv_bfloat16* act, int B, int H, int W, int R) {
+  std::memset(m, 0, sizeof *m);
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || ((uintptr_t)act & 15u) || W < kWuHW) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)W * 4, (cuuint64_t)H, 4, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16,
+                                 (cuuint64_t)W * H * 64};
+  const cuuint32_t box[4] = {(cuuint32_t)kWuHW * 4, (cuuint32_t)R, 4, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<__nv_bfloat16*>(act), dims,
+             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 px_status set_conv_attrs() {
   static bool done_by_dev[64] = {};
   bool& done = done_by_dev[px::dev_index()];
@@ -1715,9 +1764,9 @@ px_status grads(px_cnn* n, const float* x, const float* t, int B, int H, int W, 
     int nparts = wg_ctas;
     if (P.unit[l]) {
       alignas(64) CUtensorMap tmi, tmz;
-      const int use = n->use_tma && act_tensor_map(&tmi, n->a[l - 1], B, H, W, kWuPRows) &&
+      const int use = n->use_tma && act_tensor_map_halo(&tmi, n->a[l - 1], B, H, W, kWuPRows) &&
                       act_tensor_map(&tmz, gcur, B, H, W, kWuRows);
-      nparts = std::min(wg_tiles, 3 * px::device_sm_count());
+      nparts = std::min(wg_tiles, kWuCtasPerSm * px::device_sm_count());
       wgrad32_unit<<<nparts, kConvThreads, kWuSmem, st>>>(
           n->a[l - 1], gcur, n->part, H, W, tiles_x, H / kWuRows, wg_tiles, conv_fault_ptr(),
           n->wait_limit, tmi, tmz, use);
