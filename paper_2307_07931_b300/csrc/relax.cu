@@ -814,6 +814,9 @@ template <int TB, bool kRB> __host__ __device__ constexpr int r_warps() {
   return (kRB ? TB >= 8 : TB >= 5) ? 12 : 8;
 }
 constexpr int kRWarpFloats = (kRPhiRing + kRRhoRing) * kRStrip;
+// Report pattern: kRepRun reads the per-stage flags, kRepNone reports nothing
+// (known at compile time: fewer live registers than the flags).
+constexpr int kRepRun = 0, kRepNone = 1;
 template <int TB, bool kRB> constexpr size_t r_smem() {
   return (size_t)r_warps<TB, kRB>() * kRWarpFloats * sizeof(float);
 }
@@ -862,7 +865,7 @@ struct R2Task {
   int y0, lim, lmax;
 };
 
-template <int TB, int P, bool kEdge, bool kRB, bool kPack>
+template <int TB, int P, bool kEdge, bool kRB, bool kPack, int kRep>
 __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
                                        const float* __restrict__ rho, float* __restrict__ out,
                                        float* ring, int nx, int ny, int64_t ld, int gx, bool own,
@@ -926,7 +929,7 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
         q0[x] = Q0.x; q0[x + 1] = Q0.y; q1[x] = Q1.x; q1[x + 1] = Q1.y;
         o0[x] = O0.x; o0[x + 1] = O0.y; o1[x] = O1.x; o1[x + 1] = O1.y;
       }
-    } else if constexpr (!kRB && TB < 8) {
+    } else if constexpr (!kRB && (TB < 8 || kRep != kRepRun)) {
       // Tap sums per cell (scalar: every cell an independent chain), then the
       // residual and the update on packed pairs of neighbouring cells of a
       // row, which already sit in aligned register pairs. With the signs
@@ -935,7 +938,8 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
       // those of the scalar form and |q'| = |q| for the residual. Measured at
       // 16384^2 with a report every sweep: depth 4 1844 against 1789 GLUP/s,
       // depth 6 2405 against 2339; at depth 8 its extra live registers spill
-      // (2478 against 2570), so depth 8 keeps the scalar form.
+      // (2478 against 2570), so depth 8 takes it only with the report pattern
+      // fixed at compile time (no per-stage flags live).
       const float2 nih2 = make_float2(-k.ih2, -k.ih2), nc = make_float2(-k.c, -k.c);
 #pragma unroll
       for (int x = 0; x < 4; x += 2) {
@@ -981,7 +985,8 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
     // computed row is exact because stage t reads rows up to r0 + 1 only).
     // Exact values of rows outside the task are residuals of real cells, so
     // including them leaves the max unchanged.
-    if (due[t - 1]) {
+    const bool rep_t = kRep == kRepNone ? false : due[t - 1];
+    if (rep_t) {
       if (!kEdge || r0 >= 2 * t) {
         S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q0[0], q0[1]);
         S.mx[t - 1] = max3_nan_abs(S.mx[t - 1], q0[2], q0[3]);
@@ -1063,7 +1068,7 @@ __device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips,
   return false;
 }
 
-template <int TB, bool kRB, bool kPack>
+template <int TB, bool kRB, bool kPack, int kRep>
 __global__ void __launch_bounds__(r_warps<TB, kRB>() * 32)
 relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
             int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
@@ -1140,16 +1145,16 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
 #pragma unroll 1
     for (; r0 < kPro; r0 += 4) {
       if (!ready(r0)) goto task_done;
-      rstep2<TB, 0, true, kRB, kPack>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, true, kRB, kPack, kRep>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) goto task_done;
-      rstep2<TB, 1, true, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, true, kRB, kPack, kRep>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
     }
 #pragma unroll 1
     for (;; r0 += 4) {
       if (!ready(r0)) break;
-      rstep2<TB, 0, false, kRB, kPack>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, false, kRB, kPack, kRep>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
       if (!ready(r0 + 2)) break;
-      rstep2<TB, 1, false, kRB, kPack>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, false, kRB, kPack, kRep>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
     }
   task_done:
     cp_wait<0>();  // the next task's prologue reuses the ring slots
@@ -1165,21 +1170,42 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
   }
 }
 
+template <int TB, bool kRB, bool kPack, int kRep>
+cudaError_t reg2_occupancy(int& occ) {
+  static int occ_by_dev[64] = {};
+  int& o = occ_by_dev[dev_index()];
+  if (o == 0) {
+    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB, kPack, kRep>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, relaxR2_f32<TB, kRB, kPack, kRep>,
+                                                      r_warps<TB, kRB>() * 32, r_smem<TB, kRB>());
+    if (e != cudaSuccess) return e;
+    if (o < 1) return cudaErrorInvalidConfiguration;
+  }
+  occ = o;
+  return cudaSuccess;
+}
+
 template <int TB, bool kRB = false, bool kPack = false>
 cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
                           cudaStream_t st) {
-  static int occ_by_dev[64] = {};
-  int& occ = occ_by_dev[dev_index()];
-  if (occ == 0) {
-    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB, kPack>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, relaxR2_f32<TB, kRB, kPack>,
-                                                      r_warps<TB, kRB>() * 32, r_smem<TB, kRB>());
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
+  // Jacobi depth 8 without reports: no per-stage flags live, which leaves the
+  // packed residual and update room without spills (2828 against 2673 GLUP/s
+  // at 16384^2). With every stage reported the compile-time pattern measured
+  // no faster than the flags (2559 packed, 2550 scalar, against 2571), so a
+  // reporting launch keeps them.
+  int kind = kRepRun;
+  if (!kRB && !kPack && TB == 8) {
+    bool any = false;
+    for (int t = 0; t < TB; ++t) any = any || rep.due(t);
+    kind = any ? kRepRun : kRepNone;
   }
+  int occ = 0;
+  cudaError_t e0 = kind == kRepNone ? reg2_occupancy<TB, kRB, kPack, kRepNone>(occ)
+                                    : reg2_occupancy<TB, kRB, kPack, kRepRun>(occ);
+  if (e0 != cudaSuccess) return e0;
   const int nstrips = (f.nx + r_owned<TB>() - 1) / r_owned<TB>();
   const int64_t resident = (int64_t)occ * device_sm_count();
   const int64_t warps = resident * r_warps<TB, kRB>();
@@ -1198,8 +1224,15 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   const int64_t tasks = (int64_t)nstrips * nseg;
   const int blocks = (int)std::max<int64_t>(
       1, std::min<int64_t>((tasks + r_warps<TB, kRB>() - 1) / r_warps<TB, kRB>(), resident));
-  relaxR2_f32<TB, kRB, kPack><<<blocks, r_warps<TB, kRB>() * 32, r_smem<TB, kRB>(), st>>>(src, dst, rho, f.nx, f.ny, f.ld, (int)H,
-                                                        nstrips, nseg, k, rep, dyn ? sched : nullptr);
+  const dim3 grid(blocks), cta(r_warps<TB, kRB>() * 32);
+  const size_t smem = r_smem<TB, kRB>();
+  unsigned long long* const sc = dyn ? sched : nullptr;
+  if (kind == kRepNone)
+    relaxR2_f32<TB, kRB, kPack, kRepNone><<<grid, cta, smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
+                                                                   (int)H, nstrips, nseg, k, rep, sc);
+  else
+    relaxR2_f32<TB, kRB, kPack, kRepRun><<<grid, cta, smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
+                                                                  (int)H, nstrips, nseg, k, rep, sc);
   return cudaGetLastError();
 }
 
