@@ -38,7 +38,7 @@ ALGO_BYTES = {"f32": 12, "f64": 24}  # read phi + read rho + write phi', per cel
 # DRAM bytes per cell per launch from one ncu capture of the kernel as it stands
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of two 16384^2 launches, / cells).
 MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (2226466688 + 1045071360) / 16384**2,
-                             ("f32", 8): (2213740032 + 1046627712) / 16384**2}
+                             ("f32", 8): (2214730752 + 1046437632) / 16384**2}
 
 
 # red-black SOR: FP32 runs three sweeps (six colour stages) per launch of the
