@@ -118,11 +118,14 @@ def test_batch_rejects_unsupported_layouts(px):
     assert ei.value.status == px.PX_EUNSUPPORTED
 
 
-def test_batched_workload_full_size(px):
+@pytest.mark.parametrize("tuned", [False, True])
+def test_batched_workload_full_size(px, tmp_path, tuned):
     """1024 instances, N = 16 j (32..1024) log-uniform, FP64/FP32 by coin,
-    8 modes each, 300 sweeps, one persistent launch. Every instance's state-0
-    report is max|rho| exactly; a sample of instances (the largest of each
-    dtype and small ones) is checked against the oracle."""
+    8 modes each, 300 sweeps. Untuned (default rates, no configuration under
+    the shared-memory cap): one persistent launch; tuned (as the benchmark
+    plans it): the FP64 and FP32 launches side by side. Every instance's
+    state-0 report is max|rho| exactly; a sample of instances (the largest of
+    each dtype and small ones) is checked against the oracle."""
     ns, dts = synth.batch_sizes(1024)
     specs, phis, rhos, hostr = [], [], [], []
     for i, (n, dt) in enumerate(zip(ns, dts)):
@@ -136,7 +139,9 @@ def test_batched_workload_full_size(px):
         hostr.append(rho if dt == 0 else rho.astype(np.float32).astype(np.float64))
     grids = [px.Grid(n, n, n, 0, px.PX_F64 if d == "f64" else px.PX_F32, 1.0 / n)
              for n, _, d in specs]
-    b = px.Batch(grids, 300, OMEGA, 100)
+    b = px.Batch(grids, 300, OMEGA, 100, tune_cache=str(tmp_path / "t.json") if tuned else None,
+                 tune=tuned)
+    assert b.describe()["launches"] == (2 if tuned else 1)
     resid = torch.zeros(1024 * 3, dtype=torch.float64, device="cuda")
     b.run(phis, rhos, resid)
     torch.cuda.synchronize()
