@@ -50,10 +50,19 @@ __device__ __forceinline__ int wrapn(int i, int n) {
 // Non-negative floats / doubles (and +NaN) order like their bit patterns read
 // as unsigned integers, so a max-norm reduces with integer max.
 // |v| as bits by clearing the sign bit on the integer pipe (keeps the FP64 pipe,
-// the bound of the FP64 sweep, free of the residual's absolute value).
-__device__ __forceinline__ uint32_t absbits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+// the bound of the FP64 sweep, free of the residual's absolute value). The mask
+// is inline PTX: written in C++ the compiler recognises it as a floating-point
+// absolute value, and for doubles that costs one FP64-pipe operation per cell
+// (measured: 4 DADD + 3 DFMA per reported cell update instead of 3 + 3).
+__device__ __forceinline__ uint32_t absbits(float v) {
+  uint32_t b;
+  asm("and.b32 %0, %1, 0x7fffffff;" : "=r"(b) : "r"(__float_as_uint(v)));
+  return b;
+}
 __device__ __forceinline__ uint64_t absbits(double v) {
-  return (uint64_t)__double_as_longlong(v) & 0x7fffffffffffffffull;
+  uint64_t b;
+  asm("and.b64 %0, %1, 0x7fffffffffffffff;" : "=l"(b) : "l"(__double_as_longlong(v)));
+  return b;
 }
 __device__ __forceinline__ uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
 __device__ __forceinline__ uint64_t umax(uint64_t a, uint64_t b) { return a > b ? a : b; }
