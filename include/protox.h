@@ -134,9 +134,18 @@ px_status px_checked_faults(px_ctx* ctx, uint64_t* count, uint64_t* first);
  *                               launch, or for batches mixing FP64 and FP32
  *                               two side by side when that predicts less),
  *                               1 always one persistent launch.
+ *  PX_OPT_RB_FP64_PASSES        launches per FP64 red-black sweep on 16-byte
+ *                               vector layouts (px_rbsor_n, multigrid
+ *                               smoothers): 0 automatic (1), 1 one fused
+ *                               launch, 2 a red pass and a black pass.
  * px_set_option returns PX_EINVAL for an unknown option or a value out of
  * range; it affects calls made through ctx afterwards. */
-enum { PX_OPT_FP32_FAMILY = 1, PX_OPT_RB_SWEEPS_PER_LAUNCH = 2, PX_OPT_BATCH_LAUNCHES = 3 };
+enum {
+  PX_OPT_FP32_FAMILY = 1,
+  PX_OPT_RB_SWEEPS_PER_LAUNCH = 2,
+  PX_OPT_BATCH_LAUNCHES = 3,
+  PX_OPT_RB_FP64_PASSES = 4
+};
 px_status px_set_option(px_ctx* ctx, int option, int value);
 px_status px_get_option(const px_ctx* ctx, int option, int* value);
 
@@ -221,9 +230,12 @@ px_status px_relax_n_static(const px_grid* g, const void* phi_in, void* phi_out,
  *  phi_in, phi_out, rho, omega, nsweeps, resid_dev, report_every, stream
  *                   as in px_relax_n; resid_dev[k] is the residual of the
  *                   INPUT state of sweep k * report_every, over all cells.
- * Each sweep is two launches (red pass out of place with the residual, black
- * pass in place); the context's scratch field is used when in place or for
- * two sweeps or more. Asynchronous. */
+ * Launches: FP32 16-byte vector layouts run several sweeps per launch of a
+ * register wavefront (PX_OPT_RB_SWEEPS_PER_LAUNCH); FP64 vector layouts one
+ * fused launch per sweep, out of place (PX_OPT_RB_FP64_PASSES); other layouts
+ * two launches per sweep (red pass out of place with the residual, black pass
+ * in place). All give the same bits. The context's scratch field is used when
+ * in place or for two launches or more. Asynchronous. */
 px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* phi_out,
                      const void* rho, double omega, int nsweeps, double* resid_dev,
                      int report_every, void* stream);

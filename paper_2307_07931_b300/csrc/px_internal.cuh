@@ -173,6 +173,10 @@ cudaError_t launch_mg_prolong(const FieldDesc& f, const void* e, int64_t ldc, vo
 cudaError_t launch_rbsor_pass(const FieldDesc& f, const void* src, void* dst, const void* rho,
                               double omega, bool red_pass, bool vec, double* slot,
                               cudaStream_t st);
+// One red-black sweep src -> dst (out of place) in one launch: FP64, 16-byte
+// vector layouts; bitwise the red pass followed by the black pass.
+cudaError_t launch_rbsor_fused(const FieldDesc& f, const double* src, double* dst,
+                               const double* rho, double omega, double* slot, cudaStream_t st);
 
 cudaError_t launch_apply_stencil(const FieldDesc& f, const void* phi, void* out,
                                  cudaStream_t st);
@@ -245,6 +249,7 @@ struct px_ctx {
   int opt_fp32_family = 0;   // PX_OPT_FP32_FAMILY (0 = automatic)
   int opt_rb_sweeps = 0;     // PX_OPT_RB_SWEEPS_PER_LAUNCH (0 = automatic)
   int opt_batch_launches = 0;  // PX_OPT_BATCH_LAUNCHES (0 = automatic, 1 = one launch)
+  int opt_rb_fp64_passes = 0;  // PX_OPT_RB_FP64_PASSES (0 = automatic, 1 fused, 2 two passes)
   std::string err;
 };
 

@@ -245,3 +245,33 @@ def test_smoother_paths_bitwise(sweeps):
             assert torch.equal(a, b) and torch.equal(ra, rb), (nx, ny)
     finally:
         ctx.close()
+
+
+def test_fp64_smoother_fused_bitwise():
+    """On FP64 every level's smoother runs one fused launch per red-black sweep
+    (16-byte aligned levels) or a red and a black pass
+    (PX_OPT_RB_FP64_PASSES = 2); both evaluate the same per-cell expressions,
+    so whole cycles agree bitwise."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    ctxs = [px.Context(torch.cuda.current_device()) for _ in range(2)]
+    try:
+        ctxs[1].set_option(px.PX_OPT_RB_FP64_PASSES, 2)
+        g = torch.Generator(device="cuda")
+        g.manual_seed(9)
+        for (nx, ny) in [(1024, 512), (256, 256), (132, 68)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+            rho -= rho.mean()
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+            got = []
+            for ctx in ctxs:
+                a, ra = phi.clone(), torch.zeros(4, dtype=torch.float64, device="cuda")
+                px.mg_solve(a, rho, h, 3, resid=ra, ctx=ctx)
+                torch.cuda.synchronize()
+                got.append((a, ra))
+            assert torch.equal(got[0][0], got[1][0]) and torch.equal(got[0][1], got[1][1]), (nx, ny)
+    finally:
+        for c in ctxs:
+            c.close()

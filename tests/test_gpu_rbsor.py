@@ -288,3 +288,43 @@ def test_register_wavefront_depths_bitwise(sweeps):
                 assert torch.equal(op, out) and torch.equal(r1, r2), (nx, ny, omega)
     finally:
         ctx.close()
+
+
+def test_fp64_fused_sweep_bitwise():
+    """FP64 vector layouts run one fused launch per sweep (new red values of
+    the rows and columns next to a warp's block recomputed from the input);
+    the red pass + black pass form, selected with PX_OPT_RB_FP64_PASSES = 2,
+    evaluates the same expressions per cell, so states and reports agree
+    bitwise (the oracle tests above pin the fused form). Sizes cover several
+    strips of 30 column pairs and row segments, ragged strips, strips wider
+    than the grid and the smallest even extents; in place and out of place."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    fused, passes = px.Context(torch.cuda.current_device()), px.Context(torch.cuda.current_device())
+    try:
+        passes.set_option(px.PX_OPT_RB_FP64_PASSES, 2)
+        fused.set_option(px.PX_OPT_RB_FP64_PASSES, 1)
+        assert passes.get_option(px.PX_OPT_RB_FP64_PASSES) == 2
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        for (nx, ny) in [(4096, 2048), (1030, 514), (122, 66), (60, 64), (62, 6), (2, 2), (2, 130),
+                         (4, 300), (16384, 8)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+            for omega, every in ((1.0, 1), (1.7, 2), (0.9, 0)):
+                outs = []
+                for ctx in (passes, fused):
+                    out = torch.empty_like(phi)
+                    r = torch.zeros(7, dtype=torch.float64, device="cuda")
+                    px.rbsor_n(phi, out, rho, h, omega, 7, r if every else None, every, ctx=ctx)
+                    ip = phi.clone()
+                    px.rbsor_n(ip, ip, rho, h, omega, 3, None, 0, ctx=ctx)
+                    torch.cuda.synchronize()
+                    outs.append((out, r, ip))
+                (a, ra, ia), (b, rb, ib) = outs
+                assert torch.equal(a, b) and torch.equal(ra, rb) and torch.equal(ia, ib), (nx, ny, omega)
+    finally:
+        fused.close()
+        passes.close()

@@ -46,7 +46,8 @@ def test_option_values_are_checked():
     try:
         for opt, bad in ((px.PX_OPT_FP32_FAMILY, 5), (px.PX_OPT_FP32_FAMILY, -1),
                          (px.PX_OPT_RB_SWEEPS_PER_LAUNCH, 5), (px.PX_OPT_BATCH_LAUNCHES, 2),
-                         (px.PX_OPT_BATCH_LAUNCHES, -1), (99, 0)):
+                         (px.PX_OPT_BATCH_LAUNCHES, -1), (px.PX_OPT_RB_FP64_PASSES, 3),
+                         (99, 0)):
             with pytest.raises(px.PxError) as ei:
                 ctx.set_option(opt, bad)
             assert ei.value.status == px.PX_EINVAL
