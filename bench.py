@@ -42,13 +42,13 @@ MEASURED_TRAFFIC_PER_CELL = {("f32", 4): (2226466688 + 1045071360) / 16384**2,
 
 
 # red-black SOR: FP32 runs three sweeps (six colour stages) per launch of the
-# register wavefront; FP64 runs a red pass (all cells read, residual, red
-# updated) and a black pass (black updated in place) per sweep
-RBSOR_KERNEL = {"f32": "relaxR2_f32<6,true>", "f64": "rb_pass<double,2>"}
+# register wavefront; FP64 one fused launch per sweep (red and black updates,
+# the residual of every cell's input state)
+RBSOR_KERNEL = {"f32": "relaxR2_f32<6,true>", "f64": "rb_fused_f64<true>"}
 # FP64 sweep ceiling: 6 FP64 operations (3 DADD + 3 DFMA) per update at the
 # 0.555e12 FP64 operations/s measured on B300
 FP64_PIPE_GLUPS = 0.555e12 / 6 / 1e9
-RBSOR_LAUNCHES_PER_SWEEP = {"f32": 1.0 / 3.0, "f64": 2.0}
+RBSOR_LAUNCHES_PER_SWEEP = {"f32": 1.0 / 3.0, "f64": 1.0}
 
 
 def kernel_name(dt: str, tb: int, cells: int) -> str:
@@ -275,6 +275,10 @@ def bench_rbsor(px, torch, phi0, out, rho, resid, h, cells, hbm_peak, steps, war
                    "effective_GB_s": ALGO_BYTES[dt] * cells * SWEEPS / t / 1e9,
                    "launches_per_step": lps, "algo_GB_s_per_launch": per_launch,
                    "hbm_frac": per_launch / hbm_peak}
+        if dt == "f64":
+            # 8.5 FP64 operations per cell and reported sweep (red update 6, black
+            # update 6, the black cell's residual 5, per pair)
+            res[dt]["fp64_pipe_frac"] = res[dt]["GLUP_s"] / (0.555e12 / 8.5 / 1e9)
     return res
 
 
