@@ -26,6 +26,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cstring>
 
 namespace px {
@@ -59,19 +60,26 @@ struct ESmem {
 static_assert(sizeof(ESmem<float>::raw) % 128 == 0 && sizeof(ESmem<double>::raw) % 128 == 0,
               "raw is followed by the other arrays");
 
-// Reciprocal and sound speed sqrt(g p / rho) (g p passed as gp). FP64 takes
-// the IEEE operations; FP32 takes the hardware approximations (relative error
-// about 2^-22, far below the storage's own rounding of the fluxes):
-// c = gp rsqrt(gp rho), no division and no square root.
+// Reciprocal and sound speed sqrt(g p / rho) (g p passed as gp), the latter
+// as c = gp rsqrt(gp rho): no division and no square root. FP32 takes the
+// hardware approximations (relative error about 2^-22, far below the storage's
+// own rounding of the fluxes); FP64 the IEEE reciprocal and the library's
+// rsqrt (1 ulp), which costs the FP64 pipe about half of an IEEE division and
+// square root. The smallest normal number is added to gp rho (in the FMA that
+// forms the product, so at no cost): at p = 0 the product form would otherwise
+// be 0 * inf, and it gives c = 0 as sqrt(0 / rho) does; for gp rho well above
+// that number the rounded sum is the rounded product (one ulp apart only when
+// the exact product lies within the added number of a rounding midpoint), and a
+// negative or NaN pressure still gives NaN.
 template <typename T> __device__ __forceinline__ T recip(T v);
 template <> __device__ __forceinline__ float recip<float>(float v) { return __fdividef(1.0f, v); }
 template <> __device__ __forceinline__ double recip<double>(double v) { return 1.0 / v; }
 template <typename T> __device__ __forceinline__ T sound(T gp, T rho);
 template <> __device__ __forceinline__ float sound<float>(float gp, float rho) {
-  return gp * rsqrtf(gp * rho);
+  return gp * rsqrtf(fmaf(gp, rho, FLT_MIN));
 }
 template <> __device__ __forceinline__ double sound<double>(double gp, double rho) {
-  return sqrt(gp / rho);
+  return gp * rsqrt(fma(gp, rho, DBL_MIN));
 }
 
 template <typename T>

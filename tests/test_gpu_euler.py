@@ -89,6 +89,23 @@ def test_steps_match_oracle(px, nx, ny, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_pressureless_static_state_is_steady(px, dtype):
+    """p = 0 and u = v = 0 with varying density: the sound speed is 0 and every
+    flux vanishes (no pressure, no transport, a zero Rusanov coefficient), so
+    steps with a fixed dt leave the state unchanged bitwise, with no NaN (the
+    sound speed's product form g p rsqrt(g p rho) must not become 0 * inf)."""
+    rng = np.random.default_rng(3)
+    ny, nx = 40, 70
+    z = np.zeros((ny, nx))
+    U0 = E.conserved(np.stack([rng.uniform(0.5, 2.0, (ny, nx)), z, z, z]))
+    u = torch.from_numpy(U0).to(dtype).cuda()
+    out = torch.empty_like(u)
+    px.euler_step(u, out, 1.0 / nx, 1.0 / ny, 2, dt_fixed=1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(out, u)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_fixed_dt_and_in_place(px, dtype):
     rng = np.random.default_rng(5)
     nx, ny = 96, 64
