@@ -85,3 +85,28 @@ def test_binding_marshals_layout():
         px.grid_of(torch.zeros(4, 4, dtype=torch.int32), 1.0)
     with pytest.raises(ValueError):
         px.grid_of(torch.zeros(4, 4, dtype=torch.float32).t(), 1.0)
+
+
+def header_enum_values():
+    """name -> value of every PX_* enumerator with an explicit value in include/*.h."""
+    vals = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for body in re.findall(r"\benum\b[^{]*\{([^}]*)\}", text):
+            for m in re.finditer(r"\b(PX_\w+)\s*=\s*(-?\d+)", body):
+                vals[m.group(1)] = int(m.group(2))
+    return vals
+
+
+def test_binding_constants_match_header():
+    """The binding's PX_* integers (statuses, dtypes, options, solve modes) are
+    the header's enumerators, value for value."""
+    import paper_2307_07931_b300 as px
+    vals = header_enum_values()
+    for must in ("PX_OK", "PX_F64", "PX_F32", "PX_OPT_FP32_FAMILY", "PX_OPT_RB_FP64_PASSES",
+                 "PX_SOLVE_REFINE"):
+        assert must in vals, must
+    bound = {n: v for n, v in vals.items() if hasattr(px, n)}
+    assert {n: getattr(px, n) for n in bound} == bound
+    opts = [n for n in vals if n.startswith("PX_OPT_")]
+    assert all(hasattr(px, n) for n in opts), [n for n in opts if not hasattr(px, n)]
