@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libprotox.so")
 LIB_CHECKED = os.path.join(HERE, "libprotox_checked.so")
 # translation units whose kernels carry the checked build's bounds checks
-CHECKED_SOURCES = ("api.cu", "relax.cu", "euler.cu")
+CHECKED_SOURCES = ("api.cu", "relax.cu", "euler.cu", "rbsor.cu")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -30,8 +30,9 @@ def sources() -> list[str]:
 
 
 def deps() -> list[str]:
+    # this file too: its flags and source lists shape the libraries
     return (sources() + glob.glob(os.path.join(HERE, "csrc", "*.cuh"))
-            + glob.glob(os.path.join(ROOT, "include", "*.h")))
+            + glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)])
 
 
 def up_to_date(checked: bool = False) -> bool:

@@ -1,5 +1,5 @@
 """The checked build (libprotox_checked.so, -DPX_CHECKED): every global index
-the relaxation and Euler kernels compute is checked against the field's
+the relaxation, fused FP64 red-black and Euler kernels compute is checked against the field's
 extent before the access (the stand-in for a memory sanitizer). On the
 workloads below no check fails, and the checked build's results are bitwise
 those of the normal build (the checks change no arithmetic). The checked
@@ -41,6 +41,15 @@ def run(px):
         out[f"res_{nx}_{ny}_{tb}_{fam}"] = r.cpu().numpy()
         out[f"pitched_{nx}_{ny}_{tb}_{fam}"] = po.double().cpu().numpy()
         ctx.close()
+    for (nx, ny) in [(1030, 514), (62, 6), (4096, 1024)]:
+        rho = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+        phi = torch.randn(ny, nx, device="cuda", dtype=torch.float64, generator=g)
+        o = torch.empty_like(phi)
+        r = torch.zeros(5, dtype=torch.float64, device="cuda")
+        px.rbsor_n(phi, o, rho, 1.0 / nx, 1.3, 5, r, 1)  # one fused launch per sweep
+        torch.cuda.synchronize()
+        out[f"rb_{nx}_{ny}"] = o.cpu().numpy()
+        out[f"rbres_{nx}_{ny}"] = r.cpu().numpy()
     from oracle import euler as E
     rng = np.random.default_rng(4)
     for (nx, ny, dt) in [(130, 70, torch.float64), (512, 256, torch.float32), (33, 17, torch.float32)]:
