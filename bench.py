@@ -285,14 +285,16 @@ def bench_rbsor(px, torch, phi0, out, rho, resid, h, cells, hbm_peak, steps, war
 def mg_algo_bytes(n: int, es: int) -> float:
     """Algorithmic DRAM bytes of one V(2,2) cycle on an n x n field: on every
     level but the coarsest, a smoothing launch before and after (read phi and
-    rho, write phi: 3 elements per cell each), the residual-restriction (read
-    phi and rho, write the coarse rho and e: 2.5 per fine cell) and the
-    prolongation-correction (read the coarse e, read and write phi: 2.25)."""
+    rho, write phi: 3 elements per cell each) and the residual-restriction
+    (read phi and rho, write the coarse rho and e: 2.5 per fine cell); then the
+    interpolation-correction: in FP32 inside the post-smoothing launch, which
+    also reads the coarse e (0.25), in FP64 a pass of its own (read the coarse
+    e, read and write phi: 2.25)."""
     total, m = 0, n
     while m % 4 == 0:
         total += m * m
         m //= 2
-    return es * 10.75 * total
+    return es * (8.75 if es == 4 else 10.75) * total
 
 
 def bench_mg(px, torch, rho, h, n, hbm_peak, steps, warmup, ncycles=10):

@@ -138,13 +138,18 @@ px_status px_checked_faults(px_ctx* ctx, uint64_t* count, uint64_t* first);
  *                               vector layouts (px_rbsor_n, multigrid
  *                               smoothers): 0 automatic (1), 1 one fused
  *                               launch, 2 a red pass and a black pass.
+ *  PX_OPT_MG_PROLONG            multigrid interpolation + correction on levels
+ *                               that the FP32 register wavefront smooths:
+ *                               0 automatic (inside the first post-smoothing
+ *                               launch), 1 a pass of its own.
  * px_set_option returns PX_EINVAL for an unknown option or a value out of
  * range; it affects calls made through ctx afterwards. */
 enum {
   PX_OPT_FP32_FAMILY = 1,
   PX_OPT_RB_SWEEPS_PER_LAUNCH = 2,
   PX_OPT_BATCH_LAUNCHES = 3,
-  PX_OPT_RB_FP64_PASSES = 4
+  PX_OPT_RB_FP64_PASSES = 4,
+  PX_OPT_MG_PROLONG = 5
 };
 px_status px_set_option(px_ctx* ctx, int option, int value);
 px_status px_get_option(const px_ctx* ctx, int option, int* value);

@@ -25,7 +25,8 @@ LIB_CHECKED_PATH = os.path.join(HERE, "libprotox_checked.so")  # -DPX_CHECKED va
 PX_OK, PX_EINVAL, PX_ECUDA, PX_ENOMEM, PX_ENOCONV, PX_ETIMEOUT, PX_EMEAN, PX_ENAN, \
     PX_EUNSUPPORTED = range(9)
 PX_F64, PX_F32 = 0, 1
-PX_OPT_FP32_FAMILY, PX_OPT_RB_SWEEPS_PER_LAUNCH, PX_OPT_BATCH_LAUNCHES, PX_OPT_RB_FP64_PASSES = 1, 2, 3, 4
+(PX_OPT_FP32_FAMILY, PX_OPT_RB_SWEEPS_PER_LAUNCH, PX_OPT_BATCH_LAUNCHES, PX_OPT_RB_FP64_PASSES,
+ PX_OPT_MG_PROLONG) = 1, 2, 3, 4, 5
 
 
 class PxError(RuntimeError):

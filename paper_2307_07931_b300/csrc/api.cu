@@ -304,6 +304,11 @@ px_status px_set_option(px_ctx* c, int option, int value) {
         return fail(c, PX_EINVAL, "FP64 red-black passes option %d not in 0..2", value);
       c->opt_rb_fp64_passes = value;
       return PX_OK;
+    case PX_OPT_MG_PROLONG:
+      if (value < 0 || value > 1)
+        return fail(c, PX_EINVAL, "multigrid interpolation option %d not in 0..1", value);
+      c->opt_mg_prolong = value;
+      return PX_OK;
   }
   return fail(c, PX_EINVAL, "unknown option %d", option);
 }
@@ -315,6 +320,7 @@ px_status px_get_option(const px_ctx* c, int option, int* value) {
     case PX_OPT_RB_SWEEPS_PER_LAUNCH: *value = c->opt_rb_sweeps; return PX_OK;
     case PX_OPT_BATCH_LAUNCHES: *value = c->opt_batch_launches; return PX_OK;
     case PX_OPT_RB_FP64_PASSES: *value = c->opt_rb_fp64_passes; return PX_OK;
+    case PX_OPT_MG_PROLONG: *value = c->opt_mg_prolong; return PX_OK;
   }
   return PX_EINVAL;
 }
@@ -519,9 +525,12 @@ namespace {
 
 // n red-black sweeps alternating between the buffers a and b, from *cur (one
 // of them); *cur ends on the buffer that holds the result. With slot, the
-// residual of the first sweep's input state is folded into *slot.
+// residual of the first sweep's input state is folded into *slot. With pl
+// (FP32 vector layouts only, n > 0), the first launch adds the interpolated
+// coarse correction to *cur's values as it loads them.
 cudaError_t rb_sweeps_ab(px_ctx* c, const px::FieldDesc& f, void* a, void* b, void** cur,
-                         const void* rho, double omega, int n, double* slot, cudaStream_t st) {
+                         const void* rho, double omega, int n, double* slot, cudaStream_t st,
+                         const px::Prolong* pl = nullptr) {
   const bool vec = px::vector_ok(f, a, b, rho);
   const bool reg = f.dtype == 1 && vec;
   const bool fused = rb_fused(c, f, vec);
@@ -534,7 +543,7 @@ cudaError_t rb_sweeps_ab(px_ctx* c, const px::FieldDesc& f, void* a, void* b, vo
     cudaError_t e;
     if (reg) {
       e = px::launch_rbsor_reg(f, (const float*)src, (float*)dst, (const float*)rho, omega, k, s,
-                               0, n, c->sched, c->sched_cap, st);
+                               0, n, c->sched, c->sched_cap, st, done == 0 ? pl : nullptr);
     } else {
       e = rb_sweep(f, src, dst, rho, omega, fused, vec, s, st);
     }
@@ -646,9 +655,18 @@ px_status px_mg_solve(px_ctx* c, const px_grid* g, void* phi, const void* rho, i
                          L == 1 ? rep : nullptr, st));
     if (s != PX_OK) return s;
     for (int l = L - 2; l >= 0; --l) {
-      s = chk(px::launch_mg_prolong(lv[l], cur[l + 1], lv[l + 1].ld, cur[l], st));
-      if (s != PX_OK) return s;
-      s = chk(rb_sweeps_ab(c, lv[l], A[l], B[l], &cur[l], R[l], omega, nu2, nullptr, st));
+      // on levels that the FP32 register wavefront smooths, the interpolation
+      // and correction ride in the first post-smoothing launch's loads (one
+      // read and one write of the level fewer); elsewhere a pass of their own
+      const bool fold = nu2 > 0 && c->opt_mg_prolong != 1 && lv[l].dtype == 1 &&
+                        px::vector_ok(lv[l], A[l], B[l], R[l]);
+      const px::Prolong pl{(const float*)cur[l + 1], lv[l + 1].ld, lv[l + 1].nx, lv[l + 1].ny};
+      if (!fold) {
+        s = chk(px::launch_mg_prolong(lv[l], cur[l + 1], lv[l + 1].ld, cur[l], st));
+        if (s != PX_OK) return s;
+      }
+      s = chk(rb_sweeps_ab(c, lv[l], A[l], B[l], &cur[l], R[l], omega, nu2, nullptr, st,
+                           fold ? &pl : nullptr));
       if (s != PX_OK) return s;
     }
     if (cur[0] != phi) {

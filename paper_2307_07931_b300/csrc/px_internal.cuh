@@ -141,9 +141,19 @@ cudaError_t launch_relax(const FieldDesc& f, const void* src, void* dst,
 // `sweeps` (1..4) red-black SOR sweeps in one launch of the FP32 register
 // wavefront (two stages per sweep: red, then black); src != dst, vector
 // layout (vector_ok), nx and ny even. Reports as launch_relax (sweep s0 first).
+// Multigrid interpolation folded into a red-black launch of the FP32 register
+// wavefront: every input row is corrected by the bilinear interpolation of the
+// coarse correction e (nxc x nyc cells, row pitch ldc) as it is loaded, with the
+// operations of the separate interpolation pass (so bitwise its result).
+struct Prolong {
+  const float* e;
+  int64_t ldc;
+  int nxc, nyc;
+};
 cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, const float* rho,
                              double omega, int sweeps, double* resid, int s0, int every,
-                             unsigned long long* sched, int sched_cap, cudaStream_t st);
+                             unsigned long long* sched, int sched_cap, cudaStream_t st,
+                             const Prolong* pl = nullptr);
 
 // 3D fields (relax3.cu): unghosted, contiguous x, pitches ld (rows) and lp
 // (planes) in elements.
@@ -250,6 +260,7 @@ struct px_ctx {
   int opt_rb_sweeps = 0;     // PX_OPT_RB_SWEEPS_PER_LAUNCH (0 = automatic)
   int opt_batch_launches = 0;  // PX_OPT_BATCH_LAUNCHES (0 = automatic, 1 = one launch)
   int opt_rb_fp64_passes = 0;  // PX_OPT_RB_FP64_PASSES (0 = automatic, 1 fused, 2 two passes)
+  int opt_mg_prolong = 0;      // PX_OPT_MG_PROLONG (0 = automatic: fused, 1 = separate pass)
   std::string err;
 };
 

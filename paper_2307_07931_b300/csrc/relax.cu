@@ -865,11 +865,43 @@ struct R2Task {
   int y0, lim, lmax;
 };
 
-template <int TB, int P, bool kEdge, bool kRB, bool kPack, int kRep>
+// Bilinear interpolation of the coarse correction onto fine rows 2J, 2J + 1
+// (row pair a, b) at this lane's columns gx .. gx + 3 (gx a multiple of 4),
+// added to the loaded values: the expressions and order of mg_prolong_k.
+__device__ __forceinline__ void prolong_add(float (&ra)[4], float (&rb)[4], const Prolong& pl,
+                                            int J, int gx) {
+  const int I0 = gx >> 1, I1 = I0 + 1;
+  const int Il = I0 == 0 ? pl.nxc - 1 : I0 - 1, Ir = I1 + 1 == pl.nxc ? 0 : I1 + 1;
+  const int Ju = J == 0 ? pl.nyc - 1 : J - 1, Jd = J + 1 == pl.nyc ? 0 : J + 1;
+  float u[4] = {0.f, 0.f, 0.f, 0.f}, m[4] = {0.f, 0.f, 0.f, 0.f}, d[4] = {0.f, 0.f, 0.f, 0.f};
+  if (PX_IN_RANGE(35, J, 0, pl.nyc) && PX_IN_RANGE(36, I1, 0, pl.nxc)) {
+    const float* Eu = pl.e + (int64_t)Ju * pl.ldc;
+    const float* E0 = pl.e + (int64_t)J * pl.ldc;
+    const float* Ed = pl.e + (int64_t)Jd * pl.ldc;
+    u[0] = Eu[Il]; u[1] = Eu[I0]; u[2] = Eu[I1]; u[3] = Eu[Ir];
+    m[0] = E0[Il]; m[1] = E0[I0]; m[2] = E0[I1]; m[3] = E0[Ir];
+    d[0] = Ed[Il]; d[1] = Ed[I0]; d[2] = Ed[I1]; d[3] = Ed[Ir];
+  }
+  const float q = 0.1875f, o = 0.0625f;
+  const float c0 = 0.5625f * m[1], c1 = 0.5625f * m[2];
+  // columns gx, gx + 1 belong to coarse cell I0 (x neighbours Il, I1); gx + 2,
+  // gx + 3 to I1 (x neighbours I0, Ir); row a to J (y neighbour Ju), b (Jd)
+  ra[0] += fma(o, u[0], fma(q, m[0] + u[1], c0));
+  ra[1] += fma(o, u[2], fma(q, m[2] + u[1], c0));
+  ra[2] += fma(o, u[1], fma(q, m[1] + u[2], c1));
+  ra[3] += fma(o, u[3], fma(q, m[3] + u[2], c1));
+  rb[0] += fma(o, d[0], fma(q, m[0] + d[1], c0));
+  rb[1] += fma(o, d[2], fma(q, m[2] + d[1], c0));
+  rb[2] += fma(o, d[1], fma(q, m[1] + d[2], c1));
+  rb[3] += fma(o, d[3], fma(q, m[3] + d[2], c1));
+}
+
+template <int TB, int P, bool kEdge, bool kRB, bool kPack, int kRep, bool kProl = false>
 __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __restrict__ phi,
                                        const float* __restrict__ rho, float* __restrict__ out,
                                        float* ring, int nx, int ny, int64_t ld, int gx, bool own,
-                                       const R2Task& T, Coef<float> k, const bool (&due)[TB]) {
+                                       const R2Task& T, Coef<float> k, const bool (&due)[TB],
+                                       const Prolong& pl) {
   constexpr int W = 128;                      // strip floats per ring row
   float* const pr = ring;                     // phi ring, this lane's columns
   float* const rr_ = ring + kRPhiRing * W;    // rho ring
@@ -891,6 +923,10 @@ __device__ __forceinline__ void rstep2(R2State<TB>& S, int r0, const float* __re
   cp_wait<kR2Ahead>();
   lds4(S.win[0][2 * P], pr + (r0 & (kRPhiRing - 1)) * W);
   lds4(S.win[0][2 * P + 1], pr + ((r0 + 1) & (kRPhiRing - 1)) * W);
+  // input row r0 is global row y0 - TB + r0, even (red-black ranges start on
+  // even rows and TB is even), so the pair is coarse row (y0 - TB + r0) / 2
+  if constexpr (kProl) prolong_add(S.win[0][2 * P], S.win[0][2 * P + 1], pl,
+                                   wrapn(T.y0 - TB + r0, ny) >> 1, gx);
 #pragma unroll
   for (int t = 1; t <= TB; ++t) {
     // level t-1 rows r0-t-1 .. r0-t+2; r0 mod 4 = 2P
@@ -1068,11 +1104,12 @@ __device__ bool r2_steal(unsigned long long* sched, int me, int nw, int nstrips,
   return false;
 }
 
-template <int TB, bool kRB, bool kPack, int kRep>
+template <int TB, bool kRB, bool kPack, int kRep, bool kProl = false>
 __global__ void __launch_bounds__(r_warps<TB, kRB>() * 32)
 relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float* __restrict__ rho,
             int nx, int ny, int64_t ld, int H, int nstrips, int nseg, Coef<float> k, Reports rep,
-            unsigned long long* sched) {
+            unsigned long long* sched, Prolong pl) {
+  static_assert(!kProl || kRB, "the interpolation is folded into red-black launches only");
   static_assert(TB + 2 * kR2Ahead + 2 <= kRRhoRing, "rho rows in use exceed the ring");
   static_assert(!kRB || TB % 2 == 0, "red-black launches hold whole sweeps");
   extern __shared__ __align__(16) float rsm[];
@@ -1145,16 +1182,16 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
 #pragma unroll 1
     for (; r0 < kPro; r0 += 4) {
       if (!ready(r0)) goto task_done;
-      rstep2<TB, 0, true, kRB, kPack, kRep>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, true, kRB, kPack, kRep, kProl>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due, pl);
       if (!ready(r0 + 2)) goto task_done;
-      rstep2<TB, 1, true, kRB, kPack, kRep>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, true, kRB, kPack, kRep, kProl>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due, pl);
     }
 #pragma unroll 1
     for (;; r0 += 4) {
       if (!ready(r0)) break;
-      rstep2<TB, 0, false, kRB, kPack, kRep>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 0, false, kRB, kPack, kRep, kProl>(S, r0, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due, pl);
       if (!ready(r0 + 2)) break;
-      rstep2<TB, 1, false, kRB, kPack, kRep>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due);
+      rstep2<TB, 1, false, kRB, kPack, kRep, kProl>(S, r0 + 2, phi, rho, out, ring, nx, ny, ld, gx, own, T, k, due, pl);
     }
   task_done:
     cp_wait<0>();  // the next task's prologue reuses the ring slots
@@ -1170,15 +1207,15 @@ relaxR2_f32(const float* __restrict__ phi, float* __restrict__ out, const float*
   }
 }
 
-template <int TB, bool kRB, bool kPack, int kRep>
+template <int TB, bool kRB, bool kPack, int kRep, bool kProl = false>
 cudaError_t reg2_occupancy(int& occ) {
   static int occ_by_dev[64] = {};
   int& o = occ_by_dev[dev_index()];
   if (o == 0) {
-    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB, kPack, kRep>,
+    cudaError_t e = cudaFuncSetAttribute(relaxR2_f32<TB, kRB, kPack, kRep, kProl>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, relaxR2_f32<TB, kRB, kPack, kRep>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, relaxR2_f32<TB, kRB, kPack, kRep, kProl>,
                                                       r_warps<TB, kRB>() * 32, r_smem<TB, kRB>());
     if (e != cudaSuccess) return e;
     if (o < 1) return cudaErrorInvalidConfiguration;
@@ -1190,7 +1227,7 @@ cudaError_t reg2_occupancy(int& occ) {
 template <int TB, bool kRB = false, bool kPack = false>
 cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, const float* rho,
                           Coef<float> k, Reports rep, unsigned long long* sched, int sched_cap,
-                          cudaStream_t st) {
+                          cudaStream_t st, const Prolong* pl = nullptr) {
   // Jacobi depth 8 without reports: no per-stage flags live, which leaves the
   // packed residual and update room without spills (2828 against 2673 GLUP/s
   // at 16384^2). With every stage reported the compile-time pattern measured
@@ -1202,8 +1239,10 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
     for (int t = 0; t < TB; ++t) any = any || rep.due(t);
     kind = any ? kRepRun : kRepNone;
   }
+  const bool prol = kRB && pl != nullptr;
   int occ = 0;
   cudaError_t e0 = kind == kRepNone ? reg2_occupancy<TB, kRB, kPack, kRepNone>(occ)
+                   : prol           ? reg2_occupancy<TB, kRB, kPack, kRepRun, kRB>(occ)
                                     : reg2_occupancy<TB, kRB, kPack, kRepRun>(occ);
   if (e0 != cudaSuccess) return e0;
   const int nstrips = (f.nx + r_owned<TB>() - 1) / r_owned<TB>();
@@ -1227,12 +1266,16 @@ cudaError_t launch_reg2_t(const FieldDesc& f, const float* src, float* dst, cons
   const dim3 grid(blocks), cta(r_warps<TB, kRB>() * 32);
   const size_t smem = r_smem<TB, kRB>();
   unsigned long long* const sc = dyn ? sched : nullptr;
+  const Prolong p = pl ? *pl : Prolong{nullptr, 0, 0, 0};
   if (kind == kRepNone)
-    relaxR2_f32<TB, kRB, kPack, kRepNone><<<grid, cta, smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
-                                                                   (int)H, nstrips, nseg, k, rep, sc);
+    relaxR2_f32<TB, kRB, kPack, kRepNone><<<grid, cta, smem, st>>>(
+        src, dst, rho, f.nx, f.ny, f.ld, (int)H, nstrips, nseg, k, rep, sc, p);
+  else if (prol)
+    relaxR2_f32<TB, kRB, kPack, kRepRun, kRB><<<grid, cta, smem, st>>>(
+        src, dst, rho, f.nx, f.ny, f.ld, (int)H, nstrips, nseg, k, rep, sc, p);
   else
-    relaxR2_f32<TB, kRB, kPack, kRepRun><<<grid, cta, smem, st>>>(src, dst, rho, f.nx, f.ny, f.ld,
-                                                                  (int)H, nstrips, nseg, k, rep, sc);
+    relaxR2_f32<TB, kRB, kPack, kRepRun><<<grid, cta, smem, st>>>(
+        src, dst, rho, f.nx, f.ny, f.ld, (int)H, nstrips, nseg, k, rep, sc, p);
   return cudaGetLastError();
 }
 
@@ -1373,7 +1416,8 @@ int device_sm_count() {
 
 cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, const float* rho,
                              double omega, int sweeps, double* resid, int s0, int every,
-                             unsigned long long* sched, int sched_cap, cudaStream_t st) {
+                             unsigned long long* sched, int sched_cap, cudaStream_t st,
+                             const Prolong* pl) {
   Reports rep;
   rep.resid = (resid && every > 0) ? resid : nullptr;
   rep.s0 = s0;
@@ -1382,10 +1426,10 @@ cudaError_t launch_rbsor_reg(const FieldDesc& f, const float* src, float* dst, c
   k.c = (float)(omega * f.h * f.h / 4.0);
   k.ih2 = (float)(1.0 / (f.h * f.h));
   switch (sweeps) {
-    case 1: return launch_reg2_t<2, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
-    case 2: return launch_reg2_t<4, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
-    case 3: return launch_reg2_t<6, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
-    case 4: return launch_reg2_t<8, true>(f, src, dst, rho, k, rep, sched, sched_cap, st);
+    case 1: return launch_reg2_t<2, true>(f, src, dst, rho, k, rep, sched, sched_cap, st, pl);
+    case 2: return launch_reg2_t<4, true>(f, src, dst, rho, k, rep, sched, sched_cap, st, pl);
+    case 3: return launch_reg2_t<6, true>(f, src, dst, rho, k, rep, sched, sched_cap, st, pl);
+    case 4: return launch_reg2_t<8, true>(f, src, dst, rho, k, rep, sched, sched_cap, st, pl);
     default: return cudaErrorInvalidValue;
   }
 }

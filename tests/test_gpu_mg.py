@@ -275,3 +275,37 @@ def test_fp64_smoother_fused_bitwise():
     finally:
         for c in ctxs:
             c.close()
+
+
+@pytest.mark.parametrize("nu2", [1, 2, 3, 4])
+def test_interpolation_in_smoother_bitwise(nu2):
+    """On FP32 levels that the register wavefront smooths, the interpolation and
+    correction run inside the first post-smoothing launch (each input row gets
+    its correction as it is loaded), with the operations of the separate pass
+    (PX_OPT_MG_PROLONG = 1): whole cycles and their reports agree bitwise, for
+    one to four post-smoothing sweeps (one or two launches), on grids whose
+    levels cover several strips, ragged strips and row ranges of one pair."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2307_07931_b300 as px
+    ctxs = [px.Context(torch.cuda.current_device()) for _ in range(2)]
+    try:
+        ctxs[1].set_option(px.PX_OPT_MG_PROLONG, 1)
+        assert ctxs[1].get_option(px.PX_OPT_MG_PROLONG) == 1
+        g = torch.Generator(device="cuda")
+        g.manual_seed(11)
+        for (nx, ny) in [(4096, 2048), (1024, 512), (520, 264), (132, 68), (16, 8)]:
+            h = 1.0 / nx
+            rho = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            rho -= rho.mean()
+            phi = torch.randn(ny, nx, device="cuda", dtype=torch.float32, generator=g)
+            got = []
+            for ctx in ctxs:
+                a, ra = phi.clone(), torch.zeros(4, dtype=torch.float64, device="cuda")
+                px.mg_solve(a, rho, h, 3, nu1=2, nu2=nu2, resid=ra, ctx=ctx)
+                torch.cuda.synchronize()
+                got.append((a, ra))
+            assert torch.equal(got[0][0], got[1][0]) and torch.equal(got[0][1], got[1][1]), (nx, ny)
+    finally:
+        for c in ctxs:
+            c.close()

@@ -47,6 +47,7 @@ def test_option_values_are_checked():
         for opt, bad in ((px.PX_OPT_FP32_FAMILY, 5), (px.PX_OPT_FP32_FAMILY, -1),
                          (px.PX_OPT_RB_SWEEPS_PER_LAUNCH, 5), (px.PX_OPT_BATCH_LAUNCHES, 2),
                          (px.PX_OPT_BATCH_LAUNCHES, -1), (px.PX_OPT_RB_FP64_PASSES, 3),
+                         (px.PX_OPT_MG_PROLONG, 2),
                          (99, 0)):
             with pytest.raises(px.PxError) as ei:
                 ctx.set_option(opt, bad)
