@@ -13,6 +13,9 @@
 //    quarter of a coarse cell from centre (J, I) towards its x neighbour
 //    I - 1 (a = 0) or I + 1 (a = 1), and likewise in y, so it receives
 //    9/16 e(J, I) + 3/16 (e(J, I') + e(J', I)) + 1/16 e(J', I').
+//    Levels that the FP32 register wavefront smooths do this inside the first
+//    post-smoothing launch instead (prolong_add in relax.cu, the same
+//    expressions); this pass serves FP64 and layouts off the 16-byte grid.
 // A thread owns one coarse cell; a block covers 32 coarse columns x 8 coarse
 // rows and strides over rows, so neighbouring threads share fine rows through
 // L1. Per-cell arithmetic (FMA form, storage type T):
