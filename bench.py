@@ -369,6 +369,18 @@ def bench_relax3(px, torch, hbm_peak, steps, warmup, n=512, sweeps=50):
     return out
 
 
+def batch_fp64_ops(classes: dict) -> int:
+    """FP64 operations per sweep of a batch plan's FP64 instances, from the
+    plan's classes ("f64:NXxNY@cC[s]": count, mode): 6 per update in shared
+    memory (WHOLE), 5 banded (rho pre-scaled by -c)."""
+    ops = 0
+    for key, v in classes.items():
+        if key.startswith("f64:"):
+            cnx, cny = (int(t) for t in key.split(":")[1].split("@")[0].split("x"))
+            ops += v["count"] * cnx * cny * (6 if v["mode"] == "whole" else 5)
+    return ops
+
+
 def bench_batched(px, torch, steps: int, warmup: int):
     """1024 uneven instances (N = 16 j, 32..1024, log-uniform; FP64/FP32 by coin;
     8 modes each), 300 sweeps each, one persistent launch per step, tuned per size
@@ -407,13 +419,7 @@ def bench_batched(px, torch, steps: int, warmup: int):
     b.close()
     total = (cells[0] + cells[1]) * (BATCH_SWEEPS)
     whole = sum(v["count"] for v in d["classes"].values() if v["mode"] == "whole")
-    # FP64-pipe bound of the FP64 instances at their kernels' operations per
-    # update: 6 in shared memory (WHOLE), 5 banded (rho pre-scaled by -c)
-    f64_ops = 0
-    for key, v in d["classes"].items():
-        if key.startswith("f64:"):
-            cnx, cny = (int(t) for t in key.split(":")[1].split("@")[0].split("x"))
-            f64_ops += v["count"] * cnx * cny * (6 if v["mode"] == "whole" else 5)
+    f64_ops = batch_fp64_ops(d["classes"])
     return {"instances": 1024, "sweeps": BATCH_SWEEPS, "cells": cells[0] + cells[1],
             "fp64_cells": cells[0], "fp32_cells": cells[1], "ms": 1000 * t,
             "GLUP_s": total / t / 1e9, "launches_per_step": d.get("launches", 1),

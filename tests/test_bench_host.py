@@ -68,3 +68,14 @@ def test_digest_is_short_and_complete():
     assert d["c3"]["noise_free"] == [3, 1.0, 1e-11]
     assert d["euler"]["f32"] == [2.0, 0.8]
     assert len(json.dumps(d)) < 1000
+
+
+def test_batch_fp64_bound_operations():
+    """FP64 instances count 6 operations per update in shared memory and 5
+    banded; FP32 classes do not count."""
+    classes = {"f64:64x64@c2": {"count": 3, "mode": "whole"},
+               "f64:512x256@c2s": {"count": 2, "mode": "banded"},
+               "f32:1024x1024@c2": {"count": 7, "mode": "banded_t"}}
+    assert bench.batch_fp64_ops(classes) == 3 * 64 * 64 * 6 + 2 * 512 * 256 * 5
+    assert bench.batch_fp64_ops({}) == 0
+
