@@ -273,7 +273,10 @@ px_status px_rbsor_n(px_ctx* ctx, const px_grid* g, const void* phi_in, void* ph
  *                 storage precision (FMA form): [k < ncycles] by the cycle's
  *                 first kernel, [ncycles] by a residual pass over the final
  *                 state (in FP64 when the grid has a single level).
- * Working memory: the context's scratch field (phi's span) and one allocation
+ * On FP32 levels with 16-byte aligned rows the interpolation and correction
+ * are done by the first post-smoothing launch as it loads its input (the same
+ * operations, so the same bits; PX_OPT_MG_PROLONG = 1 keeps a pass of their
+ * own). Working memory: the context's scratch field (phi's span) and one allocation
  * of three fields per coarser level (a field's size in all), kept by the
  * context; PX_ENOMEM when it cannot be had. Asynchronous. */
 px_status px_mg_solve(px_ctx* ctx, const px_grid* g, void* phi, const void* rho, int ncycles,
